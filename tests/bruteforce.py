@@ -1,0 +1,105 @@
+"""Exact brute-force Tukey depth for tiny inputs, independent of the oracle.
+
+Eq. (1) (Section 1) defines T = min over unit u of #{i : u'(X_i - z) <= 0}.
+The minimum is taken in an open cell of the arrangement of the hyperplanes
+u'x_i = 0 (x_i = X_i - z nonzero): a generic direction does at least as well as
+any direction on a hyperplane.  Hence
+
+    T = #{x_i = 0} + min over sign vectors s in {+1,-1}^{n'} that are realisable
+        (some u has s_i u'x_i > 0 for every nonzero x_i) of #{i : s_i = -1}.
+
+Realisability of a system of strict homogeneous inequalities a_i'u > 0 is
+decided exactly by Fourier-Motzkin elimination on Python integers.  Nothing
+here shares code or arithmetic with ``oracle/``: it never projects, sorts or
+sweeps.
+
+A second, polynomial check for p = 2 enumerates the halfplanes just beside
+every critical line through the origin.
+"""
+from itertools import combinations
+from math import gcd
+
+
+def _normalise(row):
+    g = 0
+    for v in row:
+        g = gcd(g, abs(v))
+    if g > 1:
+        row = tuple(v // g for v in row)
+    return row
+
+
+def strictly_feasible(rows):
+    """True iff some u satisfies a'u > 0 for every a in rows (integer tuples)."""
+    rows = {_normalise(tuple(r)) for r in rows}
+    if not rows:
+        return True
+    d = len(next(iter(rows)))
+    for var in range(d - 1, -1, -1):
+        if any(all(v == 0 for v in r) for r in rows):
+            return False  # 0 > 0
+        pos = [r for r in rows if r[var] > 0]
+        neg = [r for r in rows if r[var] < 0]
+        new = {r[:var] for r in rows if r[var] == 0}
+        for a in pos:
+            for b in neg:
+                c = tuple(a[j] * (-b[var]) + b[j] * a[var] for j in range(var))
+                new.add(_normalise(c))
+        rows = new
+        if not rows:
+            return True
+    # every variable eliminated: each remaining row reads 0 > 0
+    return not rows
+
+
+def depth_bruteforce(X, z):
+    """Exact closed-halfspace depth count by sign-vector enumeration (tiny n)."""
+    X = [tuple(int(v) for v in row) for row in X]
+    z = tuple(int(v) for v in z)
+    xs = [tuple(a - b for a, b in zip(row, z)) for row in X]
+    Z = sum(1 for x in xs if all(v == 0 for v in x))
+    nz = [x for x in xs if any(v != 0 for v in x)]
+    m = len(nz)
+    for k in range(m + 1):  # fewest negatives first
+        for neg in combinations(range(m), k):
+            negset = set(neg)
+            rows = [tuple(-v for v in x) if i in negset else x for i, x in enumerate(nz)]
+            if strictly_feasible(rows):
+                return Z + k
+    raise AssertionError("unreachable: the all-positive or all-negative side of a cell exists")
+
+
+def depth_p1(X, z):
+    """p = 1 (Section 3): the smaller of #{X <= z} and #{X >= z}."""
+    xs = [int(r[0]) - int(z[0]) for r in X]
+    return min(sum(1 for v in xs if v <= 0), sum(1 for v in xs if v >= 0))
+
+
+def depth_p2_halfplanes(X, z):
+    """p = 2: count every closed halfplane through z just beside a critical line.
+
+    The count is piecewise constant in the direction u and changes only where u
+    is orthogonal to some nonzero x_i.  Each open arc between critical
+    directions is sampled by u = d + eps*d_perp for a critical direction d
+    (both orientations of both lines), with eps infinitesimal: then the sign of
+    u'x is sign(d'x), or sign(d_perp'x) when d'x = 0.  O(n^2) in total.
+    """
+    xs = [(int(a) - int(z[0]), int(b) - int(z[1])) for a, b in X]
+    Z = sum(1 for x in xs if x == (0, 0))
+    nz = [x for x in xs if x != (0, 0)]
+    if not nz:
+        return Z
+    best = None
+    for (a, b) in nz:
+        for d in ((-b, a), (b, -a)):           # directions orthogonal to x_i
+            for side in (1, -1):
+                dp = (-d[1] * side, d[0] * side)  # the two tilts
+                cnt = 0
+                for x in nz:
+                    s = d[0] * x[0] + d[1] * x[1]
+                    if s == 0:
+                        s = dp[0] * x[0] + dp[1] * x[1]
+                    if s < 0:
+                        cnt += 1
+                best = cnt if best is None else min(best, cnt)
+    return Z + best

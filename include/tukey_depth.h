@@ -1,0 +1,162 @@
+/*
+ * tukey_depth.h -- C ABI of libtukeydepth.so: the exact sample Tukey
+ * (halfspace) depth on an NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Eq. 1, Section 1): for n data points X_1..X_n in Z^p and a
+ * query point z, the depth count
+ *
+ *     T(z) = n * D_n(z) = min over unit u of #{ i : u'(X_i - z) <= 0 },
+ *
+ * the fewest data points in a closed halfspace whose boundary passes through
+ * z.  It is computed by the paper's first exact algorithm (Algorithm 1,
+ * Section 3): the minimum over all (p-2)-subsets S of the centred data of a
+ * bivariate count (Algorithm 2, Section 3) of the data projected onto the 2-D
+ * quotient of R^p by span(S), made exact for data that are not in general
+ * position (Section 2 assumes general position):
+ *
+ *   - comparisons of projected directions are decided in FP32 when a forward
+ *     error bound certifies them and otherwise by exact integer determinants;
+ *   - equal directions are flipped together (Algorithm 2, step 1(e));
+ *   - the "- (p-2)" of Algorithm 1, step 2 is replaced per subset by the
+ *     number of data points in span(S) that a tilt out of the quotient can
+ *     move off the closed halfspace (exact for every input);
+ *   - data whose centred points span fewer than p dimensions are solved in
+ *     that many coordinates; p = 1 is the trivial case of Section 3 and p = 2
+ *     is Algorithm 2 alone.
+ * The result is the integer count T in [0, n] (the paper returns T / n).
+ *
+ * Conventions for every entry point:
+ *   - X is n x p int32, row-major (point i at X[i*p .. i*p+p-1]); query points
+ *     Z are m x p int32, row-major; out is m int32.
+ *   - Pointers are host pointers unless the context was created (or set) with
+ *     td_options.device_pointers != 0, in which case they are device pointers
+ *     of the context's device, used in stream order on the context's stream.
+ *   - The caller owns every buffer.  Host inputs are copied before the call
+ *     returns (td_depth, td_depth_batched) or before td_stream_submit returns.
+ *     Results are written before td_depth / td_depth_batched return, or before
+ *     td_stream_wait returns (td_stream_poll reports done).
+ *   - Limits: 1 <= p <= TD_MAX_P, 1 <= n <= TD_MAX_N, m >= 0; for every query z
+ *     and coordinate j, |X_ij - z_j| must not exceed td_coord_limit(p), which
+ *     keeps every exact intermediate inside 64-bit (coordinates, minors,
+ *     projections) or 128-bit (cross products) integers.
+ *   - Return value 0 (TD_OK) or a negative TD_ERR_* code; on error no output
+ *     element is written (no partial results).  td_strerror() names a code.
+ *   - Results are bit-exact and independent of scheduling; the statistics
+ *     counters may vary with scheduling.
+ */
+#ifndef TUKEY_DEPTH_H
+#define TUKEY_DEPTH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TD_OK 0
+#define TD_ERR_INVALID (-1) /* null pointer, n < 1, m < 0, p outside [1, TD_MAX_P], n > TD_MAX_N */
+#define TD_ERR_RANGE (-2)   /* some |X_ij - z_j| exceeds td_coord_limit(p) */
+#define TD_ERR_OOM (-3)     /* device or pinned host allocation failed */
+#define TD_ERR_BUSY (-4)    /* stream admission refused: request exceeds the memory budget now */
+#define TD_ERR_TIMEOUT (-5) /* td_stream_wait expired before the request finished */
+#define TD_ERR_CUDA (-6)    /* a CUDA runtime call failed (see td_last_cuda_error) */
+#define TD_ERR_NOTFOUND (-7) /* unknown stream ticket */
+#define TD_ERR_INTERNAL (-8) /* a device-side consistency check failed */
+
+#define TD_MAX_P 6
+#define TD_MAX_N 2048
+
+typedef struct td_ctx td_ctx;
+typedef struct td_stream td_stream;
+
+/* Execution forms of the same computation (identical results). */
+#define TD_MODE_FILTERED 0    /* persistent launch over (dataset, query, subset-tile) work,
+                                 FP32 filter with exact fallback, angular buckets */
+#define TD_MODE_PLAIN_EXACT 1 /* one launch per query, every projection and comparison in
+                                 exact integer arithmetic, comparison sort */
+
+typedef struct {
+    int32_t mode;             /* TD_MODE_FILTERED (default) or TD_MODE_PLAIN_EXACT */
+    int32_t device_pointers;  /* nonzero: X, Z, out are device pointers */
+    int32_t use_graph;        /* nonzero (default): replay the launch sequence of a batched call
+                                 from a captured CUDA graph when the shapes repeat */
+    int32_t subsets_per_warp; /* work-tile size (subsets per warp per tile); 0 = autotuned */
+    int32_t buckets_log2;     /* angular buckets per sweep = 2^buckets_log2; 0 = autotuned */
+    int32_t reserved;
+    int64_t shard_index;      /* multi-GPU sharding of Algorithm 1's subset loop: process only the */
+    int64_t shard_count;      /* shard_index-th of shard_count contiguous ranges of subset positions
+                                 of every query (0 or 1: all).  out[q] is then the minimum over that
+                                 range (INT32_MAX if it holds no subset); the minimum of out[q] over
+                                 all shards is the depth. */
+    void *stream;             /* cudaStream_t to run on; NULL = the context's own stream */
+} td_options;
+
+/* One dataset with its queries, for td_depth_batched and td_stream_submit. */
+typedef struct {
+    int32_t n, p;
+    const int32_t *X; /* n x p */
+    int32_t m;
+    const int32_t *Z; /* m x p */
+    int32_t *out;     /* m */
+} td_dataset;
+
+/* Per-call statistics (counts summed over queries). */
+typedef struct {
+    uint64_t sweeps;            /* (query, subset of rank p-2) pairs swept (Algorithm 1 step 1) */
+    uint64_t skipped_dependent; /* subsets of rank < p-2, skipped */
+    uint64_t filtered_points;   /* projected points placed by the FP32 filter alone */
+    uint64_t exact_points;      /* projected points that needed exact integer arithmetic */
+    uint64_t tight_exceptions;  /* subsets whose span holds more data points than the subset */
+    uint64_t resolved_buckets;  /* sweeps whose extremum needed an exact in-bucket order */
+    uint64_t kernel_launches;   /* CUDA kernels launched by the call */
+    float ms;                   /* device time from first to last kernel of the call */
+} td_stats;
+
+/* Coordinate bound |X_ij - z_j| <= td_coord_limit(p) accepted for dimension p. */
+int64_t td_coord_limit(int32_t p);
+
+/* Create a context on CUDA device `device`; opt may be NULL (defaults).
+ * The context owns a CUDA stream, device work buffers (grown on demand) and
+ * pinned staging memory.  Not thread-safe: one host thread per context. */
+int td_create(td_ctx **ctx, int device, const td_options *opt);
+
+/* Replace the context's options (same meaning as in td_create). */
+int td_set_options(td_ctx *ctx, const td_options *opt);
+
+/* Wait for outstanding work and free everything the context owns. */
+int td_destroy(td_ctx *ctx);
+
+/* out[q] = T(Z_q) for the m queries Z (m x p) against data X (n x p).
+ * Algorithm 1 (Section 3) with Algorithm 2 as the inner count; Eq. (1). */
+int td_depth(td_ctx *ctx, const int32_t *X, int32_t n, int32_t p,
+             const int32_t *Z, int32_t m, int32_t *out, td_stats *st);
+
+/* The same for k independent datasets (each with its own n, p and queries),
+ * served by one persistent launch over (dataset, query, subset-tile) work. */
+int td_depth_batched(td_ctx *ctx, const td_dataset *sets, int32_t k, td_stats *st);
+
+/* Asynchronous request stream.  A request is admitted only while the device
+ * memory it needs fits under mem_budget_bytes together with the requests in
+ * flight; otherwise td_stream_submit returns TD_ERR_BUSY and changes nothing.
+ * Admitted requests run in submission order on the stream's own CUDA stream;
+ * their inputs are copied before td_stream_submit returns and their state
+ * stays on the device until td_stream_wait (or a poll that reports done)
+ * has copied the outputs into the request's out buffer. */
+int td_stream_create(td_ctx *ctx, size_t mem_budget_bytes, td_stream **s);
+int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *ticket);
+/* *done = 1 once the request's outputs have been written to its out buffer. */
+int td_stream_poll(td_stream *s, uint64_t ticket, int *done);
+/* Block until done or until timeout_us microseconds pass (TD_ERR_TIMEOUT;
+ * the request stays in flight).  timeout_us < 0 waits without limit. */
+int td_stream_wait(td_stream *s, uint64_t ticket, int64_t timeout_us);
+int td_stream_destroy(td_stream *s);
+
+const char *td_strerror(int code);
+/* Text of the last CUDA error seen by this context (empty if none). */
+const char *td_last_cuda_error(td_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUKEY_DEPTH_H */

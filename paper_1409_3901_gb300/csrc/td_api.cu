@@ -1,0 +1,840 @@
+/*
+ * td_api.cu -- host side of the C ABI declared in include/tukey_depth.h.
+ *
+ * A call packs its datasets into device arenas, then runs on one CUDA stream
+ *   set-up kernel -> tile-prefix kernel -> persistent sweep kernel -> finalize
+ * (TD_MODE_FILTERED; the launch sequence is captured once as a CUDA graph and
+ * replayed while the shapes repeat), or
+ *   set-up kernel -> one plain exact launch per query -> finalize
+ * (TD_MODE_PLAIN_EXACT), and copies the outputs out after checking the
+ * device-side error counter, so that no partial result is ever written.
+ */
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/tukey_depth.h"
+#include "td_internal.h"
+
+/* kernels and launch helpers (td_kernels.cu) */
+size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps);
+size_t td_plain_smem(int nmax, int pmax, int warps);
+int64_t td_scratch_per_warp(int nmax);
+cudaError_t td_launch_setup(const TdLaunch &L, cudaStream_t s);
+cudaError_t td_launch_tiles(const TdLaunch &L, cudaStream_t s);
+cudaError_t td_launch_filtered(const TdLaunch &L, int grid, size_t smem, cudaStream_t s);
+cudaError_t td_launch_plain(const TdLaunch &L, int q, int grid, size_t smem, cudaStream_t s);
+cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s);
+int td_filtered_occupancy(int warps, size_t smem);
+int td_plain_occupancy(int warps, size_t smem);
+cudaError_t td_prepare_filtered(size_t smem);
+cudaError_t td_prepare_plain(size_t smem);
+
+namespace {
+
+const int kWarpsFiltered = 8;
+const int kWarpsPlain = 4;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+/* Grow-only device buffer. */
+cudaError_t grow(DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.cap) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = std::max(bytes, (size_t)256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e == cudaSuccess) b.cap = want;
+    return e;
+}
+
+struct HostBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+cudaError_t grow_host(HostBuf &b, size_t bytes)
+{
+    if (bytes <= b.cap) return cudaSuccess;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = std::max(bytes, (size_t)256);
+    cudaError_t e = cudaMallocHost(&b.p, want);
+    if (e == cudaSuccess) b.cap = want;
+    return e;
+}
+
+/* Device state of one batched call (or one stream request). */
+struct Work {
+    DevBuf X, Zq, sets, q, order, prefix, tsize, ticket, qmin, out, ctr, scratch;
+    int grid_filtered = 0;
+};
+
+struct GraphKey {
+    int nq, nsets, nmax, pmax, grid, blog2, spw;
+    size_t smem;
+    const void *ptrs[13];
+    int64_t shard_index, shard_count;
+    bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+}  // namespace
+
+struct td_ctx {
+    int device = 0;
+    int sms = 0;
+    td_options opt;
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    Work w;
+    HostBuf hstage, hout;
+    std::string cuda_err;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    bool gvalid = false;
+};
+
+struct td_stream_req {
+    uint64_t ticket;
+    Work w;
+    HostBuf hin, hout;
+    int32_t *user_out;
+    int32_t m;
+    cudaEvent_t done;
+    size_t bytes;
+    bool finished;
+    int status;
+};
+
+struct td_stream {
+    td_ctx *ctx;
+    cudaStream_t s;
+    size_t budget, inflight;
+    uint64_t next;
+    DevBuf scratch;
+    std::vector<td_stream_req *> reqs;
+};
+
+namespace {
+
+int fail_cuda(td_ctx *c, cudaError_t e, const char *what)
+{
+    if (c) {
+        c->cuda_err = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    return e == cudaErrorMemoryAllocation ? TD_ERR_OOM : TD_ERR_CUDA;
+}
+
+#define TDCK(call)                                              \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return fail_cuda(ctx, _e, #call); \
+    } while (0)
+
+td_options default_options()
+{
+    td_options o;
+    memset(&o, 0, sizeof(o));
+    o.mode = TD_MODE_FILTERED;
+    o.use_graph = 1;
+    o.shard_count = 1;
+    return o;
+}
+
+cudaStream_t stream_of(td_ctx *c) { return c->opt.stream ? (cudaStream_t)c->opt.stream : c->own; }
+
+int validate_set(const td_dataset &d)
+{
+    if (d.n < 1 || d.n > TD_MAX_N || d.p < 1 || d.p > TD_MAX_P || d.m < 0) return TD_ERR_INVALID;
+    if (!d.X || (d.m > 0 && (!d.Z || !d.out))) return TD_ERR_INVALID;
+    return TD_OK;
+}
+
+/* |X_ij - z_j| <= limit for every query, from the per-coordinate range of X. */
+bool range_ok(const td_dataset &d)
+{
+    int64_t lim = td_coord_limit(d.p);
+    int64_t lo[TD_MAX_P], hi[TD_MAX_P];
+    for (int c = 0; c < d.p; ++c) {
+        lo[c] = INT64_MAX;
+        hi[c] = INT64_MIN;
+    }
+    for (int64_t i = 0; i < (int64_t)d.n; ++i)
+        for (int c = 0; c < d.p; ++c) {
+            int64_t v = d.X[i * d.p + c];
+            lo[c] = std::min(lo[c], v);
+            hi[c] = std::max(hi[c], v);
+        }
+    for (int64_t q = 0; q < (int64_t)d.m; ++q)
+        for (int c = 0; c < d.p; ++c) {
+            int64_t z = d.Z[q * d.p + c];
+            if (hi[c] - z > lim || z - lo[c] > lim) return false;
+        }
+    return true;
+}
+
+struct Plan {
+    int nq = 0, nsets = 0, nmax = 1, pmax = 1;
+    size_t x_elems = 0;
+    std::vector<TdSet> sets;
+    std::vector<TdQuery> q;
+    std::vector<int32_t> order;
+};
+
+Plan make_plan(const td_dataset *sets, int k)
+{
+    Plan P;
+    P.nsets = k;
+    std::vector<std::pair<double, int>> cost;
+    for (int s = 0; s < k; ++s) {
+        TdSet t;
+        t.x_off = (int64_t)P.x_elems;
+        t.n = sets[s].n;
+        t.p = sets[s].p;
+        P.sets.push_back(t);
+        P.x_elems += (size_t)t.n * t.p;
+        P.nmax = std::max(P.nmax, t.n);
+        P.pmax = std::max(P.pmax, t.p);
+        double c = 1.0;
+        for (int i = 0; i < t.p - 2; ++i) c *= (double)(t.n - i) / (i + 1);
+        c *= t.n;
+        for (int j = 0; j < sets[s].m; ++j) {
+            TdQuery Q;
+            memset(&Q, 0, sizeof(Q));
+            Q.set = s;
+            cost.push_back({-c, P.nq});
+            P.q.push_back(Q);
+            ++P.nq;
+        }
+    }
+    /* longest work first */
+    std::stable_sort(cost.begin(), cost.end());
+    for (auto &c : cost) P.order.push_back(c.second);
+    return P;
+}
+
+cudaError_t alloc_work(Work &w, const Plan &P, int grid_warps, bool need_x_arena)
+{
+    cudaError_t e;
+    if (need_x_arena && (e = grow(w.X, std::max<size_t>(P.x_elems, 1) * 4)) != cudaSuccess) return e;
+    if ((e = grow(w.Zq, (size_t)std::max(P.nq, 1) * TD_MAXD * 4)) != cudaSuccess) return e;
+    if ((e = grow(w.sets, (size_t)std::max(P.nsets, 1) * sizeof(TdSet))) != cudaSuccess) return e;
+    if ((e = grow(w.q, (size_t)std::max(P.nq, 1) * sizeof(TdQuery))) != cudaSuccess) return e;
+    if ((e = grow(w.order, (size_t)std::max(P.nq, 1) * 4)) != cudaSuccess) return e;
+    if ((e = grow(w.prefix, (size_t)(P.nq + 1) * 8)) != cudaSuccess) return e;
+    if ((e = grow(w.tsize, (size_t)std::max(P.nq, 1) * 4)) != cudaSuccess) return e;
+    if ((e = grow(w.ticket, 64)) != cudaSuccess) return e;
+    if ((e = grow(w.qmin, (size_t)std::max(P.nq, 1) * 4)) != cudaSuccess) return e;
+    if ((e = grow(w.out, (size_t)std::max(P.nq, 1) * 4)) != cudaSuccess) return e;
+    if ((e = grow(w.ctr, sizeof(TdCounters))) != cudaSuccess) return e;
+    size_t sc = (size_t)grid_warps * (size_t)td_scratch_per_warp(P.nmax);
+    if ((e = grow(w.scratch, sc)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+int blog2_for(int nmax, const td_options &o)
+{
+    if (o.buckets_log2 > 0) return std::max(5, std::min(o.buckets_log2, 12));
+    int b = 5;
+    while ((1 << b) < nmax && b < 11) ++b;
+    return b;
+}
+
+/* Pack the host-side inputs into pinned staging and enqueue the copies. */
+int stage_inputs(td_ctx *ctx, Work &w, HostBuf &stage, const Plan &P, const td_dataset *sets, int k,
+                 bool devptr, cudaStream_t s, const int32_t **x_arena)
+{
+    size_t zq_bytes = (size_t)P.nq * TD_MAXD * 4;
+    size_t small = P.nsets * sizeof(TdSet) + P.nq * sizeof(TdQuery) + P.nq * 4;
+    size_t host_bytes = zq_bytes + small + (devptr ? 0 : P.x_elems * 4) + 64;
+    TDCK(grow_host(stage, host_bytes));
+    char *h = (char *)stage.p;
+    /* queries, row stride TD_MAXD */
+    int32_t *hz = (int32_t *)h;
+    memset(hz, 0, zq_bytes);
+    if (!devptr) {
+        int qi = 0;
+        for (int s2 = 0; s2 < k; ++s2)
+            for (int j = 0; j < sets[s2].m; ++j, ++qi)
+                memcpy(hz + (size_t)qi * TD_MAXD, sets[s2].Z + (size_t)j * sets[s2].p, sets[s2].p * 4);
+        TDCK(cudaMemcpyAsync(w.Zq.p, hz, zq_bytes, cudaMemcpyHostToDevice, s));
+    } else {
+        int qi = 0;
+        for (int s2 = 0; s2 < k; ++s2) {
+            if (sets[s2].m > 0)
+                TDCK(cudaMemcpy2DAsync((int32_t *)w.Zq.p + (size_t)qi * TD_MAXD, TD_MAXD * 4, sets[s2].Z,
+                                       sets[s2].p * 4, sets[s2].p * 4, sets[s2].m, cudaMemcpyDeviceToDevice, s));
+            qi += sets[s2].m;
+        }
+    }
+    char *hs = h + zq_bytes;
+    memcpy(hs, P.sets.data(), P.nsets * sizeof(TdSet));
+    memcpy(hs + P.nsets * sizeof(TdSet), P.q.data(), P.nq * sizeof(TdQuery));
+    memcpy(hs + P.nsets * sizeof(TdSet) + P.nq * sizeof(TdQuery), P.order.data(), P.nq * 4);
+    TDCK(cudaMemcpyAsync(w.sets.p, hs, P.nsets * sizeof(TdSet), cudaMemcpyHostToDevice, s));
+    if (P.nq > 0) {
+        TDCK(cudaMemcpyAsync(w.q.p, hs + P.nsets * sizeof(TdSet), P.nq * sizeof(TdQuery), cudaMemcpyHostToDevice, s));
+        TDCK(cudaMemcpyAsync(w.order.p, hs + P.nsets * sizeof(TdSet) + P.nq * sizeof(TdQuery), P.nq * 4,
+                             cudaMemcpyHostToDevice, s));
+    }
+    if (devptr && k == 1) {
+        *x_arena = sets[0].X; /* used in place */
+    } else if (devptr) {
+        for (int s2 = 0; s2 < k; ++s2)
+            TDCK(cudaMemcpyAsync((int32_t *)w.X.p + P.sets[s2].x_off, sets[s2].X,
+                                 (size_t)sets[s2].n * sets[s2].p * 4, cudaMemcpyDeviceToDevice, s));
+        *x_arena = (const int32_t *)w.X.p;
+    } else {
+        int32_t *hx = (int32_t *)(((uintptr_t)(hs + small) + 63) & ~(uintptr_t)63);
+        for (int s2 = 0; s2 < k; ++s2)
+            memcpy(hx + P.sets[s2].x_off, sets[s2].X, (size_t)sets[s2].n * sets[s2].p * 4);
+        TDCK(cudaMemcpyAsync(w.X.p, hx, P.x_elems * 4, cudaMemcpyHostToDevice, s));
+        *x_arena = (const int32_t *)w.X.p;
+    }
+    return TD_OK;
+}
+
+TdLaunch make_launch(const Work &w, const Plan &P, const int32_t *x_arena, const td_options &o, int warps,
+                     int blog2)
+{
+    TdLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.X = x_arena;
+    L.Zq = (const int32_t *)w.Zq.p;
+    L.sets = (const TdSet *)w.sets.p;
+    L.q = (TdQuery *)w.q.p;
+    L.nq = P.nq;
+    L.warps = warps;
+    L.order = (const int32_t *)w.order.p;
+    L.tile_prefix = (int64_t *)w.prefix.p;
+    L.tile_size = (int32_t *)w.tsize.p;
+    L.ticket = (unsigned long long *)w.ticket.p;
+    L.qmin = (int32_t *)w.qmin.p;
+    L.out = (int32_t *)w.out.p;
+    L.ctr = (TdCounters *)w.ctr.p;
+    L.shard_index = o.shard_count > 1 ? o.shard_index : 0;
+    L.shard_count = o.shard_count > 1 ? o.shard_count : 1;
+    L.spw = o.subsets_per_warp;
+    L.blog2 = blog2;
+    L.nmax = P.nmax;
+    L.pmax = P.pmax;
+    L.scratch = (char *)w.scratch.p;
+    L.scratch_per_warp = td_scratch_per_warp(P.nmax);
+    return L;
+}
+
+/* Enqueue the kernels of one call on stream s.  Returns launches issued. */
+int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, const td_options &o, int blog2,
+                    cudaStream_t s, int *launches)
+{
+    int nl = 0;
+    if (o.mode == TD_MODE_PLAIN_EXACT) {
+        TdLaunch L = Lf;
+        L.warps = kWarpsPlain;
+        size_t smem = td_plain_smem(P.nmax, P.pmax, kWarpsPlain);
+        int occ = td_plain_occupancy(kWarpsPlain, smem);
+        if (occ < 1) return TD_ERR_INVALID;
+        int grid = ctx->sms * occ;
+        TDCK(td_launch_setup(L, s));
+        ++nl;
+        for (int q = 0; q < P.nq; ++q) {
+            TDCK(td_launch_plain(L, q, grid, smem, s));
+            ++nl;
+        }
+        TDCK(td_launch_finalize(L, s));
+        ++nl;
+    } else {
+        size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
+        TDCK(td_launch_setup(Lf, s));
+        TDCK(td_launch_tiles(Lf, s));
+        TDCK(td_launch_filtered(Lf, w.grid_filtered, smem, s));
+        TDCK(td_launch_finalize(Lf, s));
+        nl = 4;
+    }
+    *launches = nl;
+    return TD_OK;
+}
+
+int grid_filtered(td_ctx *ctx, const Plan &P, int blog2)
+{
+    size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
+    int occ = td_filtered_occupancy(kWarpsFiltered, smem);
+    return ctx->sms * occ;
+}
+
+/* One synchronous batched call. */
+int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
+{
+    if (!ctx || (!sets && k > 0) || k < 0) return TD_ERR_INVALID;
+    const bool devptr = ctx->opt.device_pointers != 0;
+    for (int s2 = 0; s2 < k; ++s2) {
+        int v = validate_set(sets[s2]);
+        if (v != TD_OK) return v;
+        if (!devptr && !range_ok(sets[s2])) return TD_ERR_RANGE;
+    }
+    if (st) memset(st, 0, sizeof(*st));
+    Plan P = make_plan(sets, k);
+    if (P.nq == 0) return TD_OK;
+    const td_options &o = ctx->opt;
+    cudaStream_t s = stream_of(ctx);
+    const int blog2 = blog2_for(P.nmax, o);
+    int grid = 0, warps_total = 0;
+    (void)cudaGetLastError(); /* clear any stale error of an earlier call */
+    if (o.mode == TD_MODE_PLAIN_EXACT) {
+        size_t smem = td_plain_smem(P.nmax, P.pmax, kWarpsPlain);
+        TDCK(td_prepare_plain(smem));
+        int occ = td_plain_occupancy(kWarpsPlain, smem);
+        if (occ < 1) return TD_ERR_INVALID;
+        grid = ctx->sms * occ;
+        warps_total = grid * kWarpsPlain;
+    } else {
+        size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
+        TDCK(td_prepare_filtered(smem));
+        grid = grid_filtered(ctx, P, blog2);
+        if (grid < 1) return TD_ERR_INVALID;
+        warps_total = grid * kWarpsFiltered;
+    }
+    TDCK(alloc_work(ctx->w, P, warps_total, true));
+    ctx->w.grid_filtered = grid;
+    const int32_t *x_arena = nullptr;
+    int rc = stage_inputs(ctx, ctx->w, ctx->hstage, P, sets, k, devptr, s, &x_arena);
+    if (rc != TD_OK) return rc;
+    TDCK(cudaMemsetAsync(ctx->w.ctr.p, 0, sizeof(TdCounters), s));
+    TdLaunch L = make_launch(ctx->w, P, x_arena, o, kWarpsFiltered, blog2);
+    TDCK(cudaEventRecord(ctx->ev0, s));
+    int launches = 0;
+    if (o.mode == TD_MODE_FILTERED && o.use_graph) {
+        GraphKey key;
+        memset(&key, 0, sizeof(key));
+        key.nq = P.nq;
+        key.nsets = P.nsets;
+        key.nmax = P.nmax;
+        key.pmax = P.pmax;
+        key.grid = grid;
+        key.blog2 = blog2;
+        key.spw = o.subsets_per_warp;
+        key.smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
+        const Work &cw = ctx->w;
+        const void *pp[13] = { x_arena, cw.Zq.p, cw.sets.p, cw.q.p, cw.order.p, cw.prefix.p, cw.tsize.p,
+                               cw.ticket.p, cw.qmin.p, cw.out.p, cw.ctr.p, cw.scratch.p, cw.X.p };
+        memcpy(key.ptrs, pp, sizeof(pp));
+        key.shard_index = L.shard_index;
+        key.shard_count = L.shard_count;
+        if (!ctx->gvalid || !(key == ctx->gkey)) {
+            if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+            ctx->gvalid = false;
+            cudaStream_t cs = nullptr;
+            TDCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                cudaStreamDestroy(cs);
+                return fail_cuda(ctx, e, "cudaStreamBeginCapture");
+            }
+            int nl = 0;
+            int rc2 = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, cs, &nl);
+            e = cudaStreamEndCapture(cs, &g);
+            cudaStreamDestroy(cs);
+            if (rc2 != TD_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc2;
+            }
+            if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaGraphInstantiate");
+            ctx->gkey = key;
+            ctx->gvalid = true;
+        }
+        TDCK(cudaGraphLaunch(ctx->gexec, s));
+        launches = 4;
+    } else {
+        rc = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, s, &launches);
+        if (rc != TD_OK) return rc;
+    }
+    TDCK(cudaEventRecord(ctx->ev1, s));
+    /* check the device-side error counter before any output is written */
+    TdCounters C;
+    TDCK(cudaMemcpyAsync(&C, ctx->w.ctr.p, sizeof(C), cudaMemcpyDeviceToHost, s));
+    TDCK(cudaStreamSynchronize(s));
+    if (C.errors != 0) return TD_ERR_INTERNAL;
+    /* range check for device pointers: the set-up kernel's maxima */
+    if (devptr) {
+        std::vector<TdQuery> hq(P.nq);
+        TDCK(cudaMemcpy(hq.data(), ctx->w.q.p, P.nq * sizeof(TdQuery), cudaMemcpyDeviceToHost));
+        for (int qi = 0; qi < P.nq; ++qi) {
+            int64_t lim = td_coord_limit(P.sets[hq[qi].set].p);
+            for (int c = 0; c < TD_MAXD; ++c)
+                if (hq[qi].mx[c] > lim) return TD_ERR_RANGE;
+        }
+    }
+    if (devptr) {
+        int qi = 0;
+        for (int s2 = 0; s2 < k; ++s2) {
+            if (sets[s2].m > 0)
+                TDCK(cudaMemcpyAsync(sets[s2].out, (int32_t *)ctx->w.out.p + qi, sets[s2].m * 4,
+                                     cudaMemcpyDeviceToDevice, s));
+            qi += sets[s2].m;
+        }
+        TDCK(cudaStreamSynchronize(s));
+    } else {
+        TDCK(grow_host(ctx->hout, (size_t)P.nq * 4));
+        TDCK(cudaMemcpyAsync(ctx->hout.p, ctx->w.out.p, (size_t)P.nq * 4, cudaMemcpyDeviceToHost, s));
+        TDCK(cudaStreamSynchronize(s));
+        int qi = 0;
+        for (int s2 = 0; s2 < k; ++s2) {
+            memcpy(sets[s2].out, (int32_t *)ctx->hout.p + qi, (size_t)sets[s2].m * 4);
+            qi += sets[s2].m;
+        }
+    }
+    if (st) {
+        st->sweeps = C.sweeps;
+        st->skipped_dependent = C.dependent;
+        st->filtered_points = C.filtered_points;
+        st->exact_points = C.exact_points;
+        st->tight_exceptions = C.tight;
+        st->resolved_buckets = C.resolved;
+        st->kernel_launches = (uint64_t)launches;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        st->ms = ms;
+    }
+    return TD_OK;
+}
+
+}  // namespace
+
+/* ======================================================================= */
+/* exported entry points                                                    */
+/* ======================================================================= */
+
+extern "C" int64_t td_coord_limit(int32_t p)
+{
+    switch (p) {
+    case 1:
+    case 2:
+    case 3: return 16777215; /* 2^24 - 1: coordinates exact in binary32 */
+    case 4: return 524287;   /* 4 * 2 M^2 * M < 2^62 */
+    case 5: return 16383;    /* 5 * 3^(3/2) M^3 * M < 2^62 */
+    case 6: return 2047;     /* 6 * (2M)^4 * M < 2^62 */
+    default: return 0;
+    }
+}
+
+extern "C" const char *td_strerror(int code)
+{
+    switch (code) {
+    case TD_OK: return "ok";
+    case TD_ERR_INVALID: return "invalid argument";
+    case TD_ERR_RANGE: return "coordinates exceed the exact-arithmetic limit";
+    case TD_ERR_OOM: return "out of memory";
+    case TD_ERR_BUSY: return "stream admission refused (memory budget)";
+    case TD_ERR_TIMEOUT: return "timed out";
+    case TD_ERR_CUDA: return "CUDA error";
+    case TD_ERR_NOTFOUND: return "unknown ticket";
+    case TD_ERR_INTERNAL: return "device-side consistency check failed";
+    default: return "unknown error";
+    }
+}
+
+extern "C" const char *td_last_cuda_error(td_ctx *ctx) { return ctx ? ctx->cuda_err.c_str() : ""; }
+
+extern "C" int td_create(td_ctx **out, int device, const td_options *opt)
+{
+    if (!out) return TD_ERR_INVALID;
+    *out = nullptr;
+    td_ctx *ctx = new (std::nothrow) td_ctx();
+    if (!ctx) return TD_ERR_OOM;
+    ctx->device = device;
+    ctx->opt = opt ? *opt : default_options();
+    if (ctx->opt.shard_count < 1) ctx->opt.shard_count = 1;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e != cudaSuccess) {
+        int rc = fail_cuda(ctx, e, "td_create");
+        td_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return TD_OK;
+}
+
+extern "C" int td_set_options(td_ctx *ctx, const td_options *opt)
+{
+    if (!ctx || !opt) return TD_ERR_INVALID;
+    if (opt->mode != TD_MODE_FILTERED && opt->mode != TD_MODE_PLAIN_EXACT) return TD_ERR_INVALID;
+    if (opt->shard_count > 1 && (opt->shard_index < 0 || opt->shard_index >= opt->shard_count)) return TD_ERR_INVALID;
+    ctx->opt = *opt;
+    if (ctx->opt.shard_count < 1) ctx->opt.shard_count = 1;
+    ctx->gvalid = false;
+    return TD_OK;
+}
+
+extern "C" int td_destroy(td_ctx *ctx)
+{
+    if (!ctx) return TD_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    if (ctx->own) cudaStreamSynchronize(ctx->own);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    Work &w = ctx->w;
+    DevBuf *bufs[] = { &w.X, &w.Zq, &w.sets, &w.q, &w.order, &w.prefix, &w.tsize, &w.ticket, &w.qmin, &w.out, &w.ctr, &w.scratch };
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (ctx->hstage.p) cudaFreeHost(ctx->hstage.p);
+    if (ctx->hout.p) cudaFreeHost(ctx->hout.p);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own) cudaStreamDestroy(ctx->own);
+    delete ctx;
+    return TD_OK;
+}
+
+extern "C" int td_depth(td_ctx *ctx, const int32_t *X, int32_t n, int32_t p, const int32_t *Z, int32_t m,
+                        int32_t *out, td_stats *st)
+{
+    if (!ctx) return TD_ERR_INVALID;
+    td_dataset d;
+    d.n = n;
+    d.p = p;
+    d.X = X;
+    d.m = m;
+    d.Z = Z;
+    d.out = out;
+    cudaSetDevice(ctx->device);
+    return run_batch(ctx, &d, 1, st);
+}
+
+extern "C" int td_depth_batched(td_ctx *ctx, const td_dataset *sets, int32_t k, td_stats *st)
+{
+    if (!ctx) return TD_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    return run_batch(ctx, sets, k, st);
+}
+
+/* ----------------------------------------------------------------------- */
+/* stream API                                                               */
+/* ----------------------------------------------------------------------- */
+
+namespace {
+
+size_t request_bytes(const Plan &P)
+{
+    return P.x_elems * 4 + (size_t)P.nq * (TD_MAXD * 4 + sizeof(TdQuery) + 4 + 8 + 4 + 4 + 4) + 4096;
+}
+
+void free_req(td_stream_req *r)
+{
+    Work &w = r->w;
+    DevBuf *bufs[] = { &w.X, &w.Zq, &w.sets, &w.q, &w.order, &w.prefix, &w.tsize, &w.ticket, &w.qmin, &w.out, &w.ctr };
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (r->hin.p) cudaFreeHost(r->hin.p);
+    if (r->hout.p) cudaFreeHost(r->hout.p);
+    if (r->done) cudaEventDestroy(r->done);
+    delete r;
+}
+
+/* finish a request whose event completed: copy outputs to the user buffer */
+int complete_req(td_stream *s, td_stream_req *r)
+{
+    if (r->finished) return r->status;
+    int32_t *h = (int32_t *)r->hout.p;
+    TdCounters *c = (TdCounters *)(h + r->m);
+    if (c->errors != 0) {
+        r->status = TD_ERR_INTERNAL;
+    } else {
+        memcpy(r->user_out, h, (size_t)r->m * 4);
+        r->status = TD_OK;
+    }
+    r->finished = true;
+    s->inflight -= r->bytes;
+    return r->status;
+}
+
+}  // namespace
+
+extern "C" int td_stream_create(td_ctx *ctx, size_t mem_budget_bytes, td_stream **out)
+{
+    if (!ctx || !out) return TD_ERR_INVALID;
+    *out = nullptr;
+    td_stream *s = new (std::nothrow) td_stream();
+    if (!s) return TD_ERR_OOM;
+    s->ctx = ctx;
+    s->budget = mem_budget_bytes;
+    s->inflight = 0;
+    s->next = 1;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete s;
+        return fail_cuda(ctx, e, "td_stream_create");
+    }
+    *out = s;
+    return TD_OK;
+}
+
+extern "C" int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *ticket)
+{
+    if (!s || !d || !ticket) return TD_ERR_INVALID;
+    td_ctx *ctx = s->ctx;
+    if (ctx->opt.device_pointers) return TD_ERR_INVALID; /* the stream takes host inputs */
+    int v = validate_set(*d);
+    if (v != TD_OK) return v;
+    if (!range_ok(*d)) return TD_ERR_RANGE;
+    cudaSetDevice(ctx->device);
+    /* reap finished requests first (frees budget) */
+    for (td_stream_req *r : s->reqs)
+        if (!r->finished && cudaEventQuery(r->done) == cudaSuccess) complete_req(s, r);
+    Plan P = make_plan(d, 1);
+    size_t bytes = request_bytes(P);
+    if (s->inflight + bytes > s->budget) return TD_ERR_BUSY;
+    td_stream_req *r = new (std::nothrow) td_stream_req();
+    if (!r) return TD_ERR_OOM;
+    r->ticket = s->next;
+    r->user_out = d->out;
+    r->m = d->m;
+    r->bytes = bytes;
+    r->finished = false;
+    r->status = TD_OK;
+    r->done = nullptr;
+    td_options o = ctx->opt;
+    o.mode = TD_MODE_FILTERED;
+    o.device_pointers = 0;
+    const int blog2 = blog2_for(P.nmax, o);
+    int grid = 0;
+    (void)cudaGetLastError();
+    if (P.nq > 0) {
+        grid = grid_filtered(ctx, P, blog2);
+        if (grid < 1) {
+            delete r;
+            return TD_ERR_INVALID;
+        }
+    }
+    cudaError_t e = alloc_work(r->w, P, 0, true);
+    if (e == cudaSuccess) {
+        size_t sc = (size_t)grid * kWarpsFiltered * (size_t)td_scratch_per_warp(TD_MAX_N);
+        e = grow(s->scratch, sc);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = grow_host(r->hout, (size_t)P.nq * 4 + sizeof(TdCounters) + 64);
+    if (e != cudaSuccess) {
+        free_req(r);
+        return fail_cuda(ctx, e, "td_stream_submit");
+    }
+    r->w.grid_filtered = grid;
+    const int32_t *x_arena = nullptr;
+    int rc = TD_OK;
+    if (P.nq > 0) {
+        rc = stage_inputs(ctx, r->w, r->hin, P, d, 1, false, s->s, &x_arena);
+        if (rc == TD_OK) {
+            TdLaunch L = make_launch(r->w, P, x_arena, o, kWarpsFiltered, blog2);
+            L.scratch = (char *)s->scratch.p;
+            L.scratch_per_warp = td_scratch_per_warp(TD_MAX_N);
+            /* scratch sized for TD_MAX_N points per warp */
+            L.nmax = P.nmax;
+            e = cudaMemsetAsync(r->w.ctr.p, 0, sizeof(TdCounters), s->s);
+            if (e == cudaSuccess) {
+                int nl = 0;
+                TdLaunch L2 = L;
+                rc = enqueue_kernels(ctx, r->w, P, L2, o, blog2, s->s, &nl);
+            } else {
+                rc = fail_cuda(ctx, e, "cudaMemsetAsync");
+            }
+            if (rc == TD_OK) {
+                e = cudaMemcpyAsync(r->hout.p, r->w.out.p, (size_t)P.nq * 4, cudaMemcpyDeviceToHost, s->s);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync((int32_t *)r->hout.p + P.nq, r->w.ctr.p, sizeof(TdCounters),
+                                        cudaMemcpyDeviceToHost, s->s);
+                if (e != cudaSuccess) rc = fail_cuda(ctx, e, "cudaMemcpyAsync");
+            }
+        }
+    } else {
+        memset(r->hout.p, 0, sizeof(TdCounters) + 64);
+    }
+    if (rc == TD_OK) {
+        e = cudaEventRecord(r->done, s->s);
+        if (e != cudaSuccess) rc = fail_cuda(ctx, e, "cudaEventRecord");
+    }
+    /* the host inputs were copied into the request's pinned buffer by
+     * stage_inputs, so the caller may reuse them as soon as this returns */
+    if (rc != TD_OK) {
+        cudaStreamSynchronize(s->s);
+        free_req(r);
+        return rc;
+    }
+    s->inflight += bytes;
+    s->next++;
+    s->reqs.push_back(r);
+    *ticket = r->ticket;
+    return TD_OK;
+}
+
+extern "C" int td_stream_poll(td_stream *s, uint64_t ticket, int *done)
+{
+    if (!s || !done) return TD_ERR_INVALID;
+    for (td_stream_req *r : s->reqs) {
+        if (r->ticket != ticket) continue;
+        if (r->finished) {
+            *done = 1;
+            return r->status;
+        }
+        cudaError_t e = cudaEventQuery(r->done);
+        if (e == cudaSuccess) {
+            *done = 1;
+            return complete_req(s, r);
+        }
+        if (e != cudaErrorNotReady) return fail_cuda(s->ctx, e, "cudaEventQuery");
+        *done = 0;
+        return TD_OK;
+    }
+    return TD_ERR_NOTFOUND;
+}
+
+extern "C" int td_stream_wait(td_stream *s, uint64_t ticket, int64_t timeout_us)
+{
+    if (!s) return TD_ERR_INVALID;
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        int done = 0;
+        int rc = td_stream_poll(s, ticket, &done);
+        if (rc != TD_OK || done) return rc;
+        if (timeout_us >= 0) {
+            auto el = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (el >= timeout_us) return TD_ERR_TIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+extern "C" int td_stream_destroy(td_stream *s)
+{
+    if (!s) return TD_ERR_INVALID;
+    cudaSetDevice(s->ctx->device);
+    cudaStreamSynchronize(s->s);
+    for (td_stream_req *r : s->reqs) free_req(r);
+    if (s->scratch.p) cudaFree(s->scratch.p);
+    cudaStreamDestroy(s->s);
+    delete s;
+    return TD_OK;
+}

@@ -1,0 +1,61 @@
+/*
+ * td_internal.h -- structures shared by the host side and the kernels of
+ * libtukeydepth.so (not part of the public ABI).
+ */
+#pragma once
+#include <stdint.h>
+
+#define TD_MAXD 6
+
+/* Per-query state written by the set-up kernel (one per query). */
+struct TdQuery {
+    int32_t set;           /* dataset index */
+    int32_t n;             /* data points of the dataset */
+    int32_t nnz;           /* centred points x_i = X_i - z that are nonzero */
+    int32_t Z;             /* centred points equal to zero (counted by every closed halfspace) */
+    int32_t d;             /* rank of the nonzero centred points (effective dimension) */
+    int32_t k;             /* subset size d - 2 of Algorithm 1, or -1 when there is no subset loop */
+    int32_t direct;        /* final count when there is no subset loop (nnz == 0 or d <= 1), else -1 */
+    int32_t pad;
+    int32_t piv[TD_MAXD];  /* coordinates on which the span of the points projects injectively */
+    int32_t mx[TD_MAXD];   /* max |x_i| per projected coordinate (FP32 error bounds) */
+    int64_t nsub;          /* subset positions C(nnz, k) of the whole loop */
+    int64_t lo, hi;        /* subset positions [lo, hi) handled by this call (shard) */
+};
+
+/* One dataset inside the device arenas. */
+struct TdSet {
+    int64_t x_off;  /* offset of X (n x p int32) in the data arena, in int32 elements */
+    int32_t n, p;
+};
+
+/* Statistics counters accumulated on the device. */
+struct TdCounters {
+    unsigned long long sweeps, dependent, filtered_points, exact_points, tight, resolved;
+    unsigned long long errors;  /* device-side consistency failures (must stay 0) */
+    unsigned long long pad;
+};
+
+/* Parameters of the work-queue launches. */
+struct TdLaunch {
+    const int32_t *X;        /* data arena */
+    const int32_t *Zq;       /* query points, m_total x p_q (row stride TD_MAXD) */
+    const TdSet *sets;
+    TdQuery *q;              /* per query */
+    int32_t nq;              /* number of queries */
+    int32_t warps;           /* warps per CTA */
+    const int32_t *order;    /* work order of the queries (a permutation of [0, nq)) */
+    int64_t *tile_prefix;    /* nq + 1 prefix sums of tiles, in work order */
+    int32_t *tile_size;      /* subsets per tile, per query */
+    unsigned long long *ticket;  /* work-queue counter */
+    int32_t *qmin;           /* per-query minimum of V(S) over the processed subsets */
+    int32_t *out;            /* per-query output */
+    TdCounters *ctr;
+    int64_t shard_index, shard_count;
+    int32_t spw;             /* subsets per warp per tile (0 = by size) */
+    int32_t blog2;           /* angular buckets log2 (0 = by size) */
+    int32_t nmax;            /* largest nnz over the queries (smem sizing) */
+    int32_t pmax;            /* largest p over the datasets */
+    char *scratch;           /* per-warp global scratch for the exact tight-set path */
+    int64_t scratch_per_warp;
+};

@@ -1,0 +1,1525 @@
+/*
+ * td_kernels.cu -- the sweep kernels of libtukeydepth.so (sm_103a).
+ *
+ * Work: for every query z, the minimum over the subsets S of K = d-2 nonzero
+ * centred points of V(S) = G(S) + m_S (Algorithm 1, Section 3, with the tie
+ * readings of the library header), where
+ *   G(S)  = min over generic directions v of the quotient of #{ y_i : v.y_i < 0 }
+ *           for the projected points y_i = (f_a(x_i), f_b(x_i)) that are nonzero
+ *           (Algorithm 2, Section 3), and
+ *   m_S   = the open depth of the points of span(S) inside span(S) (0 unless
+ *           the span holds more data points than S).
+ * T(z) = Z + min_S V(S), Z = number of x_i = 0.
+ *
+ * Kernels (one CUDA stream, in this order):
+ *   td_k_setup      one CTA per query: centring, Z, rank and pivot
+ *                   coordinates (exact), per-coordinate maxima, subset count
+ *   td_k_tiles      one CTA: tiles per query and their prefix sums
+ *   td_k_filtered   persistent CTAs popping (query, subset-tile) work from a
+ *                   counter; one warp per subset sweep; FP32 projection with
+ *                   a forward error bound, angular bucket histogram in shared
+ *                   memory, exact int64/__int128 fallback
+ *   td_k_plain      the plain exact form: one launch per query, exact int64
+ *                   projections, comparison sort with an exact comparator
+ *   td_k_finalize   out[q] = Z + min
+ *
+ * The bivariate walk.  Parametrise the boundary line of the halfplane by its
+ * direction angle phi in [0, pi).  A nonzero y with line direction psi in
+ * [0, pi) lies on the counted (left) side for phi just below psi iff y points
+ * into the upper half plane (y2 > 0, or y2 = 0 and y1 > 0; "orientation +"),
+ * and changes side at phi = psi.  Hence, starting from A = #{orientation +}
+ * (the count just below phi = 0), the count at every generic direction is A
+ * plus the running sum of -1 (orientation +) / +1 (orientation -) events in
+ * increasing psi, read only between groups of equal psi (reading of
+ * Algorithm 2 step 1(e) under ties); the opposite direction has the
+ * complementary count.  So G = min over those walk values w of min(w, m - w),
+ * m the number of nonzero projected points.  This is Algorithm 2's sweep
+ * (steps 1(c)-1(e)) with the start direction u0 = (0,-1) and its slopes
+ * replaced by exact line directions.
+ *
+ * The filtered kernel never sorts.  Directions are binned by a pseudo-angle
+ * key in [0,2) into B angular buckets whose boundaries are exact integer
+ * directions D_j; a point whose FP32 key is not certified to lie inside one
+ * bucket is placed exactly by integer cross products with D_j and D_{j+1}.
+ * Per bucket only the counts of +1 and -1 events are kept (one shared-memory
+ * atomic per point); the walk value at every bucket boundary is then exact,
+ * and inside a bucket whose events all have one sign the extremes are at the
+ * boundaries.  Only buckets holding both signs whose in-bucket range could
+ * pass the extremes seen at the boundaries are resolved, by gathering their
+ * events and ordering them exactly.  The result is the exact G.
+ */
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <limits.h>
+
+#include "td_internal.h"
+#include "td_exact.cuh"
+
+#define TD_WARPS_MAX 8
+#define TD_SENT 0xFFFFu
+
+/* unit roundoff of binary32 */
+#define TD_U (1.0f / 16777216.0f)
+
+/* ====================================================================== */
+/* per-warp global scratch for the exact tight-set path                    */
+/* ====================================================================== */
+
+struct TdScratch {
+    int32_t *c0;  /* level-0 intrinsic coordinates [NP][4] */
+    int64_t *y0;  /* level-0 normalised projections [NP][2] */
+    uint16_t *i0; /* level-0 sort list [NP] */
+    int32_t *c1;  /* level-1 coordinates [NP][4] */
+    int64_t *y1;  /* level-1 projections [NP][2] */
+    uint16_t *i1; /* level-1 sort list [NP] */
+};
+
+__host__ __device__ inline int64_t td_scratch_bytes(int np)
+{
+    return (int64_t)np * (16 + 16 + 2 + 16 + 16 + 2) + 256;
+}
+
+__device__ inline TdScratch td_scratch_at(char *base, int np)
+{
+    TdScratch s;
+    char *p = base;
+    s.c0 = (int32_t *)p; p += (size_t)np * 16;
+    s.y0 = (int64_t *)p; p += (size_t)np * 16;
+    s.c1 = (int32_t *)p; p += (size_t)np * 16;
+    s.y1 = (int64_t *)p; p += (size_t)np * 16;
+    s.i0 = (uint16_t *)p; p += (size_t)np * 2;
+    s.i1 = (uint16_t *)p;
+    return s;
+}
+
+__host__ __device__ inline int td_pow2_at_least(int v)
+{
+    int p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+/* ====================================================================== */
+/* exact sort + walk on a list of normalised projections                   */
+/* ====================================================================== */
+
+/* Item ids carry the orientation in bit 15 (set = orientation +). */
+__device__ __forceinline__ bool td_item_less(uint16_t u, uint16_t v, const int64_t *H)
+{
+    if (u == TD_SENT) return false;
+    if (v == TD_SENT) return true;
+    int a = u & 0x7FFF, b = v & 0x7FFF;
+    return td_cross_sign(H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) > 0;
+}
+
+/* Bitonic sort of idx[0..npad) (npad a power of two >= 32; entries beyond the
+ * valid ones are TD_SENT) by increasing line direction, one warp. */
+__device__ void td_sort_exact(uint16_t *idx, int npad, const int64_t *H, int lane)
+{
+    for (int size = 2; size <= npad; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < (npad >> 1); t += 32) {
+                int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
+                int j = i + stride;
+                bool up = (i & size) == 0;
+                uint16_t u = idx[i], v = idx[j];
+                bool swap = up ? td_item_less(v, u, H) : td_item_less(u, v, H);
+                if (swap) {
+                    idx[i] = v;
+                    idx[j] = u;
+                }
+            }
+            __syncwarp();
+        }
+}
+
+/* Walk over the cnt sorted items: returns min over walk values w of
+ * min(w, m - w) where the walk starts at A (orientation + count) and m = cnt. */
+__device__ int td_walk_sorted(const uint16_t *idx, int cnt, const int64_t *H, int lane)
+{
+    int A = 0;
+    for (int l = lane; l < cnt; l += 32) A += (idx[l] >> 15) & 1;
+    A = td_wsum(A);
+    int C = (cnt + 31) >> 5;
+    int beg = min(lane * C, cnt), end = min(beg + C, cnt);
+    int s = 0;
+    for (int l = beg; l < end; ++l) s += (idx[l] & 0x8000) ? -1 : 1;
+    int excl = td_wscan_incl(s, lane) - s;
+    int v = A + excl;
+    int mn = A, mx = A;
+    for (int l = beg; l < end; ++l) {
+        uint16_t it = idx[l];
+        v += (it & 0x8000) ? -1 : 1;
+        bool tie = false;
+        if (l + 1 < cnt) {
+            int a = it & 0x7FFF, b = idx[l + 1] & 0x7FFF;
+            tie = td_cross_sign(H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) == 0;
+        }
+        if (!tie) {
+            mn = min(mn, v);
+            mx = max(mx, v);
+        }
+    }
+    mn = td_wmin(mn);
+    mx = td_wmax(mx);
+    return min(mn, cnt - mx);
+}
+
+/* Given normalised projections H[0..cnt) (all nonzero) and orientations,
+ * build the item list in idx, sort and walk.  plus(i) from bit list. */
+__device__ int td_sweep_list(uint16_t *idx, int cnt, const int64_t *H, int lane)
+{
+    int npad = td_pow2_at_least(cnt);
+    for (int l = cnt + lane; l < npad; l += 32) idx[l] = TD_SENT;
+    __syncwarp();
+    td_sort_exact(idx, npad, H, lane);
+    return td_walk_sorted(idx, cnt, H, lane);
+}
+
+/* ====================================================================== */
+/* open depth of a small full-rank point set (the tight-set path)         */
+/* ====================================================================== */
+
+/* K x K determinant by cofactor expansion (K <= 4, small entries). */
+template <int N>
+__device__ int64_t td_detn(const int64_t (&m)[4][4])
+{
+    if constexpr (N == 1) {
+        return m[0][0];
+    } else {
+        int64_t acc = 0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            int64_t sub[4][4];
+#pragma unroll
+            for (int r = 1; r < N; ++r) {
+                int o = 0;
+#pragma unroll
+                for (int cc = 0; cc < N; ++cc)
+                    if (cc != c) sub[r - 1][o++] = m[r][cc];
+            }
+            int64_t t = m[0][c] * td_detn<N - 1>(sub);
+            acc += (c & 1) ? -t : t;
+        }
+        return acc;
+    }
+}
+
+template <int KK>
+__device__ int td_open_depth(const int32_t *c, int t, const TdScratch &scr, int lane, int level);
+
+/* 2-D open depth of t nonzero integer points (coordinates 0,1 of c). */
+__device__ int td_open_depth2(const int32_t *c, int t, int64_t *Y, uint16_t *I, int lane)
+{
+    for (int i = lane; i < t; i += 32) {
+        int64_t h1, h2;
+        bool plus = td_normalise(c[4 * i], c[4 * i + 1], h1, h2);
+        Y[2 * i] = h1;
+        Y[2 * i + 1] = h2;
+        I[i] = (uint16_t)(i | (plus ? 0x8000 : 0));
+    }
+    __syncwarp();
+    return td_sweep_list(I, t, Y, lane);
+}
+
+/* Projections of the t points of c (dimension DD) onto the quotient by the
+ * subset s (DD-2 points of c); writes nonzero normalised ones to Y/I, and the
+ * tight ones' intrinsic coordinates to ct (if DD-2 >= 2) or their sign counts.
+ * Returns false if the subset is dependent. */
+template <int DD>
+__device__ bool td_project_small(const int32_t *c, int t, const int *sub, int64_t *Y, uint16_t *I,
+                                 int32_t *ct, int &nz, int &nt, int &pos, int &neg, int lane)
+{
+    constexpr int K = DD - 2;
+    int64_t s[K > 0 ? K : 1][DD];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int r = 0; r < DD; ++r) s[j][r] = c[4 * sub[j] + r];
+    TdBasis<DD> B;
+    if (!td_make_basis<DD>(s, B)) return false;
+    int *cnt = (int *)nullptr;
+    (void)cnt;
+    /* lane-parallel projection with warp compaction (stable by ballot) */
+    int base_nz = 0, base_t = 0;
+    pos = 0;
+    neg = 0;
+    for (int i0 = 0; i0 < t; i0 += 32) {
+        int i = i0 + lane;
+        int64_t y1 = 0, y2 = 0;
+        bool valid = i < t;
+        if (valid) {
+#pragma unroll
+            for (int r = 0; r < DD; ++r) {
+                int64_t x = c[4 * i + r];
+                y1 += B.qa[r] * x;
+                y2 += B.qb[r] * x;
+            }
+        }
+        bool tight = valid && y1 == 0 && y2 == 0;
+        bool nonz = valid && !tight;
+        unsigned bn = __ballot_sync(TD_FULL, nonz), bt = __ballot_sync(TD_FULL, tight);
+        unsigned below = (1u << lane) - 1u;
+        if (nonz) {
+            int slot = base_nz + __popc(bn & below);
+            int64_t h1, h2;
+            bool plus = td_normalise(y1, y2, h1, h2);
+            Y[2 * slot] = h1;
+            Y[2 * slot + 1] = h2;
+            I[slot] = (uint16_t)(slot | (plus ? 0x8000 : 0));
+        }
+        if (tight) {
+            if (K == 1) {
+                int32_t v = c[4 * i + B.rows[0]];
+                pos += v > 0;
+                neg += v < 0;
+            } else {
+                int slot = base_t + __popc(bt & below);
+#pragma unroll
+                for (int r = 0; r < K; ++r) ct[4 * slot + r] = c[4 * i + B.rows[r]];
+            }
+        }
+        base_nz += __popc(bn);
+        base_t += __popc(bt);
+    }
+    pos = td_wsum(pos);
+    neg = td_wsum(neg);
+    nz = base_nz;
+    nt = base_t;
+    __syncwarp();
+    return true;
+}
+
+template <int KK>
+__device__ int td_open_depth(const int32_t *c, int t, const TdScratch &scr, int lane, int level)
+{
+    if constexpr (KK == 1) {
+        int pos = 0, neg = 0;
+        for (int i = lane; i < t; i += 32) {
+            pos += c[4 * i] > 0;
+            neg += c[4 * i] < 0;
+        }
+        pos = td_wsum(pos);
+        neg = td_wsum(neg);
+        return min(pos, neg);
+    } else if constexpr (KK == 2) {
+        return td_open_depth2(c, t, level == 0 ? scr.y0 : scr.y1, level == 0 ? scr.i0 : scr.i1, lane);
+    } else if constexpr (KK == 3) {
+        /* subsets of one point; inner tight sets are 1-D (sign counts) */
+        int best = INT_MAX;
+        for (int s0 = 0; s0 < t; ++s0) {
+            int sub[1] = { s0 };
+            int nz, nt, pos, neg;
+            if (!td_project_small<3>(c, t, sub, scr.y0, scr.i0, nullptr, nz, nt, pos, neg, lane)) continue;
+            int G = td_sweep_list(scr.i0, nz, scr.y0, lane);
+            best = min(best, G + min(pos, neg));
+        }
+        return best;
+    } else {
+        /* subsets of two points; inner tight sets are 2-D */
+        int best = INT_MAX;
+        for (int s1 = 1; s1 < t; ++s1)
+            for (int s0 = 0; s0 < s1; ++s0) {
+                int sub[2] = { s0, s1 };
+                int nz, nt, pos, neg;
+                if (!td_project_small<4>(c, t, sub, scr.y0, scr.i0, scr.c1, nz, nt, pos, neg, lane)) continue;
+                int G = td_sweep_list(scr.i0, nz, scr.y0, lane);
+                if (G >= best) continue;
+                int m = (nt > 2) ? td_open_depth2(scr.c1, nt, scr.y1, scr.i1, lane) : 0;
+                best = min(best, G + m);
+            }
+        return best;
+    }
+}
+
+/* m_S for a subset whose span holds t > K data points: the tight points'
+ * intrinsic coordinates are in scr.c0[0..t) and the subset's own points are
+ * sint[0..K).  A quick test first: if the functional w(x) = sum_j
+ * det(S with column j replaced by x) (w(s_j) = det S for every j) has the
+ * sign of det S on every tight point, the tight set lies in an open
+ * halfspace of span(S) and m_S = 0.  Otherwise the open depth is computed
+ * by the same subset method one level down. */
+template <int K>
+__device__ int td_tight_depth(int t, const int64_t (&sint)[4][4], const TdScratch &scr, int lane)
+{
+    if constexpr (K <= 1) {
+        return 0; /* handled by the caller with sign counts */
+    } else {
+        int64_t M[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) M[r][j] = (r < K && j < K) ? sint[j][r] : 0;
+        int64_t det = td_detn<K>(M);
+        int64_t cw[4] = { 0, 0, 0, 0 };
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                int64_t Mr[4][4];
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) Mr[rr][jj] = M[rr][jj];
+#pragma unroll
+                for (int rr = 0; rr < K; ++rr) Mr[rr][j] = (rr == r) ? 1 : 0;
+                cw[r] += td_detn<K>(Mr);
+            }
+        }
+        bool ok = true;
+        for (int i = lane; i < t; i += 32) {
+            int64_t w = 0;
+#pragma unroll
+            for (int r = 0; r < K; ++r) w += cw[r] * (int64_t)scr.c0[4 * i + r];
+            ok &= (det > 0) ? (w > 0) : (w < 0);
+        }
+        if (__all_sync(TD_FULL, ok)) return 0;
+        return td_open_depth<K>(scr.c0, t, scr, lane, 0);
+    }
+}
+
+/* ====================================================================== */
+/* set-up kernel                                                           */
+/* ====================================================================== */
+
+__device__ inline td_i128 td_i128_abs(td_i128 v) { return v < 0 ? -v : v; }
+
+__device__ inline td_i128 td_i128_gcd(td_i128 a, td_i128 b)
+{
+    a = td_i128_abs(a);
+    b = td_i128_abs(b);
+    while (b != 0) {
+        td_i128 r = a % b;
+        a = b;
+        b = r;
+    }
+    return a;
+}
+
+__global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
+{
+    const int q = blockIdx.x;
+    __shared__ int s_z[TD_MAXD];
+    __shared__ int s_Z, s_max[TD_MAXD], s_pos, s_neg;
+    __shared__ int s_d, s_piv[TD_MAXD];
+    TdQuery *Q = &L.q[q];
+    const int set = Q->set;
+    const TdSet S = L.sets[set];
+    const int n = S.n, p = S.p;
+    const int32_t *X = L.X + S.x_off;
+    if (threadIdx.x < TD_MAXD) {
+        s_z[threadIdx.x] = threadIdx.x < p ? L.Zq[(int64_t)q * TD_MAXD + threadIdx.x] : 0;
+        s_max[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) {
+        s_Z = 0;
+        s_pos = 0;
+        s_neg = 0;
+    }
+    __syncthreads();
+    int zc = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        bool zero = true;
+        for (int c = 0; c < p; ++c) zero &= (X[(int64_t)i * p + c] == s_z[c]);
+        zc += zero;
+    }
+    atomicAdd(&s_Z, zc);
+    /* rank and pivot coordinates, exact: incremental elimination over the
+     * nonzero points with primitive (gcd-normalised) basis rows. */
+    if (threadIdx.x == 0) {
+        td_i128 basis[TD_MAXD][TD_MAXD];
+        int pc[TD_MAXD];
+        int r = 0;
+        for (int i = 0; i < n && r < p; ++i) {
+            td_i128 v[TD_MAXD];
+            bool nz = false;
+            for (int c = 0; c < p; ++c) {
+                v[c] = (td_i128)((int64_t)X[(int64_t)i * p + c] - s_z[c]);
+                nz |= v[c] != 0;
+            }
+            if (!nz) continue;
+            for (int b = 0; b < r; ++b) {
+                td_i128 f = v[pc[b]];
+                if (f == 0) continue;
+                td_i128 e = basis[b][pc[b]];
+                bool big = false;
+                for (int c = 0; c < p; ++c) {
+                    v[c] = e * v[c] - f * basis[b][c];
+                    big |= td_i128_abs(v[c]) > ((td_i128)1 << 60);
+                }
+                if (big) {
+                    td_i128 g = 0;
+                    for (int c = 0; c < p; ++c) g = td_i128_gcd(g, v[c]);
+                    if (g > 1)
+                        for (int c = 0; c < p; ++c) v[c] /= g;
+                }
+            }
+            int lead = -1;
+            for (int c = 0; c < p; ++c)
+                if (v[c] != 0) { lead = c; break; }
+            if (lead < 0) continue;
+            td_i128 g = 0;
+            for (int c = 0; c < p; ++c) g = td_i128_gcd(g, v[c]);
+            for (int c = 0; c < p; ++c) basis[r][c] = v[c] / g;
+            pc[r] = lead;
+            ++r;
+        }
+        for (int a = 0; a < r; ++a)
+            for (int b = a + 1; b < r; ++b)
+                if (pc[b] < pc[a]) { int t = pc[a]; pc[a] = pc[b]; pc[b] = t; }
+        s_d = r;
+        for (int a = 0; a < TD_MAXD; ++a) s_piv[a] = a < r ? pc[a] : 0;
+    }
+    __syncthreads();
+    const int d = s_d;
+    /* per-coordinate maxima over the projected coordinates, and the sign
+     * counts of the single coordinate when d == 1 */
+    int lmax[TD_MAXD] = { 0, 0, 0, 0, 0, 0 };
+    int pos = 0, neg = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int c = 0; c < d; ++c) {
+            int64_t v = (int64_t)X[(int64_t)i * p + s_piv[c]] - s_z[s_piv[c]];
+            int64_t a = v < 0 ? -v : v;
+            lmax[c] = max(lmax[c], (int)min(a, (int64_t)INT_MAX));
+            if (d == 1) {
+                pos += v > 0;
+                neg += v < 0;
+            }
+        }
+    }
+    for (int c = 0; c < d; ++c) atomicMax(&s_max[c], lmax[c]);
+    if (d == 1) {
+        atomicAdd(&s_pos, pos);
+        atomicAdd(&s_neg, neg);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int Z = s_Z;
+        Q->n = n;
+        Q->Z = Z;
+        Q->nnz = n - Z;
+        Q->d = d;
+        for (int c = 0; c < TD_MAXD; ++c) {
+            Q->piv[c] = s_piv[c];
+            Q->mx[c] = c < d ? s_max[c] : 0;
+        }
+        bool first_shard = L.shard_count <= 1 || L.shard_index == 0;
+        if (n - Z == 0 || d <= 1) {
+            int direct = (n - Z == 0) ? n : Z + min(s_pos, s_neg);
+            Q->direct = first_shard ? direct : INT_MAX;
+            Q->k = -1;
+            Q->nsub = 0;
+            Q->lo = Q->hi = 0;
+        } else {
+            Q->direct = -1;
+            Q->k = d - 2;
+            int64_t ns = (int64_t)td_binom(n - Z, d - 2);
+            Q->nsub = ns;
+            int64_t sc = L.shard_count > 1 ? L.shard_count : 1;
+            int64_t si = L.shard_count > 1 ? L.shard_index : 0;
+            Q->lo = (int64_t)((__int128)ns * si / sc);
+            Q->hi = (int64_t)((__int128)ns * (si + 1) / sc);
+        }
+        L.qmin[q] = INT_MAX;
+    }
+}
+
+/* ====================================================================== */
+/* tile prefix kernel                                                      */
+/* ====================================================================== */
+
+__host__ __device__ inline int td_auto_spw(int nnz)
+{
+    int s = 16384 / (nnz > 0 ? nnz : 1);
+    return s < 4 ? 4 : (s > 64 ? 64 : s);
+}
+
+__global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
+{
+    __shared__ int64_t s_part[1024];
+    const int nq = L.nq;
+    const int T = blockDim.x;
+    const int per = (nq + T - 1) / T;
+    const int beg = min((int)threadIdx.x * per, nq), end = min(beg + per, nq);
+    int64_t sum = 0;
+    for (int j = beg; j < end; ++j) {
+        const TdQuery &Q = L.q[L.order[j]];
+        int spw = L.spw > 0 ? L.spw : td_auto_spw(Q.nnz);
+        int64_t ts = (int64_t)spw * L.warps;
+        L.tile_size[L.order[j]] = (int)ts;
+        int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? (Q.hi - Q.lo + ts - 1) / ts : 0;
+        sum += cnt;
+    }
+    s_part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int t = 0; t < T; ++t) {
+            int64_t v = s_part[t];
+            s_part[t] = acc;
+            acc += v;
+        }
+        L.tile_prefix[nq] = acc;
+        *L.ticket = 0ull;
+    }
+    __syncthreads();
+    int64_t acc = s_part[threadIdx.x];
+    for (int j = beg; j < end; ++j) {
+        L.tile_prefix[j] = acc;
+        const TdQuery &Q = L.q[L.order[j]];
+        int64_t ts = L.tile_size[L.order[j]];
+        acc += (Q.k >= 0 && Q.hi > Q.lo) ? (Q.hi - Q.lo + ts - 1) / ts : 0;
+    }
+}
+
+/* ====================================================================== */
+/* shared staging of one query's nonzero centred points                    */
+/* ====================================================================== */
+
+/* Stage the nonzero projected centred points of query q, in the order of the
+ * data, into xs (float, stride PS) -- exact, the coordinates are integers
+ * below 2^24.  Returns the number staged (== Q.nnz). */
+__device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int PS, int *s_tmp)
+{
+    const TdQuery &Q = L.q[q];
+    const TdSet S = L.sets[Q.set];
+    const int n = S.n, p = S.p, d = Q.d;
+    const int32_t *X = L.X + S.x_off;
+    const int32_t *z = L.Zq + (int64_t)q * TD_MAXD;
+    const int T = blockDim.x;
+    const int per = (n + T - 1) / T;
+    const int beg = min((int)threadIdx.x * per, n), end = min(beg + per, n);
+    int zc[TD_MAXD];
+    int pv[TD_MAXD];
+#pragma unroll
+    for (int c = 0; c < TD_MAXD; ++c) {
+        zc[c] = c < p ? z[c] : 0;
+        pv[c] = Q.piv[c];
+    }
+    int cnt = 0;
+    for (int i = beg; i < end; ++i) {
+        bool nz = false;
+        for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != zc[c];
+        cnt += nz;
+    }
+    /* block exclusive scan of cnt */
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = td_wscan_incl(cnt, lane);
+    if (lane == 31) s_tmp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int nw = T >> 5;
+        int v = lane < nw ? s_tmp[lane] : 0;
+        int vi = td_wscan_incl(v, lane);
+        if (lane < nw) s_tmp[lane] = vi - v;
+    }
+    __syncthreads();
+    int o = s_tmp[w] + inc - cnt;
+    for (int i = beg; i < end; ++i) {
+        bool nz = false;
+        for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != zc[c];
+        if (!nz) continue;
+        float *dst = xs + (size_t)o * PS;
+        for (int c = 0; c < PS; ++c) {
+            float v = 0.f;
+            if (c < d) v = (float)((int64_t)X[(int64_t)i * p + pv[c]] - zc[pv[c]]);
+            dst[c] = v;
+        }
+        ++o;
+    }
+    __syncthreads();
+    return Q.nnz;
+}
+
+/* ====================================================================== */
+/* filtered sweep (one warp, one subset)                                   */
+/* ====================================================================== */
+
+struct TdWarpStats {
+    unsigned long long sweeps, dependent, filtered, exact, tight, resolved, errors;
+};
+
+template <int D>
+__device__ __forceinline__ void td_load_point(const float *xs, int PS, int i, float (&x)[D])
+{
+    const float4 *p4 = reinterpret_cast<const float4 *>(xs + (size_t)i * PS);
+    float4 a = p4[0];
+    x[0] = a.x;
+    if (D > 1) x[1] = a.y;
+    if (D > 2) x[2] = a.z;
+    if (D > 3) x[3] = a.w;
+    if (D > 4) {
+        float4 b = p4[1];
+        x[4] = b.x;
+        if (D > 5) x[5] = b.y;
+    }
+}
+
+/* Bucket boundary direction D_j for B buckets (pseudo-angle key 2j/B). */
+__device__ __forceinline__ void td_bucket_dir(int j, int B, int64_t &d1, int64_t &d2)
+{
+    if (2 * j <= B) {
+        d1 = B - 2 * j;
+        d2 = 2 * j;
+    } else {
+        d1 = B - 2 * j;
+        d2 = 2 * B - 2 * j;
+    }
+}
+
+/* Exact bucket of a normalised direction h, starting from the estimate b. */
+__device__ __forceinline__ int td_exact_bucket(int64_t h1, int64_t h2, int b, int B)
+{
+    for (int it = 0; it < 2 * B && b > 0; ++it) {
+        int64_t d1, d2;
+        td_bucket_dir(b, B, d1, d2);
+        if (td_cross_sign(d1, d2, h1, h2) >= 0) break; /* angle(h) >= angle(D_b) */
+        --b;
+    }
+    for (int it = 0; it < 2 * B && b < B - 1; ++it) {
+        int64_t d1, d2;
+        td_bucket_dir(b + 1, B, d1, d2);
+        if (td_cross_sign(d1, d2, h1, h2) < 0) break; /* angle(h) < angle(D_{b+1}) */
+        ++b;
+    }
+    return b;
+}
+
+__device__ __forceinline__ float td_key(float h1, float h2)
+{
+    float s = fabsf(h1) + h2;
+    return 1.0f - h1 * __fdividef(1.0f, s);
+}
+
+template <int D>
+__device__ __forceinline__ void td_exact_y(const TdBasis<D> &B, const float (&x)[D], int64_t &y1, int64_t &y2)
+{
+    y1 = 0;
+    y2 = 0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        int64_t xv = (int64_t)x[r];
+        y1 += B.qa[r] * xv;
+        y2 += B.qb[r] * xv;
+    }
+}
+
+/* Exact placement of the points the FP32 filter could not certify (their ids
+ * are in W.glist[0..nu)): exact projection from the published basis; zero
+ * projections are tight points, the others go to their exact bucket. */
+template <int D>
+__device__ __forceinline__ void td_exact_pass(const float *xs, int PS, const uint32_t *hist_unused,
+                                           uint32_t *hist, uint16_t *bid, const uint16_t *list, int nu,
+                                           const int64_t *qa, const int64_t *qb, int B, int lane,
+                                           int *A_out, int *t_out)
+{
+    int A = 0, t = 0;
+    for (int l = lane; l < nu; l += 32) {
+        int i = list[l];
+        const float *xp = xs + (size_t)i * PS;
+        int64_t Y1 = 0, Y2 = 0;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            int64_t xv = (int64_t)xp[r];
+            Y1 += qa[r] * xv;
+            Y2 += qb[r] * xv;
+        }
+        if (Y1 == 0 && Y2 == 0) {
+            bid[i] = (uint16_t)TD_SENT;
+            ++t;
+            continue;
+        }
+        int64_t h1, h2;
+        bool plus = td_normalise(Y1, Y2, h1, h2);
+        float key = td_key((float)h1, (float)h2);
+        int bb = (int)(key * (float)(B >> 1));
+        bb = max(0, min(bb, B - 1));
+        int b = td_exact_bucket(h1, h2, bb, B);
+        bid[i] = (uint16_t)b;
+        atomicAdd(&hist[b], plus ? 0x10000u : 1u);
+        A += plus;
+    }
+    *A_out = td_wsum(A);
+    *t_out = td_wsum(t);
+}
+
+/* exact normalised projection of point i from the published basis */
+template <int D>
+__device__ __forceinline__ void td_exact_h(const float *xs, int PS, int i, const int64_t *qa, const int64_t *qb,
+                                           int64_t &h1, int64_t &h2, bool &plus)
+{
+    const float *xp = xs + (size_t)i * PS;
+    int64_t Y1 = 0, Y2 = 0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        int64_t xv = (int64_t)xp[r];
+        Y1 += qa[r] * xv;
+        Y2 += qb[r] * xv;
+    }
+    plus = td_normalise(Y1, Y2, h1, h2);
+}
+
+struct TdWarpSmem {
+    uint32_t *hist;   /* B packed counters: low 16 bits +1 events, high 16 bits -1 events */
+    uint16_t *bid;    /* bucket of each point (TD_SENT = tight) */
+    uint16_t *glist;  /* uncertain points, then gathered items */
+    int *gcount;
+    int64_t *qa, *qb; /* exact basis of the current subset (for the out-of-line paths) */
+    int *meta;        /* rows[0..3] (intrinsic coordinates), sub[4..7] (subset point ids) */
+};
+
+#define TD_WARP_META_BYTES (2 * TD_MAXD * 8 + 8 * 4)
+
+/* Publish the exact basis and the subset to the warp's shared area. */
+template <int D>
+__device__ __forceinline__ void td_publish_basis(const TdBasis<D> &Bs, const int (&c)[D > 2 ? D - 2 : 1],
+                                                 int64_t *qa, int64_t *qb, int *meta, int lane)
+{
+    constexpr int K = D - 2;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        if (lane == r) qa[r] = Bs.qa[r];
+        if (lane == 8 + r) qb[r] = Bs.qb[r];
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        if (lane == 16 + r) meta[r] = Bs.rows[r];
+        if (lane == 20 + r) meta[4 + r] = c[r];
+    }
+    __syncwarp();
+}
+
+/* Resolution of more than 32 gathered events: exact sort of the list in
+ * shared memory by (bucket, direction) and a sequential walk by lane 0. */
+template <int D>
+__device__ __noinline__ void td_resolve_many(const float *xs, int PS, const int64_t *qa, const int64_t *qb,
+                                             const uint32_t *hist, const uint16_t *bid, uint16_t *glist,
+                                             int G, int lane, int *mn_io, int *mx_io)
+{
+    int npad = td_pow2_at_least(G);
+    for (int l = G + lane; l < npad; l += 32) glist[l] = (uint16_t)TD_SENT;
+    __syncwarp();
+    for (int size = 2; size <= npad; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int tt = lane; tt < (npad >> 1); tt += 32) {
+                int i = ((tt & ~(stride - 1)) << 1) | (tt & (stride - 1));
+                int j = i + stride;
+                bool up = (i & size) == 0;
+                uint16_t u = glist[i], v = glist[j];
+                /* (bucket, exact direction) order */
+                auto less = [&](uint16_t x, uint16_t y) -> bool {
+                    if (x == TD_SENT) return false;
+                    if (y == TD_SENT) return true;
+                    int bx = bid[x], by = bid[y];
+                    if (bx != by) return bx < by;
+                    int64_t x1, x2, y1, y2;
+                    bool px, py;
+                    td_exact_h<D>(xs, PS, x, qa, qb, x1, x2, px);
+                    td_exact_h<D>(xs, PS, y, qa, qb, y1, y2, py);
+                    return td_cross_sign(x1, x2, y1, y2) > 0;
+                };
+                bool sw = up ? less(v, u) : less(u, v);
+                if (sw) {
+                    glist[i] = v;
+                    glist[j] = u;
+                }
+            }
+            __syncwarp();
+        }
+    int lmn = INT_MAX, lmx = INT_MIN;
+    if (lane == 0) {
+        int j = 0;
+        while (j < G) {
+            int bk = bid[glist[j]];
+            int v = (int)(hist[bk] & 0xFFFFu);
+            while (j < G && bid[glist[j]] == bk) {
+                int64_t g1, g2;
+                bool gp;
+                td_exact_h<D>(xs, PS, glist[j], qa, qb, g1, g2, gp);
+                while (j < G && bid[glist[j]] == bk) {
+                    int64_t c1, c2;
+                    bool plus;
+                    td_exact_h<D>(xs, PS, glist[j], qa, qb, c1, c2, plus);
+                    if (td_cross_sign(g1, g2, c1, c2) != 0) break;
+                    v += plus ? -1 : 1;
+                    ++j;
+                }
+                lmn = min(lmn, v);
+                lmx = max(lmx, v);
+            }
+        }
+    }
+    lmn = __shfl_sync(TD_FULL, lmn, 0);
+    lmx = __shfl_sync(TD_FULL, lmx, 0);
+    *mn_io = min(*mn_io, lmn);
+    *mx_io = max(*mx_io, lmx);
+}
+
+/* G(S) for one subset, FP32-filtered (the basis must be published to
+ * W.qa/W.qb first).  Also returns the number t of tight points (nonzero
+ * points of span S) and the number of nonzero projections. */
+template <int D>
+__device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis<D> &Bs,
+                                 const float (&fa)[D], const float (&fb)[D], float Ea, float Eb,
+                                 const TdWarpSmem &W, int blog2, int lane, TdWarpStats &st,
+                                 int &t_out, int &nzy_out)
+{
+    const int B = 1 << blog2;
+    const float halfB = (float)(B >> 1);
+    const float E = fmaxf(Ea, Eb);
+    const unsigned below = (1u << lane) - 1u;
+    int A = 0, nu = 0;
+    for (int i0 = 0; i0 < nnz; i0 += 32) {
+        const int i = i0 + lane;
+        const bool valid = i < nnz;
+        float x[D];
+        td_load_point<D>(xs, PS, valid ? i : 0, x);
+        float y1 = fa[0] * x[0], y2 = fb[0] * x[0];
+#pragma unroll
+        for (int r = 1; r < D; ++r) {
+            y1 = fmaf(fa[r], x[r], y1);
+            y2 = fmaf(fb[r], x[r], y2);
+        }
+        const float s = fabsf(y1) + fabsf(y2);
+        bool ok = (fabsf(y2) > Eb) && (s > 4.0f * E);
+        const bool plus = y2 > 0.0f;
+        const float h1 = plus ? y1 : -y1;
+        const float r = __fdividef(1.0f, s);
+        const float key = 1.0f - h1 * r;
+        const float delta = fmaf(2.0f * E, r, 16.0f * TD_U);
+        const float bf = key * halfB;
+        int b = max(0, min((int)bf, B - 1));
+        const float frac = bf - (float)b;
+        const float dB = delta * halfB;
+        if ((b > 0 && frac <= dB) || (b < B - 1 && frac >= 1.0f - dB)) ok = false;
+        const bool unc = valid && !ok;
+        const unsigned bu = __ballot_sync(TD_FULL, unc);
+        if (unc) W.glist[nu + __popc(bu & below)] = (uint16_t)i;
+        nu += __popc(bu);
+        if (valid && ok) {
+            W.bid[i] = (uint16_t)b;
+            atomicAdd(&W.hist[b], plus ? 0x10000u : 1u);
+            A += plus;
+        }
+    }
+    A = td_wsum(A);
+    int t = 0;
+    if (nu > 0) {
+        __syncwarp();
+        int Ae = 0;
+        td_exact_pass<D>(xs, PS, nullptr, W.hist, W.bid, W.glist, nu, W.qa, W.qb, B, lane, &Ae, &t);
+        A += Ae;
+    }
+    if (lane == 0) {
+        st.exact += nu;
+        st.filtered += nnz - nu;
+    }
+    const int nzy = nnz - t;
+    t_out = t;
+    nzy_out = nzy;
+    __syncwarp();
+
+    /* walk values at the bucket boundaries */
+    const int per = B >> 5;
+    uint32_t *hl = W.hist + lane * per;
+    uint32_t acc = 0;
+    for (int j = 0; j < per; ++j) acc += hl[j];
+    const int net = (int)(acc & 0xFFFFu) - (int)(acc >> 16);
+    const int excl = td_wscan_incl(net, lane) - net;
+    int P = A + excl;
+    int mn = INT_MAX, mx = INT_MIN, lo = INT_MAX, hi = INT_MIN;
+    for (int j = 0; j < per; ++j) {
+        uint32_t w = hl[j];
+        int cp = (int)(w & 0xFFFFu), cm = (int)(w >> 16);
+        mn = min(mn, P);
+        mx = max(mx, P);
+        if (cp && cm) {
+            lo = min(lo, P - cm);
+            hi = max(hi, P + cp);
+        }
+        P += cp - cm;
+    }
+    mn = min(mn, P);
+    mx = max(mx, P);
+    mn = td_wmin(mn);
+    mx = td_wmax(mx);
+    lo = td_wmin(lo);
+    hi = td_wmax(hi);
+    const bool need_lo = lo < mn, need_hi = hi > mx;
+    int mn2 = mn, mx2 = mx;
+    if (need_lo || need_hi) {
+        if (lane == 0) st.resolved++;
+        P = A + excl;
+        for (int j = 0; j < per; ++j) {
+            uint32_t w = hl[j];
+            int cp = (int)(w & 0xFFFFu), cm = (int)(w >> 16);
+            bool cand = cp && cm && ((need_lo && P - cm < mn) || (need_hi && P + cp > mx));
+            hl[j] = cand ? (0x80000000u | (uint32_t)P) : 0u;
+            P += cp - cm;
+        }
+        __syncwarp();
+        int G = 0;
+        for (int i0 = 0; i0 < nnz; i0 += 32) {
+            const int i = i0 + lane;
+            bool g = false;
+            if (i < nnz) {
+                uint16_t b = W.bid[i];
+                g = b != TD_SENT && (W.hist[b] >> 31);
+            }
+            const unsigned bg = __ballot_sync(TD_FULL, g);
+            if (g) W.glist[G + __popc(bg & below)] = (uint16_t)i;
+            G += __popc(bg);
+        }
+        __syncwarp();
+        if (G <= 32) {
+            /* one gathered event per lane: exact direction, warp bitonic sort
+             * by (bucket, direction), segmented walk */
+            int bk = INT_MAX, e = 0, Pb = 0;
+            int64_t h1 = 0, h2 = 0;
+            if (lane < G) {
+                const int i = W.glist[lane];
+                float xg[D];
+                td_load_point<D>(xs, PS, i, xg);
+                int64_t Y1, Y2;
+                td_exact_y<D>(Bs, xg, Y1, Y2);
+                const bool pl = td_normalise(Y1, Y2, h1, h2);
+                e = pl ? -1 : 1;
+                bk = W.bid[i];
+                Pb = (int)(W.hist[bk] & 0xFFFFu);
+            }
+#pragma unroll 1
+            for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll 1
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const int obk = __shfl_xor_sync(TD_FULL, bk, stride);
+                    const int oe = __shfl_xor_sync(TD_FULL, e, stride);
+                    const int oPb = __shfl_xor_sync(TD_FULL, Pb, stride);
+                    const int64_t oh1 = __shfl_xor_sync(TD_FULL, h1, stride);
+                    const int64_t oh2 = __shfl_xor_sync(TD_FULL, h2, stride);
+                    bool o_less, m_less;
+                    if (obk != bk) {
+                        o_less = obk < bk;
+                        m_less = bk < obk;
+                    } else if (bk == INT_MAX) {
+                        o_less = m_less = false;
+                    } else {
+                        const int cs = td_cross_sign(h1, h2, oh1, oh2);
+                        m_less = cs > 0;
+                        o_less = cs < 0;
+                    }
+                    const bool up = (lane & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    const bool take = (lower == up) ? o_less : m_less;
+                    if (take) {
+                        bk = obk;
+                        e = oe;
+                        Pb = oPb;
+                        h1 = oh1;
+                        h2 = oh2;
+                    }
+                }
+            const int nbk = __shfl_down_sync(TD_FULL, bk, 1);
+            const int64_t nh1 = __shfl_down_sync(TD_FULL, h1, 1);
+            const int64_t nh2 = __shfl_down_sync(TD_FULL, h2, 1);
+            const int pbk = __shfl_up_sync(TD_FULL, bk, 1);
+            const bool valid = lane < G;
+            const bool tie_next = valid && lane + 1 < G && nbk == bk && td_cross_sign(h1, h2, nh1, nh2) == 0;
+            const bool head = valid && (lane == 0 || pbk != bk);
+            const int S = td_wscan_incl(valid ? e : 0, lane);
+            const int hidx = td_wscan_max_incl(head ? lane : 0, lane);
+            const int Shead = __shfl_sync(TD_FULL, S, hidx);
+            const int ehead = __shfl_sync(TD_FULL, e, hidx);
+            const int val = Pb + (S - (Shead - ehead));
+            const int vmn = (valid && !tie_next) ? val : INT_MAX;
+            const int vmx = (valid && !tie_next) ? val : INT_MIN;
+            mn2 = min(mn2, td_wmin(vmn));
+            mx2 = max(mx2, td_wmax(vmx));
+        } else {
+            td_resolve_many<D>(xs, PS, W.qa, W.qb, W.hist, W.bid, W.glist, G, lane, &mn2, &mx2);
+        }
+        __syncwarp();
+        for (int l = lane; l < G; l += 32) W.hist[W.bid[W.glist[l]]] = 0u;
+    } else {
+        if (per >= 4) {
+            uint4 *h4 = reinterpret_cast<uint4 *>(hl);
+            for (int j = 0; j < (per >> 2); ++j) h4[j] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            for (int j = 0; j < per; ++j) hl[j] = 0u;
+        }
+    }
+    __syncwarp();
+    return min(mn2, nzy - mx2);
+}
+
+/* Tight-set correction m_S after a sweep.  Tight points are those with bucket
+ * id TD_SENT (filtered kernel, bid != NULL) or a zero projection H (plain
+ * kernel); coordinates come from xs (float, filtered) or xi (int, plain).
+ * The subset's rows and point ids are in meta (published basis). */
+template <int D>
+__device__ __noinline__ int td_tight_correction(const int *meta, const float *xs, int PS, const int32_t *xi,
+                                                int PSI, int nnz, const uint16_t *bid, const int64_t *H,
+                                                TdScratch scr, int *gcount, int lane)
+{
+    constexpr int K = D - 2;
+    if constexpr (K <= 0) {
+        return 0;
+    } else {
+        auto is_tight = [&](int i) -> bool {
+            if (bid) return bid[i] == TD_SENT;
+            return H[2 * i] == 0 && H[2 * i + 1] == 0;
+        };
+        auto coord = [&](int i, int r) -> int64_t {
+            if (xs) return (int64_t)xs[(size_t)i * PS + r];
+            return (int64_t)xi[(size_t)i * PSI + r];
+        };
+        int rows[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) rows[r] = meta[r];
+        if constexpr (K == 1) {
+            int pos = 0, neg = 0;
+            for (int i = lane; i < nnz; i += 32)
+                if (is_tight(i)) {
+                    int64_t v = coord(i, rows[0]);
+                    pos += v > 0;
+                    neg += v < 0;
+                }
+            return min(td_wsum(pos), td_wsum(neg));
+        } else {
+            int t = 0;
+            const unsigned below = (1u << lane) - 1u;
+            for (int i0 = 0; i0 < nnz; i0 += 32) {
+                const int i = i0 + lane;
+                const bool g = i < nnz && is_tight(i);
+                const unsigned bg = __ballot_sync(TD_FULL, g);
+                if (g) {
+                    const int slot = t + __popc(bg & below);
+#pragma unroll
+                    for (int r = 0; r < K; ++r) scr.c0[4 * slot + r] = (int32_t)coord(i, rows[r]);
+                }
+                t += __popc(bg);
+            }
+            __syncwarp();
+            int64_t sint[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) sint[j][r] = (j < K && r < K) ? coord(meta[4 + j], rows[r]) : 0;
+            return td_tight_depth<K>(t, sint, scr, lane);
+        }
+    }
+}
+
+/* Process subset positions [r0, r1) of query q with one warp (filtered). */
+template <int D>
+__device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int PS, int nnz,
+                                 uint64_t r0, uint64_t r1, const TdWarpSmem &W, const TdScratch &scr,
+                                 int blog2, int lane, int &best, TdWarpStats &st)
+{
+    constexpr int K = D - 2;
+    if (r0 >= r1) return;
+    const TdQuery &Q = L.q[q];
+    int c[K > 0 ? K : 1];
+    c[0] = 0;
+    td_unrank_colex<K>(r0, nnz, c);
+    int mx[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) mx[r] = Q.mx[r];
+    for (uint64_t r = r0; r < r1; ++r) {
+        if (r > r0) td_next_colex<K>(c);
+        int64_t s[K > 0 ? K : 1][D];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            float xj[D];
+            td_load_point<D>(xs, PS, c[j], xj);
+#pragma unroll
+            for (int t = 0; t < D; ++t) s[j][t] = (int64_t)xj[t];
+        }
+        TdBasis<D> Bs;
+        if (!td_make_basis<D>(s, Bs)) {
+            if (lane == 0) st.dependent++;
+            continue;
+        }
+        if (lane == 0) st.sweeps++;
+        td_publish_basis<D>(Bs, c, W.qa, W.qb, W.meta, lane);
+        float fa[D], fb[D];
+        int64_t Aa = 0, Ab = 0;
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+            fa[t] = (float)Bs.qa[t];
+            fb[t] = (float)Bs.qb[t];
+            Aa += (Bs.qa[t] < 0 ? -Bs.qa[t] : Bs.qa[t]) * (int64_t)mx[t];
+            Ab += (Bs.qb[t] < 0 ? -Bs.qb[t] : Bs.qb[t]) * (int64_t)mx[t];
+        }
+        /* forward error bound of the FP32 fma chain: (D + 1) u sum |q_i x_i|,
+         * taken as (D + 2) u with the rounding of the sum covered by the
+         * extra factor 1 + 2^-10 */
+        const float cst = (float)(D + 2) * TD_U * 1.0009765625f;
+        const float Ea = (float)Aa * cst, Eb = (float)Ab * cst;
+        int t, nzy;
+        const int G = td_sweep_filtered<D>(xs, PS, nnz, Bs, fa, fb, Ea, Eb, W, blog2, lane, st, t, nzy);
+        int V = G;
+        if (t > K && G < best) {
+            if (lane == 0) st.tight++;
+            V = G + td_tight_correction<D>(W.meta, xs, PS, nullptr, 0, nnz, W.bid, nullptr, scr, W.gcount, lane);
+        }
+        best = min(best, V);
+    }
+}
+
+/* ====================================================================== */
+/* persistent filtered kernel                                              */
+/* ====================================================================== */
+
+__device__ __forceinline__ int td_query_of_tile(const TdLaunch &L, int64_t tile)
+{
+    int lo = 0, hi = L.nq - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (L.tile_prefix[mid] <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256, 1) td_k_filtered(TdLaunch L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int64_t s_tile;
+    __shared__ int s_tmp[32];
+    __shared__ int s_best[TD_WARPS_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nmaxp = td_pow2_at_least(L.nmax);
+    const int PS = L.pmax <= 4 ? 4 : 8;
+    const int blog2_cap = L.blog2;
+    /* layout: xs [nmax][PS] floats | per warp: hist [B] u32, bid [nmaxp] u16, glist [nmaxp] u16, gcount */
+    float *xs = reinterpret_cast<float *>(smem);
+    size_t off = ((size_t)L.nmax * PS * 4 + 15) & ~(size_t)15;
+    const int Bmax = 1 << blog2_cap;
+    size_t per_warp = ((size_t)Bmax * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    unsigned char *wb = smem + off + per_warp * w;
+    TdWarpSmem W;
+    W.hist = reinterpret_cast<uint32_t *>(wb);
+    W.bid = reinterpret_cast<uint16_t *>(wb + (size_t)Bmax * 4);
+    W.glist = W.bid + nmaxp;
+    W.gcount = reinterpret_cast<int *>(W.glist + nmaxp);
+    W.qa = reinterpret_cast<int64_t *>(wb + (size_t)Bmax * 4 + (size_t)nmaxp * 4 + 16);
+    W.qb = W.qa + TD_MAXD;
+    W.meta = reinterpret_cast<int *>(W.qb + TD_MAXD);
+    for (int j = lane; j < Bmax; j += 32) W.hist[j] = 0u;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + w;
+    const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, nmaxp);
+    TdWarpStats st = { 0, 0, 0, 0, 0, 0, 0 };
+    int staged = -1;
+    const int64_t total = L.tile_prefix[L.nq];
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(L.ticket, 1ull);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= total) break;
+        const int j = td_query_of_tile(L, tile);
+        const int q = L.order[j];
+        if (q != staged) {
+            td_stage_points(L, q, xs, PS, s_tmp);
+            staged = q;
+        }
+        const TdQuery &Q = L.q[q];
+        const int nnz = Q.nnz, d = Q.d;
+        const int64_t ts = L.tile_size[q];
+        const int64_t t0 = Q.lo + (tile - L.tile_prefix[j]) * ts;
+        const int64_t t1 = min(t0 + ts, Q.hi);
+        const int64_t spw = ts / (blockDim.x >> 5);
+        const uint64_t r0 = (uint64_t)min(t0 + spw * w, t1), r1 = (uint64_t)min(t0 + spw * (w + 1), t1);
+        /* buckets: about one per nonzero point, at least 32 */
+        int blog2 = 5;
+        while ((1 << blog2) < nnz && blog2 < blog2_cap) ++blog2;
+        int best = L.qmin[q];
+        switch (d) {
+        case 2: td_warp_filtered<2>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
+        case 3: td_warp_filtered<3>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
+        case 4: td_warp_filtered<4>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
+        case 5: td_warp_filtered<5>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
+        case 6: td_warp_filtered<6>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
+        default: if (lane == 0) st.errors++; break;
+        }
+        if (lane == 0) s_best[w] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int b = INT_MAX;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b = min(b, s_best[k]);
+            if (b < INT_MAX) atomicMin(&L.qmin[q], b);
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&L.ctr->sweeps, st.sweeps);
+        atomicAdd(&L.ctr->dependent, st.dependent);
+        atomicAdd(&L.ctr->filtered_points, st.filtered);
+        atomicAdd(&L.ctr->exact_points, st.exact);
+        atomicAdd(&L.ctr->tight, st.tight);
+        atomicAdd(&L.ctr->resolved, st.resolved);
+        atomicAdd(&L.ctr->errors, st.errors);
+    }
+}
+
+/* ====================================================================== */
+/* plain exact kernel (one query per launch)                               */
+/* ====================================================================== */
+
+template <int D>
+__device__ void td_warp_plain(const TdLaunch &L, int q, const int32_t *xi, int PSI, int nnz,
+                              uint64_t r0, uint64_t r1, int64_t *H, uint16_t *idx, int *gcount,
+                              int64_t *wqa, int64_t *wqb, int *wmeta,
+                              const TdScratch &scr, int lane, int &best, TdWarpStats &st)
+{
+    constexpr int K = D - 2;
+    if (r0 >= r1) return;
+    int c[K > 0 ? K : 1];
+    c[0] = 0;
+    td_unrank_colex<K>(r0, nnz, c);
+    for (uint64_t r = r0; r < r1; ++r) {
+        if (r > r0) td_next_colex<K>(c);
+        int64_t s[K > 0 ? K : 1][D];
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+#pragma unroll
+            for (int t = 0; t < D; ++t) s[j][t] = xi[(size_t)c[j] * PSI + t];
+        TdBasis<D> Bs;
+        if (!td_make_basis<D>(s, Bs)) {
+            if (lane == 0) st.dependent++;
+            continue;
+        }
+        if (lane == 0) st.sweeps++;
+        td_publish_basis<D>(Bs, c, wqa, wqb, wmeta, lane);
+        /* exact projections of every point, compacted list of the nonzero ones */
+        int base = 0, t = 0;
+        for (int i0 = 0; i0 < nnz; i0 += 32) {
+            int i = i0 + lane;
+            int64_t y1 = 0, y2 = 0;
+            bool valid = i < nnz;
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    int64_t xv = xi[(size_t)i * PSI + k];
+                    y1 += Bs.qa[k] * xv;
+                    y2 += Bs.qb[k] * xv;
+                }
+            }
+            bool tight = valid && y1 == 0 && y2 == 0;
+            bool nonz = valid && !tight;
+            int64_t h1 = 0, h2 = 0;
+            bool plus = false;
+            if (nonz) plus = td_normalise(y1, y2, h1, h2);
+            if (valid) {
+                H[2 * i] = h1;
+                H[2 * i + 1] = h2;
+            }
+            unsigned bn = __ballot_sync(TD_FULL, nonz);
+            if (nonz) idx[base + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)(i | (plus ? 0x8000 : 0));
+            base += __popc(bn);
+            t += __popc(__ballot_sync(TD_FULL, tight));
+        }
+        __syncwarp();
+        int G = td_sweep_list(idx, base, H, lane);
+        st.exact += (lane == 0) ? nnz : 0;
+        int V = G;
+        if (t > K && G < best) {
+            if (lane == 0) st.tight++;
+            V = G + td_tight_correction<D>(wmeta, nullptr, 0, xi, PSI, nnz, nullptr, H, scr, gcount, lane);
+        }
+        best = min(best, V);
+    }
+}
+
+__global__ void __launch_bounds__(128, 1) td_k_plain(TdLaunch L, int q)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_tmp[32];
+    __shared__ int s_best[TD_WARPS_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const TdQuery &Q = L.q[q];
+    if (Q.k < 0 || Q.hi <= Q.lo) return;
+    const int nnz = Q.nnz, d = Q.d;
+    const int nmaxp = td_pow2_at_least(L.nmax);
+    const int PSI = L.pmax <= 4 ? 4 : 8;
+    /* layout: xi [nmax][PSI] int32 | per warp: H [nmaxp][2] int64, idx [nmaxp] u16, gcount */
+    int32_t *xi = reinterpret_cast<int32_t *>(smem);
+    size_t off = ((size_t)L.nmax * PSI * 4 + 15) & ~(size_t)15;
+    size_t per_warp = ((size_t)nmaxp * 16 + (size_t)nmaxp * 2 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    unsigned char *wb = smem + off + per_warp * w;
+    int64_t *H = reinterpret_cast<int64_t *>(wb);
+    uint16_t *idx = reinterpret_cast<uint16_t *>(wb + (size_t)nmaxp * 16);
+    int *gcount = reinterpret_cast<int *>(idx + nmaxp);
+    int64_t *wqa = reinterpret_cast<int64_t *>(wb + (size_t)nmaxp * 16 + (size_t)nmaxp * 2 + 16);
+    int64_t *wqb = wqa + TD_MAXD;
+    int *wmeta = reinterpret_cast<int *>(wqb + TD_MAXD);
+    {
+        const TdSet S = L.sets[Q.set];
+        const int n = S.n, p = S.p;
+        const int32_t *X = L.X + S.x_off;
+        const int32_t *z = L.Zq + (int64_t)q * TD_MAXD;
+        const int T = blockDim.x;
+        const int per = (n + T - 1) / T;
+        const int beg = min((int)threadIdx.x * per, n), end = min(beg + per, n);
+        int cnt = 0;
+        for (int i = beg; i < end; ++i) {
+            bool nz = false;
+            for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != z[c];
+            cnt += nz;
+        }
+        int inc = td_wscan_incl(cnt, lane);
+        if (lane == 31) s_tmp[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            int v = lane < nw ? s_tmp[lane] : 0;
+            int vi = td_wscan_incl(v, lane);
+            if (lane < nw) s_tmp[lane] = vi - v;
+        }
+        __syncthreads();
+        int o = s_tmp[w] + inc - cnt;
+        for (int i = beg; i < end; ++i) {
+            bool nz = false;
+            for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != z[c];
+            if (!nz) continue;
+            for (int c = 0; c < PSI; ++c)
+                xi[(size_t)o * PSI + c] = c < d ? (int32_t)((int64_t)X[(int64_t)i * p + Q.piv[c]] - z[Q.piv[c]]) : 0;
+            ++o;
+        }
+        __syncthreads();
+    }
+    const int gw = blockIdx.x * nw + w;
+    const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, nmaxp);
+    TdWarpStats st = { 0, 0, 0, 0, 0, 0, 0 };
+    const int64_t ts = (int64_t)(L.spw > 0 ? L.spw : 8) * nw;
+    const int64_t ntiles = (Q.hi - Q.lo + ts - 1) / ts;
+    int best = INT_MAX;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t t0 = Q.lo + tile * ts, t1 = min(t0 + ts, Q.hi);
+        const int64_t spw = ts / nw;
+        const uint64_t r0 = (uint64_t)min(t0 + spw * w, t1), r1 = (uint64_t)min(t0 + spw * (w + 1), t1);
+        switch (d) {
+        case 2: td_warp_plain<2>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
+        case 3: td_warp_plain<3>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
+        case 4: td_warp_plain<4>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
+        case 5: td_warp_plain<5>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
+        case 6: td_warp_plain<6>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
+        default: if (lane == 0) st.errors++; break;
+        }
+    }
+    if (lane == 0) s_best[w] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int b = INT_MAX;
+        for (int k = 0; k < nw; ++k) b = min(b, s_best[k]);
+        if (b < INT_MAX) atomicMin(&L.qmin[q], b);
+    }
+    if (lane == 0) {
+        atomicAdd(&L.ctr->sweeps, st.sweeps);
+        atomicAdd(&L.ctr->dependent, st.dependent);
+        atomicAdd(&L.ctr->exact_points, st.exact);
+        atomicAdd(&L.ctr->tight, st.tight);
+        atomicAdd(&L.ctr->errors, st.errors);
+    }
+}
+
+/* ====================================================================== */
+/* finalize                                                                */
+/* ====================================================================== */
+
+__global__ void td_k_finalize(TdLaunch L)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= L.nq) return;
+    const TdQuery &Q = L.q[q];
+    int r;
+    if (Q.direct >= 0) {
+        r = Q.direct;
+    } else if (L.qmin[q] == INT_MAX) {
+        /* no independent subset in this shard's range */
+        r = (L.shard_count > 1) ? INT_MAX : -1;
+        if (L.shard_count <= 1) atomicAdd(&L.ctr->errors, 1ull);
+    } else {
+        r = Q.Z + L.qmin[q];
+    }
+    L.out[q] = r;
+}
+
+/* ====================================================================== */
+/* host-side launch helpers (called from td_api.cu)                        */
+/* ====================================================================== */
+
+size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
+{
+    int nmaxp = td_pow2_at_least(nmax);
+    int PS = pmax <= 4 ? 4 : 8;
+    size_t off = ((size_t)nmax * PS * 4 + 15) & ~(size_t)15;
+    size_t per_warp = ((size_t)(1 << blog2) * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    return off + per_warp * warps;
+}
+
+size_t td_plain_smem(int nmax, int pmax, int warps)
+{
+    int nmaxp = td_pow2_at_least(nmax);
+    int PSI = pmax <= 4 ? 4 : 8;
+    size_t off = ((size_t)nmax * PSI * 4 + 15) & ~(size_t)15;
+    size_t per_warp = ((size_t)nmaxp * 16 + (size_t)nmaxp * 2 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    return off + per_warp * warps;
+}
+
+int64_t td_scratch_per_warp(int nmax) { return (td_scratch_bytes(td_pow2_at_least(nmax)) + 255) & ~(int64_t)255; }
+
+cudaError_t td_launch_setup(const TdLaunch &L, cudaStream_t s)
+{
+    td_k_setup<<<L.nq, 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t td_launch_tiles(const TdLaunch &L, cudaStream_t s)
+{
+    td_k_tiles<<<1, 1024, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+/* The dynamic shared memory attribute is set to exactly what a launch uses
+ * (td_prepare_*), before any stream capture; the launches do not touch it. */
+cudaError_t td_prepare_filtered(size_t smem)
+{
+    return cudaFuncSetAttribute(td_k_filtered, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t td_prepare_plain(size_t smem)
+{
+    return cudaFuncSetAttribute(td_k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t td_launch_filtered(const TdLaunch &L, int grid, size_t smem, cudaStream_t s)
+{
+    td_k_filtered<<<grid, L.warps * 32, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t td_launch_plain(const TdLaunch &L, int q, int grid, size_t smem, cudaStream_t s)
+{
+    td_k_plain<<<grid, L.warps * 32, smem, s>>>(L, q);
+    return cudaGetLastError();
+}
+
+cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s)
+{
+    td_k_finalize<<<(L.nq + 255) / 256, 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+int td_filtered_occupancy(int warps, size_t smem)
+{
+    int blocks = 0;
+    if (td_prepare_filtered(smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_k_filtered, warps * 32, smem) != cudaSuccess) return 0;
+    return blocks;
+}
+
+int td_plain_occupancy(int warps, size_t smem)
+{
+    int blocks = 0;
+    if (td_prepare_plain(smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_k_plain, warps * 32, smem) != cudaSuccess) return 0;
+    return blocks;
+}

@@ -1,0 +1,82 @@
+"""Write the stored expected depth counts under tests/golden/ (CPU only).
+
+Every value written here comes from the CPU oracle (``oracle/``) applied to the
+seeded workloads of ``paper_1409_3901_gb300.workloads``; each file records the
+input checksum so that a test on another machine first checks that it
+regenerated the same inputs.  Queries are spread over worker processes
+(``spawn`` start method); the oracle code is the same in each.
+
+    python tests/golden/make_golden.py W1 W2 W4 W3S W5S [--procs 8]
+
+W3S and W5S are bounded samples of the batched and stream workloads: every
+query of the datasets (requests) whose full oracle cost is small.
+"""
+import argparse
+import json
+import multiprocessing as mp
+import os
+import sys
+import time
+from math import comb
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1409_3901_gb300 import workloads as W  # noqa: E402
+
+# per-query oracle cost budget for the sampled workloads (point-subset slots)
+SAMPLE_COST = 6e7
+
+
+def _one(args):
+    import oracle
+    X, z = args
+    return oracle.depth(X, z)
+
+
+def _run(pool, X, Zq):
+    return [int(v) for v in pool.map(_one, [(X, z) for z in Zq], chunksize=1)]
+
+
+def _cost(d):
+    return comb(d.n, max(d.p - 2, 0)) * d.n
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("names", nargs="+")
+    ap.add_argument("--procs", type=int, default=os.cpu_count())
+    a = ap.parse_args()
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(a.procs) as pool:
+        for name in a.names:
+            t0 = time.time()
+            if name in ("W1", "W2", "W4"):
+                d = W.WORKLOADS[name]()
+                out = {"workload": name, "description": d.name, "checksum": d.checksum(),
+                       "n": d.n, "p": d.p, "m": d.m, "T": _run(pool, d.X, d.Zq)}
+            elif name in ("W3S", "W5S"):
+                sets = W.w3() if name == "W3S" else W.w5()
+                items = []
+                for i, d in enumerate(sets):
+                    if _cost(d) <= SAMPLE_COST:
+                        items.append({"index": i, "checksum": d.checksum(), "n": d.n, "p": d.p,
+                                      "m": d.m, "T": _run(pool, d.X, d.Zq)})
+                out = {"workload": name[:2], "sample": "every query of the datasets with "
+                       "C(n,p-2)*n <= %.0e" % SAMPLE_COST, "items": items}
+            else:
+                raise SystemExit("unknown workload " + name)
+            out["source"] = "oracle/tukey_oracle.c via tests/golden/make_golden.py"
+            path = os.path.join(HERE, name + ".json")
+            with open(path, "w") as f:
+                json.dump(out, f, indent=1)
+            print("%s written in %.1f s" % (path, time.time() - t0), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,95 @@
+"""The C-ABI library loads and exports every symbol include/tukey_depth.h
+declares; host-side argument checks (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tukey_depth.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(td_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def tukey():
+    from paper_1409_3901_gb300 import build
+    build.build()
+    from paper_1409_3901_gb300 import tukey as t
+    return t
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ["td_create", "td_destroy", "td_depth", "td_depth_batched", "td_stream_create",
+              "td_stream_submit", "td_stream_poll", "td_stream_wait", "td_stream_destroy",
+              "td_strerror"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(tukey):
+    lib = ctypes.CDLL(tukey.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(tukey.EXPORTED) == _declared_functions()
+
+
+def test_coord_limits_and_strerror(tukey):
+    lim = [tukey.td_coord_limit(p) for p in range(0, 8)]
+    assert lim[0] == 0 and lim[7] == 0
+    assert lim[1] == lim[2] == lim[3] == 2 ** 24 - 1
+    # every exact intermediate fits: d * max|minor| * M < 2^62
+    assert 4 * 2 * lim[4] ** 3 < 2 ** 62
+    assert 5 * 3 ** 1.5 * lim[5] ** 4 < 2 ** 62
+    assert 6 * 16 * lim[6] ** 5 < 2 ** 62
+    for code in range(-8, 1):
+        assert tukey.td_strerror(code)
+    assert tukey.td_strerror(-99) == b"unknown error"
+
+
+def test_null_and_bad_arguments_rejected_without_device(tukey):
+    assert tukey.td_create(None, 0, None) == tukey.TD_ERR_INVALID
+    assert tukey.td_depth(None, None, 1, 1, None, 0, None, None) == tukey.TD_ERR_INVALID
+    assert tukey.td_destroy(None) == tukey.TD_ERR_INVALID
+    assert tukey.td_stream_create(None, 0, None) == tukey.TD_ERR_INVALID
+    done = ctypes.c_int()
+    assert tukey.td_stream_poll(None, 1, ctypes.byref(done)) == tukey.TD_ERR_INVALID
+
+
+def test_create_reports_missing_device(tukey):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    ptr = ctypes.c_void_p()
+    rc = tukey.td_create(ctypes.byref(ptr), 0, None)
+    assert rc in (tukey.TD_ERR_CUDA, tukey.TD_ERR_OOM)
+    assert not ptr.value
+
+
+def test_structs_match_header_layout(tukey):
+    assert ctypes.sizeof(tukey.td_options) == 4 * 6 + 8 * 2 + 8
+    assert ctypes.sizeof(tukey.td_dataset) == 8 + 8 + 8 + 8 + 8
+    assert ctypes.sizeof(tukey.td_stats) == 7 * 8 + 8
+
+
+def test_workload_generators_are_deterministic():
+    from paper_1409_3901_gb300 import workloads as W
+    a, b = W.w1(), W.w1()
+    assert a.checksum() == b.checksum()
+    d = W.w2()
+    assert d.X.shape == (1000, 4) and d.Zq.shape == (64, 4)
+    assert np.abs(d.X).max() <= 127
+    d4 = W.w4()
+    # the copied rows and the hyperplane rows are present
+    uniq = np.unique(d4.X, axis=0)
+    assert len(uniq) <= 200 - 15
+    a_, c_ = d4.meta["hyperplane_a"], d4.meta["hyperplane_c"]
+    on = (d4.X @ np.array(a_) == c_).sum()
+    assert on >= 10

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer results, so the bar is bit-exact.  Both execution forms are checked:
+the FP32-filtered persistent form (TD_MODE_FILTERED, what bench.py times)
+and the plain exact one-query-per-launch form (TD_MODE_PLAIN_EXACT).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import load_golden, random_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def td():
+    from paper_1409_3901_gb300 import tukey
+    return tukey
+
+
+@pytest.fixture(scope="module")
+def ctx(td):
+    return td.Context(0)
+
+
+@pytest.fixture(scope="module")
+def plain(td):
+    return td.Context(0, mode=td.TD_MODE_PLAIN_EXACT)
+
+
+def _check_both(ctx, plain, X, Z):
+    want = oracle.depth_many(X, Z)
+    got = ctx.depth(X, Z)
+    assert np.array_equal(got, want), (got.tolist(), want.tolist())
+    got_p = plain.depth(X, Z)
+    assert np.array_equal(got_p, want), (got_p.tolist(), want.tolist())
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_small_random_with_ties(ctx, plain, p):
+    rng = np.random.default_rng(100 + p)
+    for trial in range(6):
+        n = int(rng.integers(p + 1, {1: 80, 2: 80, 3: 70, 4: 45, 5: 30, 6: 18}[p]))
+        lim = int(rng.choice([2, 5, 40, 127]))
+        X = random_case(rng, p, n, lim)
+        rows = X[rng.integers(0, n, size=3)]
+        unif = rng.integers(-lim, lim + 1, size=(3, p)).astype(np.int32)
+        _check_both(ctx, plain, X, np.vstack([rows, unif]))
+
+
+@pytest.mark.parametrize("p", [3, 4, 5, 6])
+def test_tie_heavy_small_grid(ctx, plain, p):
+    """Coordinates in {-2..2}: many equal directions, tight sets and duplicates."""
+    rng = np.random.default_rng(200 + p)
+    n = {3: 60, 4: 35, 5: 20, 6: 14}[p]
+    for trial in range(4):
+        X = rng.integers(-2, 3, size=(n, p)).astype(np.int32)
+        Z = np.vstack([X[:3], rng.integers(-1, 2, size=(3, p))]).astype(np.int32)
+        _check_both(ctx, plain, X, Z)
+
+
+@pytest.mark.parametrize("p,r", [(3, 1), (3, 2), (4, 2), (4, 3), (5, 3), (5, 4), (6, 4), (6, 5)])
+def test_rank_deficient(ctx, plain, p, r):
+    rng = np.random.default_rng(300 + 10 * p + r)
+    for trial in range(3):
+        B = rng.integers(-3, 4, size=(r, p))
+        n = int(rng.integers(r + 2, 24))
+        C = rng.integers(-4, 5, size=(n, r))
+        z = rng.integers(-3, 4, size=p)
+        X = (C @ B + z).astype(np.int32)
+        Z = np.vstack([z, X[0], X[1] + 1]).astype(np.int32)
+        _check_both(ctx, plain, X, Z)
+
+
+def test_edge_cases(ctx, plain, td):
+    X = np.array([[5, 5, 5]], np.int32)
+    _check_both(ctx, plain, X, np.array([[5, 5, 5], [0, 0, 0]], np.int32))       # n = 1
+    X = np.tile(np.array([[1, -2, 3, 4]], np.int32), (9, 1))
+    _check_both(ctx, plain, X, np.array([[1, -2, 3, 4], [1, -2, 3, 5]], np.int32))  # all equal
+    X = np.arange(12, dtype=np.int32).reshape(4, 3)                               # n <= p
+    _check_both(ctx, plain, X, np.array([[0, 0, 0], [3, 4, 5], [1, 2, 3]], np.int32))
+    out = ctx.depth(np.zeros((3, 2), np.int32), np.zeros((0, 2), np.int32))       # m = 0
+    assert out.shape == (0,)
+
+
+def test_golden_w1(ctx, plain):
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W1")
+    d = W.w1()
+    assert d.checksum() == g["checksum"]
+    want = np.array(g["T"])
+    assert np.array_equal(ctx.depth(d.X, d.Zq), want)
+    assert np.array_equal(plain.depth(d.X, d.Zq), want)
+
+
+@pytest.mark.parametrize("name", ["W2", "W4"])
+def test_golden_full_size(ctx, name):
+    """The full benchmark workloads, every query, in the launch form bench.py times."""
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden(name)
+    d = W.WORKLOADS[name]()
+    assert d.checksum() == g["checksum"]
+    got = ctx.depth(d.X, d.Zq)
+    assert np.array_equal(got, np.array(g["T"])), np.nonzero(got != np.array(g["T"]))
+    st = ctx.last_stats
+    assert st.sweeps > 0 and st.kernel_launches >= 4
+
+
+def test_golden_w4_plain_sample(plain):
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W4")
+    d = W.w4()
+    idx = np.array([0, 5, 20, 41, 129, 200])
+    got = plain.depth(d.X, d.Zq[idx])
+    assert np.array_equal(got, np.array(g["T"])[idx])
+
+
+def test_batched_matches_single(ctx, td):
+    rng = np.random.default_rng(7)
+    sets = []
+    for p in (1, 2, 3, 4, 5, 3, 4):
+        n = int(rng.integers(p + 2, 50 if p <= 4 else 25))
+        X = random_case(rng, p, n, 30)
+        Z = np.vstack([X[:2], rng.integers(-30, 31, size=(2, p))]).astype(np.int32)
+        sets.append((X, Z))
+    outs = ctx.depth_batched(sets)
+    for (X, Z), o in zip(sets, outs):
+        assert np.array_equal(o, oracle.depth_many(X, Z))
+
+
+def test_golden_w3_sample_batched(ctx):
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W3S")
+    sets = W.w3()
+    items = g["items"][:40]
+    batch = []
+    for it in items:
+        d = sets[it["index"]]
+        assert d.checksum() == it["checksum"]
+        batch.append((d.X, d.Zq))
+    outs = ctx.depth_batched(batch)
+    for it, o in zip(items, outs):
+        assert np.array_equal(o, np.array(it["T"]))
+
+
+def test_shards_merge_to_depth(td):
+    rng = np.random.default_rng(9)
+    X = random_case(rng, 4, 40, 20)
+    Z = np.vstack([X[:3], rng.integers(-20, 21, size=(3, 4))]).astype(np.int32)
+    want = oracle.depth_many(X, Z)
+    parts = []
+    for s in range(3):
+        c = td.Context(0, shard_index=s, shard_count=3)
+        parts.append(c.depth(X, Z).astype(np.int64))
+    assert np.array_equal(np.min(np.stack(parts), axis=0), want)
+
+
+def test_stream_api(td):
+    rng = np.random.default_rng(11)
+    ctx = td.Context(0)
+    s = ctx.stream(mem_budget_bytes=1 << 30)
+    reqs = []
+    for i in range(6):
+        p = int(rng.integers(3, 6))
+        n = int(rng.integers(20, 60 if p < 5 else 30))
+        X = random_case(rng, p, n, 50)
+        Z = np.vstack([X[:2], rng.integers(-50, 51, size=(2, p))]).astype(np.int32)
+        t = s.submit(X, Z)
+        assert t is not None
+        reqs.append((t, X, Z))
+    for t, X, Z in reqs:
+        out = s.wait(t, timeout_us=60_000_000)
+        assert np.array_equal(out, oracle.depth_many(X, Z))
+    # admission by memory: a budget too small for any request refuses it
+    tiny = ctx.stream(mem_budget_bytes=16)
+    assert tiny.submit(reqs[0][1], reqs[0][2]) is None
+
+
+def test_errors_leave_outputs_untouched(ctx, td):
+    X = np.array([[0, 0, 0], [2 ** 24, 0, 0]], np.int32)
+    Z = np.zeros((1, 3), np.int32)
+    out = np.full(1, -12345, np.int32)
+    with pytest.raises(td.TdError) as e:
+        ctx.depth(X, Z, out=out)
+    assert e.value.code == td.TD_ERR_RANGE
+    assert out[0] == -12345
+    with pytest.raises(td.TdError) as e:
+        ctx.depth(np.zeros((3, 7), np.int32), np.zeros((1, 7), np.int32))
+    assert e.value.code == td.TD_ERR_INVALID
+
+
+def test_device_pointers(td):
+    import torch
+    rng = np.random.default_rng(13)
+    X = random_case(rng, 4, 50, 40)
+    Z = np.vstack([X[:3], rng.integers(-40, 41, size=(3, 4))]).astype(np.int32)
+    want = oracle.depth_many(X, Z)
+    c = td.Context(0, device_pointers=True)
+    Xd = torch.from_numpy(X).cuda()
+    Zd = torch.from_numpy(Z).cuda()
+    got = c.depth(Xd, Zd).cpu().numpy()
+    assert np.array_equal(got, want)
+    got2 = c.depth(Xd, Zd).cpu().numpy()     # graph replay
+    assert np.array_equal(got2, want)

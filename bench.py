@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Benchmark of the exact Tukey depth hot path on GB300.
+
+One step = one td_depth call over the whole batch of queries of the
+workload: p = 4, n = 1000 data points round(40 N(0,1)) clipped to [-127,127],
+64 query points (32 data rows, the lower coordinate-wise median, 31 uniform
+points of the bounding box) -- C(1000, 2) = 499,500 subset sweeps per query
+(Algorithm 1 with Algorithm 2 as the inner count, exact under ties).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is subset sweeps/s with the inputs resident in
+device memory (CUDA events on the launch stream, L2 flushed between steps by
+writing a 512 MB buffer outside the timed events); `e2e` is the same metric
+through td_depth with host buffers (host<->device copies inside); the plain
+exact one-query-per-launch form is timed beside it; `cpu_baseline` is the CPU
+oracle on a bounded sample.  `--impl reference` times the CPU oracle alone.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "p=4 n=1000 m=64, round(40*N(0,1)) clipped to [-127,127], int32; C(1000,2) subsets/query"
+METRIC = "subset sweeps/sec"
+UNIT = "sweeps/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--plain-queries", type=int, default=8)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(rank):
+    from paper_1409_3901_gb300 import workloads as W
+    # weak scaling: rank r solves its own batch (seed 1 + r); rank 0 is the
+    # benchmark workload itself
+    return W.w2(seed=1 + rank)
+
+
+def _ops_per_sweep(nnz, p):
+    """Algorithmic work of one sweep: projection 2p, key ~6, comparison sort
+    ceil(log2 n') compare-exchanges at ~2 ops, O(1) walk: n'(2p+6+2ceil(log2 n'))."""
+    return nnz * (2 * p + 6 + 2 * math.ceil(math.log2(max(nnz, 2))))
+
+
+def _algorithmic_ops(d, sweeps_per_call):
+    """Sum over queries of C(n'_q, p-2) * ops(n'_q), scaled to the sweeps the
+    library reports (dependent subsets are skipped)."""
+    tot_ops, tot_sw = 0.0, 0.0
+    for z in d.Zq:
+        nnz = int(d.n - np.all(d.X == z, axis=1).sum())
+        sw = math.comb(nnz, d.p - 2)
+        tot_ops += sw * _ops_per_sweep(nnz, d.p)
+        tot_sw += sw
+    return tot_ops * (sweeps_per_call / tot_sw)
+
+
+class _Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def _traffic_for_current_kernel():
+    """DRAM bytes per launch of the sweep kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged since the capture."""
+    src = os.path.join(ROOT, "paper_1409_3901_gb300", "csrc", "td_kernels.cu")
+    path = os.path.join(ROOT, "profiles", "td_k_filtered_w2.json")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        rec = json.load(open(path))
+        if rec.get("kernel_source_sha") == h:
+            return rec.get("dram_bytes_per_launch_full")
+    except Exception:
+        pass
+    return None
+
+
+def _cpu_baseline(d, seconds):
+    """The CPU oracle, as it stands, on one host core: a bounded sample of the
+    same workload (the first subset positions of query 0)."""
+    import oracle
+    oracle.build()
+    z = d.Zq[0]
+    t = time.perf_counter()
+    oracle.depth_range(d.X, z, 0, 500)
+    rate = 500 / max(time.perf_counter() - t, 1e-6)
+    S = int(max(1000, min(rate * seconds, 2_000_000)))
+    t = time.perf_counter()
+    _, npos, ctr = oracle.depth_range(d.X, z, 0, S)
+    dt = time.perf_counter() - t
+    swept = ctr[0] - ctr[1]
+    return {"value": swept / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "query 0, subset positions [0, %d) of %d (%.1f s single-threaded)" % (S, npos, dt)}
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    d = _workload(0)
+    import oracle
+    oracle.build()
+    z = d.Zq[0]
+    t = time.perf_counter()
+    oracle.depth_range(d.X, z, 0, 300)
+    rate = 300 / max(time.perf_counter() - t, 1e-6)
+    # each step: a bounded sample sized so that warmup + steps end in ~2 minutes
+    per_step = max(200, int(rate * min(8.0, 120.0 / max(a.steps + a.warmup, 1))))
+    times, swept = [], 0
+    for s in range(a.warmup + a.steps):
+        q = d.Zq[s % d.m]
+        t = time.perf_counter()
+        _, npos, ctr = oracle.depth_range(d.X, q, 0, per_step)
+        dt = time.perf_counter() - t
+        if s >= a.warmup:
+            times.append(dt)
+            swept += ctr[0] - ctr[1]
+    total = sum(times)
+    value = swept / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i128",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": d.m, "seq_len": None, "parallelism": "cpu1"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                             "sample": "each step: subset positions [0, %d) of one query" % per_step},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1409_3901_gb300 import tukey
+
+    d = _workload(rank)
+    stream = torch.cuda.current_stream(dev)
+    ctx = tukey.Context(local, device_pointers=True, stream=stream.cuda_stream)
+    Xd = torch.from_numpy(d.X).to(dev)
+    Zd = torch.from_numpy(d.Zq).to(dev)
+    out = torch.empty(d.m, dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    for _ in range(a.warmup):
+        ctx.depth(Xd, Zd, out)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    clocks = _Clocks(local)
+    clocks.start()
+    evs = []
+    sweeps = 0
+    launches = 0
+    ms_sweep = 0.0
+    for _ in range(a.steps):
+        flush.fill_(1)                           # L2 flush, outside the events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.depth(Xd, Zd, out)
+        e1.record(stream)
+        evs.append((e0, e1))
+        st = ctx.last_stats
+        sweeps += st.sweeps
+        launches += st.kernel_launches
+        ms_sweep += st.ms_sweep
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms_steps = [e0.elapsed_time(e1) for e0, e1 in evs]
+    t_total = sum(ms_steps) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+        sw = torch.tensor([sweeps], device=dev, dtype=torch.float64)
+        dist.all_reduce(sw, op=dist.ReduceOp.SUM)
+        sweeps_all = float(sw.item())
+    else:
+        sweeps_all = float(sweeps)
+    value = sweeps_all / t_total
+    queries_per_s = ws * d.m * a.steps / t_total
+
+    # end to end through the public API with host buffers (copies inside)
+    host = tukey.Context(local, stream=stream.cuda_stream)
+    host.depth(d.X, d.Zq)
+    e2e_steps = max(3, min(a.steps, 5))
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    e2e_sweeps = 0
+    for _ in range(e2e_steps):
+        o = host.depth(d.X, d.Zq)
+        e2e_sweeps += host.last_stats.sweeps
+    e2e_t = time.perf_counter() - t
+    e2e = {"value": e2e_sweeps / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": int(d.X.nbytes + d.Zq.nbytes), "d2h_bytes_per_step": int(o.nbytes)}
+
+    # the plain exact one-query-per-launch form on the same GPU
+    plain = tukey.Context(local, mode=tukey.TD_MODE_PLAIN_EXACT, device_pointers=True,
+                          stream=stream.cuda_stream)
+    Zp = Zd[: a.plain_queries].contiguous()
+    outp = torch.empty(Zp.shape[0], dtype=torch.int32, device=dev)
+    plain.depth(Xd, Zp, outp)
+    pm, psw = 0.0, 0
+    for _ in range(2):
+        flush.fill_(1)
+        plain.depth(Xd, Zp, outp)
+        pm += plain.last_stats.ms
+        psw += plain.last_stats.sweeps
+    plain_rate = psw / (pm / 1e3)
+    same = bool(torch.equal(outp, out[: a.plain_queries]))
+
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peaks, kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(dev)
+    peak_tops = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12
+    ops_per_call = _algorithmic_ops(d, sweeps / a.steps)
+    if ms_sweep <= 0:
+        raise SystemExit("the library reported no sweep-kernel time")
+    achieved = ops_per_call * a.steps / (ms_sweep / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved / peak_tops, "traffic": _traffic_for_current_kernel(),
+                "kernel": "td_k_filtered", "kernel_ms": ms_sweep / a.steps,
+                "peak_basis": "%d SMs x 128 INT32/FP32 lanes x %.0f MHz (%s sm_max_mhz)"
+                              % (props.multi_processor_count, sm_max, kind),
+                "ops_per_sweep": "n'(2p+6+2ceil(log2 n'))"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * t_total / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64/i128", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": d.m * ws, "seq_len": None,
+                       "parallelism": "dp%d" % ws, "l2": "flushed between steps (512 MB write)"},
+            "queries_per_s": queries_per_s,
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+            "plain_exact": {"value": plain_rate, "unit": UNIT, "queries": int(Zp.shape[0]),
+                            "same_results": same, "speedup_filtered_over_plain": value / ws / plain_rate},
+            "stats_per_step": {k: v for k, v in ctx.last_stats.as_dict().items()},
+            "clocks": clk}
+    if not a.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(d, a.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.warmup < 3:
+        a.warmup = 3
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

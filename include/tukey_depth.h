@@ -111,6 +111,8 @@ typedef struct {
     uint64_t resolved_buckets;  /* sweeps whose extremum needed an exact in-bucket order */
     uint64_t kernel_launches;   /* CUDA kernels launched by the call */
     float ms;                   /* device time from first to last kernel of the call */
+    float ms_sweep;             /* device time of the sweep kernel(s) alone (CUDA events on the
+                                   launch stream around them) */
 } td_stats;
 
 /* Coordinate bound |X_ij - z_j| <= td_coord_limit(p) accepted for dimension p. */

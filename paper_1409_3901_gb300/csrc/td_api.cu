@@ -33,13 +33,11 @@ size_t td_plain_smem(int nmax, int pmax, int warps);
 int64_t td_scratch_per_warp(int nmax);
 cudaError_t td_launch_setup(const TdLaunch &L, cudaStream_t s);
 cudaError_t td_launch_tiles(const TdLaunch &L, cudaStream_t s);
-cudaError_t td_launch_filtered(const TdLaunch &L, int grid, size_t smem, cudaStream_t s);
-cudaError_t td_launch_plain(const TdLaunch &L, int q, int grid, size_t smem, cudaStream_t s);
+cudaError_t td_launch_filtered(int D, const TdLaunch &L, int grid, size_t smem, cudaStream_t s);
+cudaError_t td_launch_plain(int D, const TdLaunch &L, int q, int grid, size_t smem, cudaStream_t s);
 cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s);
-int td_filtered_occupancy(int warps, size_t smem);
-int td_plain_occupancy(int warps, size_t smem);
-cudaError_t td_prepare_filtered(size_t smem);
-cudaError_t td_prepare_plain(size_t smem);
+int td_filtered_occupancy(int D, int warps, size_t smem);
+int td_plain_occupancy(int D, int warps, size_t smem);
 
 namespace {
 
@@ -84,11 +82,11 @@ cudaError_t grow_host(HostBuf &b, size_t bytes)
 /* Device state of one batched call (or one stream request). */
 struct Work {
     DevBuf X, Zq, sets, q, order, prefix, tsize, ticket, qmin, out, ctr, scratch;
-    int grid_filtered = 0;
+    int grid[TD_NDIM] = { 0, 0, 0, 0, 0 }; /* persistent grid of the sweep kernel of dimension D = 2 + i */
 };
 
 struct GraphKey {
-    int nq, nsets, nmax, pmax, grid, blog2, spw;
+    int nq, nsets, nmax, pmax, grid[TD_NDIM], blog2, spw;
     size_t smem;
     const void *ptrs[13];
     int64_t shard_index, shard_count;
@@ -102,7 +100,7 @@ struct td_ctx {
     int sms = 0;
     td_options opt;
     cudaStream_t own = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
     Work w;
     HostBuf hstage, hout;
     std::string cuda_err;
@@ -238,9 +236,9 @@ cudaError_t alloc_work(Work &w, const Plan &P, int grid_warps, bool need_x_arena
     if ((e = grow(w.sets, (size_t)std::max(P.nsets, 1) * sizeof(TdSet))) != cudaSuccess) return e;
     if ((e = grow(w.q, (size_t)std::max(P.nq, 1) * sizeof(TdQuery))) != cudaSuccess) return e;
     if ((e = grow(w.order, (size_t)std::max(P.nq, 1) * 4)) != cudaSuccess) return e;
-    if ((e = grow(w.prefix, (size_t)(P.nq + 1) * 8)) != cudaSuccess) return e;
+    if ((e = grow(w.prefix, (size_t)TD_NDIM * (P.nq + 1) * 8)) != cudaSuccess) return e;
     if ((e = grow(w.tsize, (size_t)std::max(P.nq, 1) * 4)) != cudaSuccess) return e;
-    if ((e = grow(w.ticket, 64)) != cudaSuccess) return e;
+    if ((e = grow(w.ticket, (size_t)TD_NDIM * TD_TICKET_STRIDE * 8)) != cudaSuccess) return e;
     if ((e = grow(w.qmin, (size_t)std::max(P.nq, 1) * 4)) != cudaSuccess) return e;
     if ((e = grow(w.out, (size_t)std::max(P.nq, 1) * 4)) != cudaSuccess) return e;
     if ((e = grow(w.ctr, sizeof(TdCounters))) != cudaSuccess) return e;
@@ -249,10 +247,12 @@ cudaError_t alloc_work(Work &w, const Plan &P, int grid_warps, bool need_x_arena
     return cudaSuccess;
 }
 
+/* Histogram size of the sweep kernels (shared memory sizing): 2^blog2 angular
+ * buckets, at least 128 (four per lane, the 128-bit scan granularity). */
 int blog2_for(int nmax, const td_options &o)
 {
-    if (o.buckets_log2 > 0) return std::max(5, std::min(o.buckets_log2, 12));
-    int b = 5;
+    if (o.buckets_log2 > 0) return std::max(7, std::min(o.buckets_log2, 12));
+    int b = 7;
     while ((1 << b) < nmax && b < 11) ++b;
     return b;
 }
@@ -340,43 +340,70 @@ TdLaunch make_launch(const Work &w, const Plan &P, const int32_t *x_arena, const
     return L;
 }
 
-/* Enqueue the kernels of one call on stream s.  Returns launches issued. */
+/* Enqueue the kernels of one call on stream s.  Returns launches issued.
+ * ev_a / ev_b (may be null) are recorded around the sweep kernel(s).  The
+ * plain form needs each query's effective dimension, read back after the
+ * set-up kernel (so it is never captured in a graph). */
 int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, const td_options &o, int blog2,
-                    cudaStream_t s, int *launches)
+                    cudaStream_t s, int *launches, cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
 {
     int nl = 0;
     if (o.mode == TD_MODE_PLAIN_EXACT) {
         TdLaunch L = Lf;
         L.warps = kWarpsPlain;
         size_t smem = td_plain_smem(P.nmax, P.pmax, kWarpsPlain);
-        int occ = td_plain_occupancy(kWarpsPlain, smem);
-        if (occ < 1) return TD_ERR_INVALID;
-        int grid = ctx->sms * occ;
         TDCK(td_launch_setup(L, s));
         ++nl;
+        std::vector<TdQuery> hq(P.nq);
+        TDCK(cudaMemcpyAsync(hq.data(), w.q.p, P.nq * sizeof(TdQuery), cudaMemcpyDeviceToHost, s));
+        TDCK(cudaStreamSynchronize(s));
+        if (ev_a) TDCK(cudaEventRecord(ev_a, s));
         for (int q = 0; q < P.nq; ++q) {
-            TDCK(td_launch_plain(L, q, grid, smem, s));
+            const int D = hq[q].d;
+            if (hq[q].k < 0 || hq[q].hi <= hq[q].lo || D < 2 || D > 6) continue;
+            int occ = td_plain_occupancy(D, kWarpsPlain, smem);
+            if (occ < 1) return TD_ERR_INVALID;
+            TDCK(td_launch_plain(D, L, q, ctx->sms * occ, smem, s));
             ++nl;
         }
+        if (ev_b) TDCK(cudaEventRecord(ev_b, s));
         TDCK(td_launch_finalize(L, s));
         ++nl;
     } else {
         size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
         TDCK(td_launch_setup(Lf, s));
         TDCK(td_launch_tiles(Lf, s));
-        TDCK(td_launch_filtered(Lf, w.grid_filtered, smem, s));
+        nl = 2;
+        /* inside a stream capture only an "external" record becomes an event
+         * node of the graph; outside a capture the flag changes nothing */
+        if (ev_a) TDCK(cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
+        for (int D = 2; D <= std::min(P.pmax, 6); ++D) {
+            TDCK(td_launch_filtered(D, Lf, w.grid[D - 2], smem, s));
+            ++nl;
+        }
+        if (ev_b) TDCK(cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
         TDCK(td_launch_finalize(Lf, s));
-        nl = 4;
+        ++nl;
     }
     *launches = nl;
     return TD_OK;
 }
 
-int grid_filtered(td_ctx *ctx, const Plan &P, int blog2)
+/* Persistent grids of the sweep kernels (D = 2 .. min(pmax, 6)); sets the
+ * dynamic shared memory attribute of each.  Returns the largest total warp
+ * count (for the scratch), or 0 if a kernel cannot be resident. */
+int filtered_grids(td_ctx *ctx, const Plan &P, int blog2, int *grid)
 {
     size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
-    int occ = td_filtered_occupancy(kWarpsFiltered, smem);
-    return ctx->sms * occ;
+    int warps = 0;
+    for (int i = 0; i < TD_NDIM; ++i) grid[i] = 0;
+    for (int D = 2; D <= std::min(P.pmax, 6); ++D) {
+        int occ = td_filtered_occupancy(D, kWarpsFiltered, smem);
+        if (occ < 1) return 0;
+        grid[D - 2] = ctx->sms * occ;
+        warps = std::max(warps, grid[D - 2] * kWarpsFiltered);
+    }
+    return std::max(warps, 1);
 }
 
 /* One synchronous batched call. */
@@ -397,22 +424,20 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     const int blog2 = blog2_for(P.nmax, o);
     int grid = 0, warps_total = 0;
     (void)cudaGetLastError(); /* clear any stale error of an earlier call */
+    int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
     if (o.mode == TD_MODE_PLAIN_EXACT) {
         size_t smem = td_plain_smem(P.nmax, P.pmax, kWarpsPlain);
-        TDCK(td_prepare_plain(smem));
-        int occ = td_plain_occupancy(kWarpsPlain, smem);
+        int occ = 0;
+        for (int D = 2; D <= 6; ++D) occ = std::max(occ, td_plain_occupancy(D, kWarpsPlain, smem));
         if (occ < 1) return TD_ERR_INVALID;
         grid = ctx->sms * occ;
         warps_total = grid * kWarpsPlain;
     } else {
-        size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
-        TDCK(td_prepare_filtered(smem));
-        grid = grid_filtered(ctx, P, blog2);
-        if (grid < 1) return TD_ERR_INVALID;
-        warps_total = grid * kWarpsFiltered;
+        warps_total = filtered_grids(ctx, P, blog2, grids);
+        if (warps_total < 1) return TD_ERR_INVALID;
     }
     TDCK(alloc_work(ctx->w, P, warps_total, true));
-    ctx->w.grid_filtered = grid;
+    memcpy(ctx->w.grid, grids, sizeof(grids));
     const int32_t *x_arena = nullptr;
     int rc = stage_inputs(ctx, ctx->w, ctx->hstage, P, sets, k, devptr, s, &x_arena);
     if (rc != TD_OK) return rc;
@@ -427,7 +452,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         key.nsets = P.nsets;
         key.nmax = P.nmax;
         key.pmax = P.pmax;
-        key.grid = grid;
+        memcpy(key.grid, grids, sizeof(grids));
         key.blog2 = blog2;
         key.spw = o.subsets_per_warp;
         key.smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
@@ -450,7 +475,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
                 return fail_cuda(ctx, e, "cudaStreamBeginCapture");
             }
             int nl = 0;
-            int rc2 = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, cs, &nl);
+            int rc2 = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, cs, &nl, ctx->evs0, ctx->evs1);
             e = cudaStreamEndCapture(cs, &g);
             cudaStreamDestroy(cs);
             if (rc2 != TD_OK) {
@@ -467,7 +492,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         TDCK(cudaGraphLaunch(ctx->gexec, s));
         launches = 4;
     } else {
-        rc = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, s, &launches);
+        rc = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, s, &launches, ctx->evs0, ctx->evs1);
         if (rc != TD_OK) return rc;
     }
     TDCK(cudaEventRecord(ctx->ev1, s));
@@ -513,9 +538,11 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         st->tight_exceptions = C.tight;
         st->resolved_buckets = C.resolved;
         st->kernel_launches = (uint64_t)launches;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        float ms = 0.f, mss = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) != cudaSuccess) ms = -1.f;
+        if (cudaEventElapsedTime(&mss, ctx->evs0, ctx->evs1) != cudaSuccess) mss = -1.f;
         st->ms = ms;
+        st->ms_sweep = mss;
     }
     return TD_OK;
 }
@@ -571,6 +598,8 @@ extern "C" int td_create(td_ctx **out, int device, const td_options *opt)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->evs0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->evs1);
     if (e != cudaSuccess) {
         int rc = fail_cuda(ctx, e, "td_create");
         td_destroy(ctx);
@@ -605,6 +634,8 @@ extern "C" int td_destroy(td_ctx *ctx)
     if (ctx->hout.p) cudaFreeHost(ctx->hout.p);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->evs0) cudaEventDestroy(ctx->evs0);
+    if (ctx->evs1) cudaEventDestroy(ctx->evs1);
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
     return TD_OK;
@@ -724,8 +755,9 @@ extern "C" int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *tic
     const int blog2 = blog2_for(P.nmax, o);
     int grid = 0;
     (void)cudaGetLastError();
+    int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
     if (P.nq > 0) {
-        grid = grid_filtered(ctx, P, blog2);
+        grid = filtered_grids(ctx, P, blog2, grids);
         if (grid < 1) {
             delete r;
             return TD_ERR_INVALID;
@@ -733,7 +765,7 @@ extern "C" int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *tic
     }
     cudaError_t e = alloc_work(r->w, P, 0, true);
     if (e == cudaSuccess) {
-        size_t sc = (size_t)grid * kWarpsFiltered * (size_t)td_scratch_per_warp(TD_MAX_N);
+        size_t sc = (size_t)grid * (size_t)td_scratch_per_warp(TD_MAX_N);
         e = grow(s->scratch, sc);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
@@ -742,7 +774,7 @@ extern "C" int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *tic
         free_req(r);
         return fail_cuda(ctx, e, "td_stream_submit");
     }
-    r->w.grid_filtered = grid;
+    memcpy(r->w.grid, grids, sizeof(grids));
     const int32_t *x_arena = nullptr;
     int rc = TD_OK;
     if (P.nq > 0) {

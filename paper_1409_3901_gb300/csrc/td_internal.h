@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #define TD_MAXD 6
+#define TD_NDIM 5            /* effective dimensions 2..6 with a subset loop */
+#define TD_TICKET_STRIDE 16  /* work counters 128 bytes apart */
 
 /* Per-query state written by the set-up kernel (one per query). */
 struct TdQuery {
@@ -45,9 +47,9 @@ struct TdLaunch {
     int32_t nq;              /* number of queries */
     int32_t warps;           /* warps per CTA */
     const int32_t *order;    /* work order of the queries (a permutation of [0, nq)) */
-    int64_t *tile_prefix;    /* nq + 1 prefix sums of tiles, in work order */
+    int64_t *tile_prefix;    /* TD_NDIM x (nq + 1) prefix sums of tiles, per dimension, in work order */
     int32_t *tile_size;      /* subsets per tile, per query */
-    unsigned long long *ticket;  /* work-queue counter */
+    unsigned long long *ticket;  /* work-queue counters, one per dimension (stride TD_TICKET_STRIDE) */
     int32_t *qmin;           /* per-query minimum of V(S) over the processed subsets */
     int32_t *out;            /* per-query output */
     TdCounters *ctr;

@@ -61,6 +61,18 @@
 /* unit roundoff of binary32 */
 #define TD_U (1.0f / 16777216.0f)
 
+/* int64 -> binary32 off the FP64 pipe: exact-to-nearest when the value fits
+ * 32 bits, else hi * 2^32 + lo with two roundings (relative error <= 2u,
+ * covered by the error bounds below). */
+__device__ __forceinline__ float td_i64_to_f32(int64_t v)
+{
+    int32_t lo32 = (int32_t)v;
+    if ((int64_t)lo32 == v) return __int2float_rn(lo32);
+    int32_t hi = (int32_t)(v >> 32);
+    uint32_t lo = (uint32_t)v;
+    return __fadd_rn(__int2float_rn(hi) * 4294967296.0f, __uint2float_rn(lo));
+}
+
 /* ====================================================================== */
 /* per-warp global scratch for the exact tight-set path                    */
 /* ====================================================================== */
@@ -534,41 +546,54 @@ __host__ __device__ inline int td_auto_spw(int nnz)
     return s < 4 ? 4 : (s > 64 ? 64 : s);
 }
 
+/* Tiles of every query, and for each effective dimension D = 2..6 the prefix
+ * sums of the tiles of the queries of that dimension in work order
+ * (tile_prefix[(D-2)*(nq+1) + j]); resets the work counters. */
 __global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
 {
-    __shared__ int64_t s_part[1024];
+    __shared__ int64_t s_part[TD_NDIM][1024];
     const int nq = L.nq;
     const int T = blockDim.x;
     const int per = (nq + T - 1) / T;
     const int beg = min((int)threadIdx.x * per, nq), end = min(beg + per, nq);
-    int64_t sum = 0;
+    int64_t sum[TD_NDIM] = { 0, 0, 0, 0, 0 };
     for (int j = beg; j < end; ++j) {
-        const TdQuery &Q = L.q[L.order[j]];
+        const int q = L.order[j];
+        const TdQuery &Q = L.q[q];
         int spw = L.spw > 0 ? L.spw : td_auto_spw(Q.nnz);
         int64_t ts = (int64_t)spw * L.warps;
-        L.tile_size[L.order[j]] = (int)ts;
+        L.tile_size[q] = (int)ts;
         int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? (Q.hi - Q.lo + ts - 1) / ts : 0;
-        sum += cnt;
+        if (Q.d >= 2 && Q.d <= 6) sum[Q.d - 2] += cnt;
     }
-    s_part[threadIdx.x] = sum;
+#pragma unroll
+    for (int D = 0; D < TD_NDIM; ++D) s_part[D][threadIdx.x] = sum[D];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < TD_NDIM) {
+        const int D = threadIdx.x;
         int64_t acc = 0;
         for (int t = 0; t < T; ++t) {
-            int64_t v = s_part[t];
-            s_part[t] = acc;
+            int64_t v = s_part[D][t];
+            s_part[D][t] = acc;
             acc += v;
         }
-        L.tile_prefix[nq] = acc;
-        *L.ticket = 0ull;
+        L.tile_prefix[(int64_t)D * (nq + 1) + nq] = acc;
+        L.ticket[D * TD_TICKET_STRIDE] = 0ull;
     }
     __syncthreads();
-    int64_t acc = s_part[threadIdx.x];
+    int64_t acc[TD_NDIM];
+#pragma unroll
+    for (int D = 0; D < TD_NDIM; ++D) acc[D] = s_part[D][threadIdx.x];
     for (int j = beg; j < end; ++j) {
-        L.tile_prefix[j] = acc;
-        const TdQuery &Q = L.q[L.order[j]];
-        int64_t ts = L.tile_size[L.order[j]];
-        acc += (Q.k >= 0 && Q.hi > Q.lo) ? (Q.hi - Q.lo + ts - 1) / ts : 0;
+        const int q = L.order[j];
+        const TdQuery &Q = L.q[q];
+        const int64_t ts = L.tile_size[q];
+        const int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? (Q.hi - Q.lo + ts - 1) / ts : 0;
+#pragma unroll
+        for (int D = 0; D < TD_NDIM; ++D) {
+            L.tile_prefix[(int64_t)D * (nq + 1) + j] = acc[D];
+            if (Q.d == D + 2) acc[D] += cnt;
+        }
     }
 }
 
@@ -704,11 +729,20 @@ __device__ __forceinline__ void td_exact_y(const TdBasis<D> &B, const float (&x)
     }
 }
 
+/* Histogram layout.  Lane l scans the per = B/32 consecutive buckets
+ * [l*per, (l+1)*per) as per/4 chunks of four; chunk c of lane l is stored at
+ * chunk position c XOR (l mod per/4), so that the lanes of a quarter warp read
+ * distinct bank quads (no shared-memory bank conflicts in the scans). */
+__device__ __forceinline__ int td_phys(int b, int lp, int chm)
+{
+    return b ^ (((b >> lp) & chm) << 2);
+}
+
 /* Exact placement of the points the FP32 filter could not certify (their ids
  * are in W.glist[0..nu)): exact projection from the published basis; zero
  * projections are tight points, the others go to their exact bucket. */
 template <int D>
-__device__ __forceinline__ void td_exact_pass(const float *xs, int PS, const uint32_t *hist_unused,
+__device__ __forceinline__ void td_exact_pass(const float *xs, int PS, int lp, int chm,
                                            uint32_t *hist, uint16_t *bid, const uint16_t *list, int nu,
                                            const int64_t *qa, const int64_t *qb, int B, int lane,
                                            int *A_out, int *t_out)
@@ -731,12 +765,12 @@ __device__ __forceinline__ void td_exact_pass(const float *xs, int PS, const uin
         }
         int64_t h1, h2;
         bool plus = td_normalise(Y1, Y2, h1, h2);
-        float key = td_key((float)h1, (float)h2);
+        float key = td_key(td_i64_to_f32(h1), td_i64_to_f32(h2));
         int bb = (int)(key * (float)(B >> 1));
         bb = max(0, min(bb, B - 1));
         int b = td_exact_bucket(h1, h2, bb, B);
         bid[i] = (uint16_t)b;
-        atomicAdd(&hist[b], plus ? 0x10000u : 1u);
+        atomicAdd(&hist[td_phys(b, lp, chm)], plus ? 0x10000u : 1u);
         A += plus;
     }
     *A_out = td_wsum(A);
@@ -794,7 +828,7 @@ __device__ __forceinline__ void td_publish_basis(const TdBasis<D> &Bs, const int
 template <int D>
 __device__ __noinline__ void td_resolve_many(const float *xs, int PS, const int64_t *qa, const int64_t *qb,
                                              const uint32_t *hist, const uint16_t *bid, uint16_t *glist,
-                                             int G, int lane, int *mn_io, int *mx_io)
+                                             int G, int lp, int chm, int lane, int *mn_io, int *mx_io)
 {
     int npad = td_pow2_at_least(G);
     for (int l = G + lane; l < npad; l += 32) glist[l] = (uint16_t)TD_SENT;
@@ -831,7 +865,7 @@ __device__ __noinline__ void td_resolve_many(const float *xs, int PS, const int6
         int j = 0;
         while (j < G) {
             int bk = bid[glist[j]];
-            int v = (int)(hist[bk] & 0xFFFFu);
+            int v = (int)(hist[td_phys(bk, lp, chm)] & 0xFFFFu);
             while (j < G && bid[glist[j]] == bk) {
                 int64_t g1, g2;
                 bool gp;
@@ -864,7 +898,10 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
                                  const TdWarpSmem &W, int blog2, int lane, TdWarpStats &st,
                                  int &t_out, int &nzy_out)
 {
-    const int B = 1 << blog2;
+    const int B = 1 << blog2;               /* blog2 >= 7: at least 4 buckets per lane */
+    const int lp = blog2 - 5;               /* log2 buckets per lane */
+    const int nch = 1 << (lp - 2);          /* chunks of four per lane */
+    const int chm = nch - 1;
     const float halfB = (float)(B >> 1);
     const float E = fmaxf(Ea, Eb);
     const unsigned below = (1u << lane) - 1u;
@@ -898,7 +935,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
         nu += __popc(bu);
         if (valid && ok) {
             W.bid[i] = (uint16_t)b;
-            atomicAdd(&W.hist[b], plus ? 0x10000u : 1u);
+            atomicAdd(&W.hist[td_phys(b, lp, chm)], plus ? 0x10000u : 1u);
             A += plus;
         }
     }
@@ -907,7 +944,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
     if (nu > 0) {
         __syncwarp();
         int Ae = 0;
-        td_exact_pass<D>(xs, PS, nullptr, W.hist, W.bid, W.glist, nu, W.qa, W.qb, B, lane, &Ae, &t);
+        td_exact_pass<D>(xs, PS, lp, chm, W.hist, W.bid, W.glist, nu, W.qa, W.qb, B, lane, &Ae, &t);
         A += Ae;
     }
     if (lane == 0) {
@@ -919,25 +956,32 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
     nzy_out = nzy;
     __syncwarp();
 
-    /* walk values at the bucket boundaries */
-    const int per = B >> 5;
-    uint32_t *hl = W.hist + lane * per;
+    /* walk values at the bucket boundaries (conflict-free 128-bit scans) */
+    uint4 *h4 = reinterpret_cast<uint4 *>(W.hist) + lane * nch;
+    const int sw = lane & chm;
     uint32_t acc = 0;
-    for (int j = 0; j < per; ++j) acc += hl[j];
+    for (int c = 0; c < nch; ++c) {
+        const uint4 v = h4[c ^ sw];
+        acc += v.x + v.y + v.z + v.w;
+    }
     const int net = (int)(acc & 0xFFFFu) - (int)(acc >> 16);
     const int excl = td_wscan_incl(net, lane) - net;
     int P = A + excl;
     int mn = INT_MAX, mx = INT_MIN, lo = INT_MAX, hi = INT_MIN;
-    for (int j = 0; j < per; ++j) {
-        uint32_t w = hl[j];
-        int cp = (int)(w & 0xFFFFu), cm = (int)(w >> 16);
-        mn = min(mn, P);
-        mx = max(mx, P);
-        if (cp && cm) {
-            lo = min(lo, P - cm);
-            hi = max(hi, P + cp);
+    for (int c = 0; c < nch; ++c) {
+        const uint4 v = h4[c ^ sw];
+        const uint32_t w4[4] = { v.x, v.y, v.z, v.w };
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int cp = (int)(w4[k] & 0xFFFFu), cm = (int)(w4[k] >> 16);
+            mn = min(mn, P);
+            mx = max(mx, P);
+            if (cp && cm) {
+                lo = min(lo, P - cm);
+                hi = max(hi, P + cp);
+            }
+            P += cp - cm;
         }
-        P += cp - cm;
     }
     mn = min(mn, P);
     mx = max(mx, P);
@@ -950,12 +994,17 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
     if (need_lo || need_hi) {
         if (lane == 0) st.resolved++;
         P = A + excl;
-        for (int j = 0; j < per; ++j) {
-            uint32_t w = hl[j];
-            int cp = (int)(w & 0xFFFFu), cm = (int)(w >> 16);
-            bool cand = cp && cm && ((need_lo && P - cm < mn) || (need_hi && P + cp > mx));
-            hl[j] = cand ? (0x80000000u | (uint32_t)P) : 0u;
-            P += cp - cm;
+        for (int c = 0; c < nch; ++c) {
+            const uint4 v = h4[c ^ sw];
+            uint32_t w4[4] = { v.x, v.y, v.z, v.w };
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int cp = (int)(w4[k] & 0xFFFFu), cm = (int)(w4[k] >> 16);
+                const bool cand = cp && cm && ((need_lo && P - cm < mn) || (need_hi && P + cp > mx));
+                w4[k] = cand ? (0x80000000u | (uint32_t)P) : 0u;
+                P += cp - cm;
+            }
+            h4[c ^ sw] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
         }
         __syncwarp();
         int G = 0;
@@ -964,7 +1013,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
             bool g = false;
             if (i < nnz) {
                 uint16_t b = W.bid[i];
-                g = b != TD_SENT && (W.hist[b] >> 31);
+                g = b != TD_SENT && (W.hist[td_phys(b, lp, chm)] >> 31);
             }
             const unsigned bg = __ballot_sync(TD_FULL, g);
             if (g) W.glist[G + __popc(bg & below)] = (uint16_t)i;
@@ -985,7 +1034,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
                 const bool pl = td_normalise(Y1, Y2, h1, h2);
                 e = pl ? -1 : 1;
                 bk = W.bid[i];
-                Pb = (int)(W.hist[bk] & 0xFFFFu);
+                Pb = (int)(W.hist[td_phys(bk, lp, chm)] & 0xFFFFu);
             }
 #pragma unroll 1
             for (int size = 2; size <= 32; size <<= 1)
@@ -1035,17 +1084,12 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
             mn2 = min(mn2, td_wmin(vmn));
             mx2 = max(mx2, td_wmax(vmx));
         } else {
-            td_resolve_many<D>(xs, PS, W.qa, W.qb, W.hist, W.bid, W.glist, G, lane, &mn2, &mx2);
+            td_resolve_many<D>(xs, PS, W.qa, W.qb, W.hist, W.bid, W.glist, G, lp, chm, lane, &mn2, &mx2);
         }
         __syncwarp();
-        for (int l = lane; l < G; l += 32) W.hist[W.bid[W.glist[l]]] = 0u;
+        for (int l = lane; l < G; l += 32) W.hist[td_phys(W.bid[W.glist[l]], lp, chm)] = 0u;
     } else {
-        if (per >= 4) {
-            uint4 *h4 = reinterpret_cast<uint4 *>(hl);
-            for (int j = 0; j < (per >> 2); ++j) h4[j] = make_uint4(0u, 0u, 0u, 0u);
-        } else {
-            for (int j = 0; j < per; ++j) hl[j] = 0u;
-        }
+        for (int c = 0; c < nch; ++c) h4[c ^ sw] = make_uint4(0u, 0u, 0u, 0u);
     }
     __syncwarp();
     return min(mn2, nzy - mx2);
@@ -1145,16 +1189,17 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
         int64_t Aa = 0, Ab = 0;
 #pragma unroll
         for (int t = 0; t < D; ++t) {
-            fa[t] = (float)Bs.qa[t];
-            fb[t] = (float)Bs.qb[t];
+            fa[t] = td_i64_to_f32(Bs.qa[t]);
+            fb[t] = td_i64_to_f32(Bs.qb[t]);
             Aa += (Bs.qa[t] < 0 ? -Bs.qa[t] : Bs.qa[t]) * (int64_t)mx[t];
             Ab += (Bs.qb[t] < 0 ? -Bs.qb[t] : Bs.qb[t]) * (int64_t)mx[t];
         }
-        /* forward error bound of the FP32 fma chain: (D + 1) u sum |q_i x_i|,
-         * taken as (D + 2) u with the rounding of the sum covered by the
-         * extra factor 1 + 2^-10 */
-        const float cst = (float)(D + 2) * TD_U * 1.0009765625f;
-        const float Ea = (float)Aa * cst, Eb = (float)Ab * cst;
+        /* forward error bound of the FP32 projection: the fma chain adds at
+         * most D u sum |q_i x_i|, the rounded coefficients (at most 2u each,
+         * see td_i64_to_f32) 2u more; taken as (D + 3) u, with the rounding of
+         * the bound itself covered by the extra factor 1 + 2^-10 */
+        const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
+        const float Ea = td_i64_to_f32(Aa) * cst, Eb = td_i64_to_f32(Ab) * cst;
         int t, nzy;
         const int G = td_sweep_filtered<D>(xs, PS, nnz, Bs, fa, fb, Ea, Eb, W, blog2, lane, st, t, nzy);
         int V = G;
@@ -1170,32 +1215,42 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
 /* persistent filtered kernel                                              */
 /* ====================================================================== */
 
-__device__ __forceinline__ int td_query_of_tile(const TdLaunch &L, int64_t tile)
+__device__ __forceinline__ int td_query_of_tile(const int64_t *prefix, int nq, int64_t tile)
 {
-    int lo = 0, hi = L.nq - 1;
+    int lo = 0, hi = nq - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (L.tile_prefix[mid] <= tile) lo = mid;
+        if (prefix[mid] <= tile) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-__global__ void __launch_bounds__(256, 1) td_k_filtered(TdLaunch L)
+/* Persistent sweep kernel for the queries of effective dimension D: CTAs pop
+ * (query, subset-tile) work from the dimension's counter until it runs dry;
+ * the points of the current query stay staged in shared memory; every warp
+ * sweeps its share of the tile's subsets; one atomicMin per tile. */
+template <int D>
+__global__ void __launch_bounds__(256, (D <= 4 ? 2 : 1)) td_k_filtered(TdLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_tile;
     __shared__ int s_tmp[32];
     __shared__ int s_best[TD_WARPS_MAX];
+    const int64_t *prefix = L.tile_prefix + (int64_t)(D - 2) * (L.nq + 1);
+    unsigned long long *ticket = L.ticket + (D - 2) * TD_TICKET_STRIDE;
+    const int64_t total = prefix[L.nq];
+    if (total == 0) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nmaxp = td_pow2_at_least(L.nmax);
     const int PS = L.pmax <= 4 ? 4 : 8;
     const int blog2_cap = L.blog2;
-    /* layout: xs [nmax][PS] floats | per warp: hist [B] u32, bid [nmaxp] u16, glist [nmaxp] u16, gcount */
+    /* layout: xs [nmax][PS] floats | per warp: hist [B] u32, bid [nmaxp] u16,
+     * glist [nmaxp] u16, gcount, basis (qa, qb, meta) */
     float *xs = reinterpret_cast<float *>(smem);
-    size_t off = ((size_t)L.nmax * PS * 4 + 15) & ~(size_t)15;
+    const size_t off = ((size_t)L.nmax * PS * 4 + 15) & ~(size_t)15;
     const int Bmax = 1 << blog2_cap;
-    size_t per_warp = ((size_t)Bmax * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    const size_t per_warp = ((size_t)Bmax * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     unsigned char *wb = smem + off + per_warp * w;
     TdWarpSmem W;
     W.hist = reinterpret_cast<uint32_t *>(wb);
@@ -1210,37 +1265,32 @@ __global__ void __launch_bounds__(256, 1) td_k_filtered(TdLaunch L)
     const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, nmaxp);
     TdWarpStats st = { 0, 0, 0, 0, 0, 0, 0 };
     int staged = -1;
-    const int64_t total = L.tile_prefix[L.nq];
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(L.ticket, 1ull);
+        if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(ticket, 1ull);
         __syncthreads();
         const int64_t tile = s_tile;
         if (tile >= total) break;
-        const int j = td_query_of_tile(L, tile);
+        const int j = td_query_of_tile(prefix, L.nq, tile);
         const int q = L.order[j];
         if (q != staged) {
             td_stage_points(L, q, xs, PS, s_tmp);
             staged = q;
         }
         const TdQuery &Q = L.q[q];
-        const int nnz = Q.nnz, d = Q.d;
+        const int nnz = Q.nnz;
         const int64_t ts = L.tile_size[q];
-        const int64_t t0 = Q.lo + (tile - L.tile_prefix[j]) * ts;
+        const int64_t t0 = Q.lo + (tile - prefix[j]) * ts;
         const int64_t t1 = min(t0 + ts, Q.hi);
         const int64_t spw = ts / (blockDim.x >> 5);
         const uint64_t r0 = (uint64_t)min(t0 + spw * w, t1), r1 = (uint64_t)min(t0 + spw * (w + 1), t1);
-        /* buckets: about one per nonzero point, at least 32 */
-        int blog2 = 5;
+        /* buckets: about one per nonzero point, at least 128 (four per lane) */
+        int blog2 = 7;
         while ((1 << blog2) < nnz && blog2 < blog2_cap) ++blog2;
         int best = L.qmin[q];
-        switch (d) {
-        case 2: td_warp_filtered<2>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
-        case 3: td_warp_filtered<3>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
-        case 4: td_warp_filtered<4>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
-        case 5: td_warp_filtered<5>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
-        case 6: td_warp_filtered<6>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st); break;
-        default: if (lane == 0) st.errors++; break;
-        }
+        if (Q.d == D && blog2 <= blog2_cap && nnz <= L.nmax)
+            td_warp_filtered<D>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st);
+        else if (lane == 0)
+            st.errors++; /* inconsistent sizes: skip, the host reports TD_ERR_INTERNAL */
         if (lane == 0) s_best[w] = best;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1329,6 +1379,7 @@ __device__ void td_warp_plain(const TdLaunch &L, int q, const int32_t *xi, int P
     }
 }
 
+template <int D>
 __global__ void __launch_bounds__(128, 1) td_k_plain(TdLaunch L, int q)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1395,14 +1446,8 @@ __global__ void __launch_bounds__(128, 1) td_k_plain(TdLaunch L, int q)
         const int64_t t0 = Q.lo + tile * ts, t1 = min(t0 + ts, Q.hi);
         const int64_t spw = ts / nw;
         const uint64_t r0 = (uint64_t)min(t0 + spw * w, t1), r1 = (uint64_t)min(t0 + spw * (w + 1), t1);
-        switch (d) {
-        case 2: td_warp_plain<2>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
-        case 3: td_warp_plain<3>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
-        case 4: td_warp_plain<4>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
-        case 5: td_warp_plain<5>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
-        case 6: td_warp_plain<6>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st); break;
-        default: if (lane == 0) st.errors++; break;
-        }
+        if (d == D) td_warp_plain<D>(L, q, xi, PSI, nnz, r0, r1, H, idx, gcount, wqa, wqb, wmeta, scr, lane, best, st);
+        else if (lane == 0) st.errors++;
     }
     if (lane == 0) s_best[w] = best;
     __syncthreads();
@@ -1480,25 +1525,50 @@ cudaError_t td_launch_tiles(const TdLaunch &L, cudaStream_t s)
 
 /* The dynamic shared memory attribute is set to exactly what a launch uses
  * (td_prepare_*), before any stream capture; the launches do not touch it. */
-cudaError_t td_prepare_filtered(size_t smem)
+typedef void (*td_kfn)(TdLaunch);
+typedef void (*td_kfn_plain)(TdLaunch, int);
+
+static td_kfn td_filtered_fn(int D)
 {
-    return cudaFuncSetAttribute(td_k_filtered, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    switch (D) {
+    case 2: return td_k_filtered<2>;
+    case 3: return td_k_filtered<3>;
+    case 4: return td_k_filtered<4>;
+    case 5: return td_k_filtered<5>;
+    default: return td_k_filtered<6>;
+    }
 }
 
-cudaError_t td_prepare_plain(size_t smem)
+static td_kfn_plain td_plain_fn(int D)
 {
-    return cudaFuncSetAttribute(td_k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    switch (D) {
+    case 2: return td_k_plain<2>;
+    case 3: return td_k_plain<3>;
+    case 4: return td_k_plain<4>;
+    case 5: return td_k_plain<5>;
+    default: return td_k_plain<6>;
+    }
 }
 
-cudaError_t td_launch_filtered(const TdLaunch &L, int grid, size_t smem, cudaStream_t s)
+cudaError_t td_prepare_filtered(int D, size_t smem)
 {
-    td_k_filtered<<<grid, L.warps * 32, smem, s>>>(L);
+    return cudaFuncSetAttribute(td_filtered_fn(D), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t td_prepare_plain(int D, size_t smem)
+{
+    return cudaFuncSetAttribute(td_plain_fn(D), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t td_launch_filtered(int D, const TdLaunch &L, int grid, size_t smem, cudaStream_t s)
+{
+    td_filtered_fn(D)<<<grid, L.warps * 32, smem, s>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t td_launch_plain(const TdLaunch &L, int q, int grid, size_t smem, cudaStream_t s)
+cudaError_t td_launch_plain(int D, const TdLaunch &L, int q, int grid, size_t smem, cudaStream_t s)
 {
-    td_k_plain<<<grid, L.warps * 32, smem, s>>>(L, q);
+    td_plain_fn(D)<<<grid, L.warps * 32, smem, s>>>(L, q);
     return cudaGetLastError();
 }
 
@@ -1508,18 +1578,20 @@ cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s)
     return cudaGetLastError();
 }
 
-int td_filtered_occupancy(int warps, size_t smem)
+int td_filtered_occupancy(int D, int warps, size_t smem)
 {
     int blocks = 0;
-    if (td_prepare_filtered(smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_k_filtered, warps * 32, smem) != cudaSuccess) return 0;
+    if (td_prepare_filtered(D, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_filtered_fn(D), warps * 32, smem) != cudaSuccess)
+        return 0;
     return blocks;
 }
 
-int td_plain_occupancy(int warps, size_t smem)
+int td_plain_occupancy(int D, int warps, size_t smem)
 {
     int blocks = 0;
-    if (td_prepare_plain(smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_k_plain, warps * 32, smem) != cudaSuccess) return 0;
+    if (td_prepare_plain(D, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_plain_fn(D), warps * 32, smem) != cudaSuccess)
+        return 0;
     return blocks;
 }

@@ -59,7 +59,8 @@ class td_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_uint64), ("skipped_dependent", ctypes.c_uint64),
                 ("filtered_points", ctypes.c_uint64), ("exact_points", ctypes.c_uint64),
                 ("tight_exceptions", ctypes.c_uint64), ("resolved_buckets", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint64), ("ms", ctypes.c_float)]
+                ("kernel_launches", ctypes.c_uint64), ("ms", ctypes.c_float),
+                ("ms_sweep", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

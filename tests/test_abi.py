@@ -76,7 +76,7 @@ def test_create_reports_missing_device(tukey):
 def test_structs_match_header_layout(tukey):
     assert ctypes.sizeof(tukey.td_options) == 4 * 6 + 8 * 2 + 8
     assert ctypes.sizeof(tukey.td_dataset) == 8 + 8 + 8 + 8 + 8
-    assert ctypes.sizeof(tukey.td_stats) == 7 * 8 + 8
+    assert ctypes.sizeof(tukey.td_stats) == 7 * 8 + 4 + 4
 
 
 def test_workload_generators_are_deterministic():

@@ -745,9 +745,9 @@ template <int D>
 __device__ __forceinline__ void td_exact_pass(const float *xs, int PS, int lp, int chm,
                                            uint32_t *hist, uint16_t *bid, const uint16_t *list, int nu,
                                            const int64_t *qa, const int64_t *qb, int B, int lane,
-                                           int *A_out, int *t_out)
+                                           int *t_out)
 {
-    int A = 0, t = 0;
+    int t = 0;
     for (int l = lane; l < nu; l += 32) {
         int i = list[l];
         const float *xp = xs + (size_t)i * PS;
@@ -771,9 +771,7 @@ __device__ __forceinline__ void td_exact_pass(const float *xs, int PS, int lp, i
         int b = td_exact_bucket(h1, h2, bb, B);
         bid[i] = (uint16_t)b;
         atomicAdd(&hist[td_phys(b, lp, chm)], plus ? 0x10000u : 1u);
-        A += plus;
     }
-    *A_out = td_wsum(A);
     *t_out = td_wsum(t);
 }
 
@@ -890,12 +888,23 @@ __device__ __noinline__ void td_resolve_many(const float *xs, int PS, const int6
 }
 
 /* G(S) for one subset, FP32-filtered (the basis must be published to
- * W.qa/W.qb first).  Also returns the number t of tight points (nonzero
- * points of span S) and the number of nonzero projections. */
+ * W.qa/W.qb first).  Returns G(S) exactly whenever G(S) < best; otherwise it
+ * may return any value >= best (the subset cannot lower the minimum, so the
+ * exact in-bucket order is not resolved).  Also returns the number t of tight
+ * points (nonzero points of span S) and the number of nonzero projections.
+ *
+ * FP32 certification of a point's bucket: with E >= |y_f - y| (both
+ * coordinates), |y2_f| > E fixes the orientation, and for s = |y1_f|+|y2_f| > 4E
+ * the pseudo-angle key = 1 - h1/(|h1|+h2) of the exact point differs from the
+ * computed one by at most E/(s-2E) <= 2E/s (the key is 1/s-Lipschitz in the
+ * max norm of its argument) plus at most ~10 rounding errors of values <= 2
+ * (reciprocal within 2 ulp, products, sums, the +-delta below); delta =
+ * 2E/s + 24u covers both.  The bucket floor(key * B/2) is certain when
+ * floor((key - delta) B/2) == floor((key + delta) B/2) and lies in [0, B). */
 template <int D>
 __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis<D> &Bs,
                                  const float (&fa)[D], const float (&fb)[D], float Ea, float Eb,
-                                 const TdWarpSmem &W, int blog2, int lane, TdWarpStats &st,
+                                 const TdWarpSmem &W, int blog2, int lane, int best, TdWarpStats &st,
                                  int &t_out, int &nzy_out)
 {
     const int B = 1 << blog2;               /* blog2 >= 7: at least 4 buckets per lane */
@@ -904,13 +913,16 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
     const int chm = nch - 1;
     const float halfB = (float)(B >> 1);
     const float E = fmaxf(Ea, Eb);
+    const float E4 = 4.0f * E;
+    const float cE = 2.0f * E * halfB;
+    const float cU = 24.0f * TD_U * halfB;
     const unsigned below = (1u << lane) - 1u;
-    int A = 0, nu = 0;
-    for (int i0 = 0; i0 < nnz; i0 += 32) {
-        const int i = i0 + lane;
-        const bool valid = i < nnz;
+    (void)below;
+    if (lane == 0) *W.gcount = 0;
+    __syncwarp();
+    auto place = [&](int i) {
         float x[D];
-        td_load_point<D>(xs, PS, valid ? i : 0, x);
+        td_load_point<D>(xs, PS, i, x);
         float y1 = fa[0] * x[0], y2 = fb[0] * x[0];
 #pragma unroll
         for (int r = 1; r < D; ++r) {
@@ -918,34 +930,33 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
             y2 = fmaf(fb[r], x[r], y2);
         }
         const float s = fabsf(y1) + fabsf(y2);
-        bool ok = (fabsf(y2) > Eb) && (s > 4.0f * E);
         const bool plus = y2 > 0.0f;
-        const float h1 = plus ? y1 : -y1;
         const float r = __fdividef(1.0f, s);
-        const float key = 1.0f - h1 * r;
-        const float delta = fmaf(2.0f * E, r, 16.0f * TD_U);
-        const float bf = key * halfB;
-        int b = max(0, min((int)bf, B - 1));
-        const float frac = bf - (float)b;
-        const float dB = delta * halfB;
-        if ((b > 0 && frac <= dB) || (b < B - 1 && frac >= 1.0f - dB)) ok = false;
-        const bool unc = valid && !ok;
-        const unsigned bu = __ballot_sync(TD_FULL, unc);
-        if (unc) W.glist[nu + __popc(bu & below)] = (uint16_t)i;
-        nu += __popc(bu);
-        if (valid && ok) {
-            W.bid[i] = (uint16_t)b;
-            atomicAdd(&W.hist[td_phys(b, lp, chm)], plus ? 0x10000u : 1u);
-            A += plus;
+        const float rh = r * (plus ? halfB : -halfB);
+        const float kb = fmaf(-y1, rh, halfB);  /* key * B/2 */
+        const float db = fmaf(cE, r, cU);       /* delta * B/2 */
+        const int blo = __float2int_rd(kb - db), bhi = __float2int_rd(kb + db);
+        const bool ok = (fabsf(y2) > Eb) & (s > E4) & (blo == bhi) & ((unsigned)blo < (unsigned)B);
+        if (ok) {
+            W.bid[i] = (uint16_t)blo;
+            atomicAdd(&W.hist[td_phys(blo, lp, chm)], plus ? 0x10000u : 1u);
+        } else {
+            const int slot = atomicAdd(W.gcount, 1);
+            W.glist[slot] = (uint16_t)i;
         }
+    };
+    int i = lane;
+    for (; i + 32 < nnz; i += 64) {
+        place(i);
+        place(i + 32);
     }
-    A = td_wsum(A);
+    if (i < nnz) place(i);
+    __syncwarp();
+    const int nu = *W.gcount;
     int t = 0;
     if (nu > 0) {
         __syncwarp();
-        int Ae = 0;
-        td_exact_pass<D>(xs, PS, lp, chm, W.hist, W.bid, W.glist, nu, W.qa, W.qb, B, lane, &Ae, &t);
-        A += Ae;
+        td_exact_pass<D>(xs, PS, lp, chm, W.hist, W.bid, W.glist, nu, W.qa, W.qb, B, lane, &t);
     }
     if (lane == 0) {
         st.exact += nu;
@@ -956,143 +967,220 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
     nzy_out = nzy;
     __syncwarp();
 
-    /* walk values at the bucket boundaries (conflict-free 128-bit scans) */
+    /* Pass 1: per-lane totals of the +1/-1 events, i.e. a histogram of 32
+     * coarse buckets.  Inside lane l's range the walk stays within
+     * [P_l - c-_l, P_l + c+_l], which bounds G from below. */
     uint4 *h4 = reinterpret_cast<uint4 *>(W.hist) + lane * nch;
     const int sw = lane & chm;
+    const int per = B >> 5;
     uint32_t acc = 0;
     for (int c = 0; c < nch; ++c) {
         const uint4 v = h4[c ^ sw];
         acc += v.x + v.y + v.z + v.w;
     }
-    const int net = (int)(acc & 0xFFFFu) - (int)(acc >> 16);
-    const int excl = td_wscan_incl(net, lane) - net;
-    int P = A + excl;
-    int mn = INT_MAX, mx = INT_MIN, lo = INT_MAX, hi = INT_MIN;
-    for (int c = 0; c < nch; ++c) {
-        const uint4 v = h4[c ^ sw];
-        const uint32_t w4[4] = { v.x, v.y, v.z, v.w };
+    const int cpl = (int)(acc & 0xFFFFu), cml = (int)(acc >> 16);
+    const int A = td_wsum(cml); /* orientation + points: one -1 event each */
+    const int netl = cpl - cml;
+    const int excl = td_wscan_incl(netl, lane) - netl;
+    const int Pl = A + excl;
+    const int lol = Pl - cml, hil = Pl + cpl;
+    int G = min(td_wmin(lol), nzy - td_wmax(hil));
+    if (G < best) {
+        /* Pass 2, only over the lanes whose range could hold a walk value
+         * giving less than best (cooperatively, one bucket per lane, when
+         * they are few): the walk value at every bucket boundary, and the
+         * in-bucket bounds of buckets holding both event signs.  The values
+         * left out are all >= best on the side they could affect. */
+        const unsigned cl = __ballot_sync(TD_FULL, lol < best || hil > nzy - best);
+        const bool coop = __popc(cl) <= 8;
+        int mn = INT_MAX, mx = INT_MIN, lo = INT_MAX, hi = INT_MIN;
+        if (coop) {
+            unsigned rest = cl;
+            while (rest) {
+                const int L = __ffs(rest) - 1;
+                rest &= rest - 1;
+                int carry = __shfl_sync(TD_FULL, Pl, L);
+                for (int base = 0; base < per; base += 32) {
+                    const int tt = base + lane;
+                    const bool v = tt < per;
+                    const uint32_t w = v ? W.hist[td_phys(L * per + tt, lp, chm)] : 0u;
+                    const int cp = (int)(w & 0xFFFFu), cm = (int)(w >> 16);
+                    const int nt = cp - cm;
+                    const int inc = td_wscan_incl(nt, lane);
+                    const int Pb = carry + inc - nt;
+                    if (v) {
+                        mn = min(mn, Pb);
+                        mx = max(mx, Pb);
+                        if (cp && cm) {
+                            lo = min(lo, Pb - cm);
+                            hi = max(hi, Pb + cp);
+                        }
+                    }
+                    carry += __shfl_sync(TD_FULL, inc, 31);
+                }
+                mn = min(mn, carry);
+                mx = max(mx, carry);
+            }
+        } else {
+            int P = Pl;
+            for (int c = 0; c < nch; ++c) {
+                const uint4 v = h4[c ^ sw];
+                const uint32_t w4[4] = { v.x, v.y, v.z, v.w };
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int cp = (int)(w4[k] & 0xFFFFu), cm = (int)(w4[k] >> 16);
+                for (int k = 0; k < 4; ++k) {
+                    const int cp = (int)(w4[k] & 0xFFFFu), cm = (int)(w4[k] >> 16);
+                    mn = min(mn, P);
+                    mx = max(mx, P);
+                    if (cp && cm) {
+                        lo = min(lo, P - cm);
+                        hi = max(hi, P + cp);
+                    }
+                    P += cp - cm;
+                }
+            }
             mn = min(mn, P);
             mx = max(mx, P);
-            if (cp && cm) {
-                lo = min(lo, P - cm);
-                hi = max(hi, P + cp);
-            }
-            P += cp - cm;
         }
-    }
-    mn = min(mn, P);
-    mx = max(mx, P);
-    mn = td_wmin(mn);
-    mx = td_wmax(mx);
-    lo = td_wmin(lo);
-    hi = td_wmax(hi);
-    const bool need_lo = lo < mn, need_hi = hi > mx;
-    int mn2 = mn, mx2 = mx;
-    if (need_lo || need_hi) {
-        if (lane == 0) st.resolved++;
-        P = A + excl;
-        for (int c = 0; c < nch; ++c) {
-            const uint4 v = h4[c ^ sw];
-            uint32_t w4[4] = { v.x, v.y, v.z, v.w };
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int cp = (int)(w4[k] & 0xFFFFu), cm = (int)(w4[k] >> 16);
-                const bool cand = cp && cm && ((need_lo && P - cm < mn) || (need_hi && P + cp > mx));
-                w4[k] = cand ? (0x80000000u | (uint32_t)P) : 0u;
-                P += cp - cm;
-            }
-            h4[c ^ sw] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-        }
-        __syncwarp();
-        int G = 0;
-        for (int i0 = 0; i0 < nnz; i0 += 32) {
-            const int i = i0 + lane;
-            bool g = false;
-            if (i < nnz) {
-                uint16_t b = W.bid[i];
-                g = b != TD_SENT && (W.hist[td_phys(b, lp, chm)] >> 31);
-            }
-            const unsigned bg = __ballot_sync(TD_FULL, g);
-            if (g) W.glist[G + __popc(bg & below)] = (uint16_t)i;
-            G += __popc(bg);
-        }
-        __syncwarp();
-        if (G <= 32) {
-            /* one gathered event per lane: exact direction, warp bitonic sort
-             * by (bucket, direction), segmented walk */
-            int bk = INT_MAX, e = 0, Pb = 0;
-            int64_t h1 = 0, h2 = 0;
-            if (lane < G) {
-                const int i = W.glist[lane];
-                float xg[D];
-                td_load_point<D>(xs, PS, i, xg);
-                int64_t Y1, Y2;
-                td_exact_y<D>(Bs, xg, Y1, Y2);
-                const bool pl = td_normalise(Y1, Y2, h1, h2);
-                e = pl ? -1 : 1;
-                bk = W.bid[i];
-                Pb = (int)(W.hist[td_phys(bk, lp, chm)] & 0xFFFFu);
-            }
-#pragma unroll 1
-            for (int size = 2; size <= 32; size <<= 1)
-#pragma unroll 1
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    const int obk = __shfl_xor_sync(TD_FULL, bk, stride);
-                    const int oe = __shfl_xor_sync(TD_FULL, e, stride);
-                    const int oPb = __shfl_xor_sync(TD_FULL, Pb, stride);
-                    const int64_t oh1 = __shfl_xor_sync(TD_FULL, h1, stride);
-                    const int64_t oh2 = __shfl_xor_sync(TD_FULL, h2, stride);
-                    bool o_less, m_less;
-                    if (obk != bk) {
-                        o_less = obk < bk;
-                        m_less = bk < obk;
-                    } else if (bk == INT_MAX) {
-                        o_less = m_less = false;
-                    } else {
-                        const int cs = td_cross_sign(h1, h2, oh1, oh2);
-                        m_less = cs > 0;
-                        o_less = cs < 0;
-                    }
-                    const bool up = (lane & size) == 0;
-                    const bool lower = (lane & stride) == 0;
-                    const bool take = (lower == up) ? o_less : m_less;
-                    if (take) {
-                        bk = obk;
-                        e = oe;
-                        Pb = oPb;
-                        h1 = oh1;
-                        h2 = oh2;
+        mn = td_wmin(mn);
+        mx = td_wmax(mx);
+        lo = td_wmin(lo);
+        hi = td_wmax(hi);
+        /* a side is resolved only if its in-bucket range can pass the
+         * boundary extremes and could give a value below best; an unresolved
+         * side keeps its bound (exact when no bucket can pass the extremes,
+         * >= best otherwise) */
+        const bool need_lo = lo < mn && lo < best;
+        const bool need_hi = hi > mx && hi > nzy - best;
+        int mn2 = min(mn, lo), mx2 = max(mx, hi);
+        if (need_lo) mn2 = mn;
+        if (need_hi) mx2 = mx;
+        if (need_lo || need_hi) {
+            if (lane == 0) st.resolved++;
+            /* flag the candidate buckets with their start value (counts stay
+             * below 2^15, so bit 31 is free) */
+            auto cand = [&](int Pb, int cp, int cm) -> bool {
+                return cp && cm && ((need_lo && Pb - cm < mn) || (need_hi && Pb + cp > mx));
+            };
+            if (coop) {
+                unsigned rest = cl;
+                while (rest) {
+                    const int L = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    int carry = __shfl_sync(TD_FULL, Pl, L);
+                    for (int base = 0; base < per; base += 32) {
+                        const int tt = base + lane;
+                        const bool v = tt < per;
+                        const int ph = td_phys(L * per + tt, lp, chm);
+                        const uint32_t w = v ? W.hist[ph] : 0u;
+                        const int cp = (int)(w & 0xFFFFu), cm = (int)(w >> 16);
+                        const int nt = cp - cm;
+                        const int inc = td_wscan_incl(nt, lane);
+                        const int Pb = carry + inc - nt;
+                        if (v && cand(Pb, cp, cm)) W.hist[ph] = 0x80000000u | (uint32_t)Pb;
+                        carry += __shfl_sync(TD_FULL, inc, 31);
                     }
                 }
-            const int nbk = __shfl_down_sync(TD_FULL, bk, 1);
-            const int64_t nh1 = __shfl_down_sync(TD_FULL, h1, 1);
-            const int64_t nh2 = __shfl_down_sync(TD_FULL, h2, 1);
-            const int pbk = __shfl_up_sync(TD_FULL, bk, 1);
-            const bool valid = lane < G;
-            const bool tie_next = valid && lane + 1 < G && nbk == bk && td_cross_sign(h1, h2, nh1, nh2) == 0;
-            const bool head = valid && (lane == 0 || pbk != bk);
-            const int S = td_wscan_incl(valid ? e : 0, lane);
-            const int hidx = td_wscan_max_incl(head ? lane : 0, lane);
-            const int Shead = __shfl_sync(TD_FULL, S, hidx);
-            const int ehead = __shfl_sync(TD_FULL, e, hidx);
-            const int val = Pb + (S - (Shead - ehead));
-            const int vmn = (valid && !tie_next) ? val : INT_MAX;
-            const int vmx = (valid && !tie_next) ? val : INT_MIN;
-            mn2 = min(mn2, td_wmin(vmn));
-            mx2 = max(mx2, td_wmax(vmx));
-        } else {
-            td_resolve_many<D>(xs, PS, W.qa, W.qb, W.hist, W.bid, W.glist, G, lp, chm, lane, &mn2, &mx2);
+            } else {
+                int P = Pl;
+                for (int c = 0; c < nch; ++c) {
+                    const uint4 v = h4[c ^ sw];
+                    uint32_t w4[4] = { v.x, v.y, v.z, v.w };
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int cp = (int)(w4[k] & 0xFFFFu), cm = (int)(w4[k] >> 16);
+                        if (cand(P, cp, cm)) w4[k] = 0x80000000u | (uint32_t)P;
+                        P += cp - cm;
+                    }
+                    h4[c ^ sw] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                }
+            }
+            __syncwarp();
+            int Gn = 0;
+            for (int i0 = 0; i0 < nnz; i0 += 32) {
+                const int i = i0 + lane;
+                bool g = false;
+                if (i < nnz) {
+                    uint16_t b = W.bid[i];
+                    g = b != TD_SENT && (W.hist[td_phys(b, lp, chm)] >> 31);
+                }
+                const unsigned bg = __ballot_sync(TD_FULL, g);
+                if (g) W.glist[Gn + __popc(bg & below)] = (uint16_t)i;
+                Gn += __popc(bg);
+            }
+            __syncwarp();
+            if (Gn <= 32) {
+                /* one gathered event per lane: exact direction, warp bitonic
+                 * sort by (bucket, direction), segmented walk */
+                int bk = INT_MAX, e = 0, Pb = 0;
+                int64_t h1 = 0, h2 = 0;
+                if (lane < Gn) {
+                    const int i = W.glist[lane];
+                    float xg[D];
+                    td_load_point<D>(xs, PS, i, xg);
+                    int64_t Y1, Y2;
+                    td_exact_y<D>(Bs, xg, Y1, Y2);
+                    const bool pl = td_normalise(Y1, Y2, h1, h2);
+                    e = pl ? -1 : 1;
+                    bk = W.bid[i];
+                    Pb = (int)(W.hist[td_phys(bk, lp, chm)] & 0xFFFFu);
+                }
+#pragma unroll 1
+                for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll 1
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        const int obk = __shfl_xor_sync(TD_FULL, bk, stride);
+                        const int oe = __shfl_xor_sync(TD_FULL, e, stride);
+                        const int oPb = __shfl_xor_sync(TD_FULL, Pb, stride);
+                        const int64_t oh1 = __shfl_xor_sync(TD_FULL, h1, stride);
+                        const int64_t oh2 = __shfl_xor_sync(TD_FULL, h2, stride);
+                        bool o_less, m_less;
+                        if (obk != bk) {
+                            o_less = obk < bk;
+                            m_less = bk < obk;
+                        } else if (bk == INT_MAX) {
+                            o_less = m_less = false;
+                        } else {
+                            const int cs = td_cross_sign(h1, h2, oh1, oh2);
+                            m_less = cs > 0;
+                            o_less = cs < 0;
+                        }
+                        const bool up = (lane & size) == 0;
+                        const bool lower = (lane & stride) == 0;
+                        const bool take = (lower == up) ? o_less : m_less;
+                        if (take) {
+                            bk = obk;
+                            e = oe;
+                            Pb = oPb;
+                            h1 = oh1;
+                            h2 = oh2;
+                        }
+                    }
+                const int nbk = __shfl_down_sync(TD_FULL, bk, 1);
+                const int64_t nh1 = __shfl_down_sync(TD_FULL, h1, 1);
+                const int64_t nh2 = __shfl_down_sync(TD_FULL, h2, 1);
+                const int pbk = __shfl_up_sync(TD_FULL, bk, 1);
+                const bool valid = lane < Gn;
+                const bool tie_next = valid && lane + 1 < Gn && nbk == bk && td_cross_sign(h1, h2, nh1, nh2) == 0;
+                const bool head = valid && (lane == 0 || pbk != bk);
+                const int S = td_wscan_incl(valid ? e : 0, lane);
+                const int hidx = td_wscan_max_incl(head ? lane : 0, lane);
+                const int Shead = __shfl_sync(TD_FULL, S, hidx);
+                const int ehead = __shfl_sync(TD_FULL, e, hidx);
+                const int val = Pb + (S - (Shead - ehead));
+                const int vmn = (valid && !tie_next) ? val : INT_MAX;
+                const int vmx = (valid && !tie_next) ? val : INT_MIN;
+                mn2 = min(mn2, td_wmin(vmn));
+                mx2 = max(mx2, td_wmax(vmx));
+            } else {
+                td_resolve_many<D>(xs, PS, W.qa, W.qb, W.hist, W.bid, W.glist, Gn, lp, chm, lane, &mn2, &mx2);
+            }
         }
-        __syncwarp();
-        for (int l = lane; l < G; l += 32) W.hist[td_phys(W.bid[W.glist[l]], lp, chm)] = 0u;
-    } else {
-        for (int c = 0; c < nch; ++c) h4[c ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+        G = min(mn2, nzy - mx2);
     }
     __syncwarp();
-    return min(mn2, nzy - mx2);
+    for (int c = 0; c < nch; ++c) h4[c ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    return G;
 }
 
 /* Tight-set correction m_S after a sweep.  Tight points are those with bucket
@@ -1201,7 +1289,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
         const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
         const float Ea = td_i64_to_f32(Aa) * cst, Eb = td_i64_to_f32(Ab) * cst;
         int t, nzy;
-        const int G = td_sweep_filtered<D>(xs, PS, nnz, Bs, fa, fb, Ea, Eb, W, blog2, lane, st, t, nzy);
+        const int G = td_sweep_filtered<D>(xs, PS, nnz, Bs, fa, fb, Ea, Eb, W, blog2, lane, best, st, t, nzy);
         int V = G;
         if (t > K && G < best) {
             if (lane == 0) st.tight++;

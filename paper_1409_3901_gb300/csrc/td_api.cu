@@ -490,7 +490,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
             ctx->gvalid = true;
         }
         TDCK(cudaGraphLaunch(ctx->gexec, s));
-        launches = 4;
+        launches = 3 + std::min(P.pmax, 6) - 1; /* set-up, tiles, sweeps for D = 2..min(p,6), finalize */
     } else {
         rc = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, s, &launches, ctx->evs0, ctx->evs1);
         if (rc != TD_OK) return rc;

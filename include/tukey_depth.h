@@ -154,6 +154,35 @@ int td_stream_poll(td_stream *s, uint64_t ticket, int *done);
 int td_stream_wait(td_stream *s, uint64_t ticket, int64_t timeout_us);
 int td_stream_destroy(td_stream *s);
 
+/* Allocation-free depth (no counterpart in the paper; a deployment need).
+ * For callers that must not allocate device memory: code running under a
+ * framework whose memory pool owns the GPU, processes with a device-memory
+ * budget fixed when they load, or latency-critical paths where cudaMalloc
+ * and cudaFree would synchronise the device.  Same operation and results as
+ * td_depth, but needs no context and calls no allocating routine: X (n x p),
+ * Z (m x p) and out (m) are DEVICE pointers of the current device, used on
+ * `stream` (a cudaStream_t; NULL = the default stream); every other buffer is
+ * carved out of one file-scope __device__ array of TD_NOALLOC_BYTES bytes
+ * that each GPU loading this library holds until the process exits.
+ *   - Limits: n <= TD_NOALLOC_MAX_N, m <= TD_NOALLOC_MAX_M (TD_ERR_INVALID
+ *     beyond them: the array has no room), p <= TD_MAX_P, and the coordinate
+ *     limit of td_coord_limit (TD_ERR_RANGE, checked on the device).
+ *   - The first call on a device looks the array up (cudaGetSymbolAddress)
+ *     and so loads the module there; make that first call before any stream
+ *     capture.
+ *   - Returns after the results are in out (it synchronises `stream`); on an
+ *     error out is left untouched.
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     host threads, or other streams still running an earlier call) race and
+ *     must be serialised by the caller.  The sweep uses at most
+ *     TD_NOALLOC_CTAS thread blocks. */
+#define TD_NOALLOC_MAX_N 512
+#define TD_NOALLOC_MAX_M 4096
+#define TD_NOALLOC_CTAS 80
+#define TD_NOALLOC_BYTES (24u << 20)
+int td_depth_noalloc(const int32_t *X, int32_t n, int32_t p, const int32_t *Z, int32_t m,
+                     int32_t *out, void *stream);
+
 const char *td_strerror(int code);
 /* Text of the last CUDA error seen by this context (empty if none). */
 const char *td_last_cuda_error(td_ctx *ctx);

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtukeydepth.so")
-SOURCES = ["td_kernels.cu", "td_api.cu"]
+SOURCES = ["td_kernels.cu", "td_api.cu", "td_noalloc.cu"]
 HEADERS = ["td_internal.h", "td_exact.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "550"]

@@ -86,6 +86,7 @@ def _load():
         "td_stream_destroy": (ctypes.c_int, [vp]),
         "td_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "td_last_cuda_error": (ctypes.c_char_p, [vp]),
+        "td_depth_noalloc": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -110,10 +111,14 @@ td_stream_wait = lib.td_stream_wait
 td_stream_destroy = lib.td_stream_destroy
 td_strerror = lib.td_strerror
 td_last_cuda_error = lib.td_last_cuda_error
+td_depth_noalloc = lib.td_depth_noalloc
+TD_NOALLOC_MAX_N = 512
+TD_NOALLOC_MAX_M = 4096
 
 EXPORTED = ["td_coord_limit", "td_create", "td_set_options", "td_destroy", "td_depth",
             "td_depth_batched", "td_stream_create", "td_stream_submit", "td_stream_poll",
-            "td_stream_wait", "td_stream_destroy", "td_strerror", "td_last_cuda_error"]
+            "td_stream_wait", "td_stream_destroy", "td_strerror", "td_last_cuda_error",
+            "td_depth_noalloc"]
 
 
 def _check(rc, ctx=None):

@@ -558,7 +558,7 @@ extern "C" int64_t td_coord_limit(int32_t p)
     switch (p) {
     case 1:
     case 2:
-    case 3: return 16777215; /* 2^24 - 1: coordinates exact in binary32 */
+    case 3: return 4194303; /* 2^22 - 1: exact in binary32 and in the magic-constant conversion */
     case 4: return 524287;   /* 4 * 2 M^2 * M < 2^62 */
     case 5: return 16383;    /* 5 * 3^(3/2) M^3 * M < 2^62 */
     case 6: return 2047;     /* 6 * (2M)^4 * M < 2^62 */

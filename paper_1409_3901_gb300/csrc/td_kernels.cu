@@ -723,7 +723,7 @@ __device__ __forceinline__ void td_exact_y(const TdBasis<D> &B, const float (&x)
     y2 = 0;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-        int64_t xv = (int64_t)x[r];
+        const int64_t xv = td_f2i(x[r]);
         y1 += B.qa[r] * xv;
         y2 += B.qb[r] * xv;
     }
@@ -754,7 +754,7 @@ __device__ __forceinline__ void td_exact_pass(const float *xs, int PS, int lp, i
         int64_t Y1 = 0, Y2 = 0;
 #pragma unroll
         for (int r = 0; r < D; ++r) {
-            int64_t xv = (int64_t)xp[r];
+            const int64_t xv = td_f2i(xp[r]);
             Y1 += qa[r] * xv;
             Y2 += qb[r] * xv;
         }
@@ -784,7 +784,7 @@ __device__ __forceinline__ void td_exact_h(const float *xs, int PS, int i, const
     int64_t Y1 = 0, Y2 = 0;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-        int64_t xv = (int64_t)xp[r];
+        const int64_t xv = td_f2i(xp[r]);
         Y1 += qa[r] * xv;
         Y2 += qb[r] * xv;
     }
@@ -935,8 +935,11 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
         const float rh = r * (plus ? halfB : -halfB);
         const float kb = fmaf(-y1, rh, halfB);  /* key * B/2 */
         const float db = fmaf(cE, r, cU);       /* delta * B/2 */
-        const int blo = __float2int_rd(kb - db), bhi = __float2int_rd(kb + db);
-        const bool ok = (fabsf(y2) > Eb) & (s > E4) & (blo == bhi) & ((unsigned)blo < (unsigned)B);
+        /* floors by the magic-constant addition (|kb -+ db| <= 2^22 whenever
+         * s > 4E, since then db < B/2); garbage otherwise, but then ok fails */
+        const int flo = td_floor_bits(kb - db), fhi = td_floor_bits(kb + db);
+        const int blo = flo - 0x4B400000;
+        const bool ok = (fabsf(y2) > Eb) & (s > E4) & (flo == fhi) & ((unsigned)blo < (unsigned)B);
         if (ok) {
             W.bid[i] = (uint16_t)blo;
             atomicAdd(&W.hist[td_phys(blo, lp, chm)], plus ? 0x10000u : 1u);
@@ -1201,7 +1204,7 @@ __device__ __noinline__ int td_tight_correction(const int *meta, const float *xs
             return H[2 * i] == 0 && H[2 * i + 1] == 0;
         };
         auto coord = [&](int i, int r) -> int64_t {
-            if (xs) return (int64_t)xs[(size_t)i * PS + r];
+            if (xs) return td_f2i(xs[(size_t)i * PS + r]);
             return (int64_t)xi[(size_t)i * PSI + r];
         };
         int rows[K];
@@ -1258,16 +1261,8 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     for (int r = 0; r < D; ++r) mx[r] = Q.mx[r];
     for (uint64_t r = r0; r < r1; ++r) {
         if (r > r0) td_next_colex<K>(c);
-        int64_t s[K > 0 ? K : 1][D];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            float xj[D];
-            td_load_point<D>(xs, PS, c[j], xj);
-#pragma unroll
-            for (int t = 0; t < D; ++t) s[j][t] = (int64_t)xj[t];
-        }
         TdBasis<D> Bs;
-        if (!td_make_basis<D>(s, Bs)) {
+        if (!td_make_basis_coop<D>(xs, PS, c, lane, Bs)) {
             if (lane == 0) st.dependent++;
             continue;
         }

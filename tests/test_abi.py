@@ -44,7 +44,7 @@ def test_library_exports_every_declared_symbol(tukey):
 def test_coord_limits_and_strerror(tukey):
     lim = [tukey.td_coord_limit(p) for p in range(0, 8)]
     assert lim[0] == 0 and lim[7] == 0
-    assert lim[1] == lim[2] == lim[3] == 2 ** 24 - 1
+    assert lim[1] == lim[2] == lim[3] == 2 ** 22 - 1
     # every exact intermediate fits: d * max|minor| * M < 2^62
     assert 4 * 2 * lim[4] ** 3 < 2 ** 62
     assert 5 * 3 ** 1.5 * lim[5] ** 4 < 2 ** 62

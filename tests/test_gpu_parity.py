@@ -178,7 +178,7 @@ def test_stream_api(td):
 
 
 def test_errors_leave_outputs_untouched(ctx, td):
-    X = np.array([[0, 0, 0], [2 ** 24, 0, 0]], np.int32)
+    X = np.array([[0, 0, 0], [2 ** 22, 0, 0]], np.int32)
     Z = np.zeros((1, 3), np.int32)
     out = np.full(1, -12345, np.int32)
     with pytest.raises(td.TdError) as e:

@@ -248,12 +248,13 @@ cudaError_t alloc_work(Work &w, const Plan &P, int grid_warps, bool need_x_arena
 }
 
 /* Histogram size of the sweep kernels (shared memory sizing): 2^blog2 angular
- * buckets, at least 128 (four per lane, the 128-bit scan granularity). */
+ * buckets, about one per two points and at least 128 (four per lane, the
+ * 128-bit scan granularity). */
 int blog2_for(int nmax, const td_options &o)
 {
     if (o.buckets_log2 > 0) return std::max(7, std::min(o.buckets_log2, 12));
     int b = 7;
-    while ((1 << b) < nmax && b < 11) ++b;
+    while ((2 << b) < nmax && b < 11) ++b;
     return b;
 }
 

@@ -652,6 +652,9 @@ __device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int PS, int 
         }
         ++o;
     }
+    /* zero rows up to the next multiple of 128 (the sweep loads them unmasked) */
+    const int nnz = Q.nnz, npad = (nnz + 127) & ~127;
+    for (int k = nnz * PS + (int)threadIdx.x; k < npad * PS; k += T) xs[k] = 0.f;
     __syncthreads();
     return Q.nnz;
 }
@@ -729,13 +732,16 @@ __device__ __forceinline__ void td_exact_y(const TdBasis<D> &B, const float (&x)
     }
 }
 
-/* Histogram layout.  Lane l scans the per = B/32 consecutive buckets
- * [l*per, (l+1)*per) as per/4 chunks of four; chunk c of lane l is stored at
- * chunk position c XOR (l mod per/4), so that the lanes of a quarter warp read
- * distinct bank quads (no shared-memory bank conflicts in the scans). */
+/* Histogram layout: bucket b at word b.  Lane l owns the per = B/32 buckets
+ * [l*per, (l+1)*per).  The scans that run on every sweep (per-lane totals,
+ * clearing) visit a lane's chunks of four in the rotated order c = (k + l)
+ * mod per/4, so that the lanes of a quarter warp touch distinct bank quads;
+ * only the rare in-order pass reads them in order. */
 __device__ __forceinline__ int td_phys(int b, int lp, int chm)
 {
-    return b ^ (((b >> lp) & chm) << 2);
+    (void)lp;
+    (void)chm;
+    return b;
 }
 
 /* Exact placement of the points the FP32 filter could not certify (their ids
@@ -913,49 +919,71 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
     const int chm = nch - 1;
     const float halfB = (float)(B >> 1);
     const float E = fmaxf(Ea, Eb);
-    const float E4 = 4.0f * E;
     const float cE = 2.0f * E * halfB;
     const float cU = 24.0f * TD_U * halfB;
     const unsigned below = (1u << lane) - 1u;
     (void)below;
-    if (lane == 0) *W.gcount = 0;
-    __syncwarp();
-    auto place = [&](int i) {
-        float x[D];
-        td_load_point<D>(xs, PS, i, x);
-        float y1 = fa[0] * x[0], y2 = fb[0] * x[0];
+    /* Placement of UNR points per lane per round: the common path (certified
+     * bucket: one bucket id store and one shared atomic) is predicated; the
+     * rare uncertain points are appended to W.glist under a warp-uniform
+     * branch.  All lanes run every round (indices past nnz are masked). */
+    constexpr int UNR = 4;
+    int nu = 0;
+    for (int i0 = 0; i0 < nnz; i0 += 32 * UNR) {
+        bool okv[UNR], vv[UNR];
+        int bl[UNR];
+        uint32_t inc[UNR];
 #pragma unroll
-        for (int r = 1; r < D; ++r) {
-            y1 = fmaf(fa[r], x[r], y1);
-            y2 = fmaf(fb[r], x[r], y2);
+        for (int u = 0; u < UNR; ++u) {
+            const int i = i0 + 32 * u + lane; /* rows up to a multiple of 128 are staged */
+            vv[u] = i < nnz;
+            float x[D];
+            td_load_point<D>(xs, PS, i, x);
+            float y1 = fa[0] * x[0], y2 = fb[0] * x[0];
+#pragma unroll
+            for (int r = 1; r < D; ++r) {
+                y1 = fmaf(fa[r], x[r], y1);
+                y2 = fmaf(fb[r], x[r], y2);
+            }
+            /* the orientation rides on the sign of the divisor: with
+             * s' = sign(y2) (|y1| + |y2|), key * B/2 = B/2 - y1 * (B/2) / s' */
+            const float sg = copysignf(fabsf(y1) + fabsf(y2), y2);
+            const float rr = __fdividef(1.0f, sg);
+            const float kb = fmaf(-y1, rr * halfB, halfB); /* key * B/2 */
+            const float db = fmaf(cE, fabsf(rr), cU);      /* delta * B/2 */
+            /* Floors by the magic-constant addition.  When |y1|+|y2| <= 4E the
+             * interval is at least B/4 wide, or outside the conversion window,
+             * or NaN: it never yields one in-range bucket, so no separate test. */
+            const int flo = td_floor_bits(kb - db), fhi = td_floor_bits(kb + db);
+            bl[u] = flo - 0x4B400000;
+            okv[u] = (fabsf(y2) > Eb) & (flo == fhi) & ((unsigned)bl[u] < (unsigned)B);
+            /* +1 event (orientation -): 1; -1 event (orientation +): 1 << 16 */
+            inc[u] = (uint32_t)(0x10000 + (__float_as_int(y2) >> 31) * 0xFFFF);
         }
-        const float s = fabsf(y1) + fabsf(y2);
-        const bool plus = y2 > 0.0f;
-        const float r = __fdividef(1.0f, s);
-        const float rh = r * (plus ? halfB : -halfB);
-        const float kb = fmaf(-y1, rh, halfB);  /* key * B/2 */
-        const float db = fmaf(cE, r, cU);       /* delta * B/2 */
-        /* floors by the magic-constant addition (|kb -+ db| <= 2^22 whenever
-         * s > 4E, since then db < B/2); garbage otherwise, but then ok fails */
-        const int flo = td_floor_bits(kb - db), fhi = td_floor_bits(kb + db);
-        const int blo = flo - 0x4B400000;
-        const bool ok = (fabsf(y2) > Eb) & (s > E4) & (flo == fhi) & ((unsigned)blo < (unsigned)B);
-        if (ok) {
-            W.bid[i] = (uint16_t)blo;
-            atomicAdd(&W.hist[td_phys(blo, lp, chm)], plus ? 0x10000u : 1u);
-        } else {
-            const int slot = atomicAdd(W.gcount, 1);
-            W.glist[slot] = (uint16_t)i;
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int i = i0 + 32 * u + lane;
+            if (vv[u] & okv[u]) {
+                W.bid[i] = (uint16_t)bl[u];
+                atomicAdd(&W.hist[bl[u]], inc[u]);
+            }
         }
-    };
-    int i = lane;
-    for (; i + 32 < nnz; i += 64) {
-        place(i);
-        place(i + 32);
+        unsigned bad[UNR];
+        unsigned any = 0;
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            bad[u] = __ballot_sync(TD_FULL, vv[u] & !okv[u]);
+            any |= bad[u];
+        }
+        if (any) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                if ((bad[u] >> lane) & 1u) W.glist[nu + __popc(bad[u] & below)] = (uint16_t)(i0 + 32 * u + lane);
+                nu += __popc(bad[u]);
+            }
+        }
     }
-    if (i < nnz) place(i);
     __syncwarp();
-    const int nu = *W.gcount;
     int t = 0;
     if (nu > 0) {
         __syncwarp();
@@ -974,11 +1002,11 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
      * coarse buckets.  Inside lane l's range the walk stays within
      * [P_l - c-_l, P_l + c+_l], which bounds G from below. */
     uint4 *h4 = reinterpret_cast<uint4 *>(W.hist) + lane * nch;
-    const int sw = lane & chm;
+    const int rot = lane & chm;
     const int per = B >> 5;
     uint32_t acc = 0;
-    for (int c = 0; c < nch; ++c) {
-        const uint4 v = h4[c ^ sw];
+    for (int k = 0; k < nch; ++k) {
+        const uint4 v = h4[(k + rot) & chm];
         acc += v.x + v.y + v.z + v.w;
     }
     const int cpl = (int)(acc & 0xFFFFu), cml = (int)(acc >> 16);
@@ -1027,7 +1055,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
         } else {
             int P = Pl;
             for (int c = 0; c < nch; ++c) {
-                const uint4 v = h4[c ^ sw];
+                const uint4 v = h4[c];
                 const uint32_t w4[4] = { v.x, v.y, v.z, v.w };
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -1086,7 +1114,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
             } else {
                 int P = Pl;
                 for (int c = 0; c < nch; ++c) {
-                    const uint4 v = h4[c ^ sw];
+                    const uint4 v = h4[c];
                     uint32_t w4[4] = { v.x, v.y, v.z, v.w };
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -1094,7 +1122,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
                         if (cand(P, cp, cm)) w4[k] = 0x80000000u | (uint32_t)P;
                         P += cp - cm;
                     }
-                    h4[c ^ sw] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                    h4[c] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
                 }
             }
             __syncwarp();
@@ -1181,7 +1209,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
         G = min(mn2, nzy - mx2);
     }
     __syncwarp();
-    for (int c = 0; c < nch; ++c) h4[c ^ sw] = make_uint4(0u, 0u, 0u, 0u);
+    for (int k = 0; k < nch; ++k) h4[(k + rot) & chm] = make_uint4(0u, 0u, 0u, 0u);
     __syncwarp();
     return G;
 }
@@ -1314,7 +1342,7 @@ __device__ __forceinline__ int td_query_of_tile(const int64_t *prefix, int nq, i
  * the points of the current query stay staged in shared memory; every warp
  * sweeps its share of the tile's subsets; one atomicMin per tile. */
 template <int D>
-__global__ void __launch_bounds__(256, (D <= 4 ? 2 : 1)) td_k_filtered(TdLaunch L)
+__global__ void __launch_bounds__(256, (D <= 4 ? 3 : 1)) td_k_filtered(TdLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_tile;
@@ -1331,7 +1359,7 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 2 : 1)) td_k_filtered(TdLaunch 
     /* layout: xs [nmax][PS] floats | per warp: hist [B] u32, bid [nmaxp] u16,
      * glist [nmaxp] u16, gcount, basis (qa, qb, meta) */
     float *xs = reinterpret_cast<float *>(smem);
-    const size_t off = ((size_t)L.nmax * PS * 4 + 15) & ~(size_t)15;
+    const size_t off = (size_t)((L.nmax + 127) & ~127) * PS * 4;
     const int Bmax = 1 << blog2_cap;
     const size_t per_warp = ((size_t)Bmax * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     unsigned char *wb = smem + off + per_warp * w;
@@ -1366,9 +1394,9 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 2 : 1)) td_k_filtered(TdLaunch 
         const int64_t t1 = min(t0 + ts, Q.hi);
         const int64_t spw = ts / (blockDim.x >> 5);
         const uint64_t r0 = (uint64_t)min(t0 + spw * w, t1), r1 = (uint64_t)min(t0 + spw * (w + 1), t1);
-        /* buckets: about one per nonzero point, at least 128 (four per lane) */
+        /* buckets: about one per two nonzero points, at least 128 (four per lane) */
         int blog2 = 7;
-        while ((1 << blog2) < nnz && blog2 < blog2_cap) ++blog2;
+        while ((2 << blog2) < nnz && blog2 < blog2_cap) ++blog2;
         int best = L.qmin[q];
         if (Q.d == D && blog2 <= blog2_cap && nnz <= L.nmax)
             td_warp_filtered<D>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st);
@@ -1578,7 +1606,7 @@ size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
 {
     int nmaxp = td_pow2_at_least(nmax);
     int PS = pmax <= 4 ? 4 : 8;
-    size_t off = ((size_t)nmax * PS * 4 + 15) & ~(size_t)15;
+    size_t off = (size_t)((nmax + 127) & ~127) * PS * 4;
     size_t per_warp = ((size_t)(1 << blog2) * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     return off + per_warp * warps;
 }

@@ -139,7 +139,7 @@ extern "C" int td_depth_noalloc(const int32_t *X, int32_t n, int32_t p, const in
     if (cudaGetDevice(&dev) != cudaSuccess) return TD_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TD_ERR_CUDA;
     int blog2 = 7;
-    while ((1 << blog2) < n && blog2 < 11) ++blog2;
+    while ((2 << blog2) < n && blog2 < 11) ++blog2;
     const size_t smem = td_filtered_smem(n, p, blog2, kWarps);
 
     TdLaunch L;

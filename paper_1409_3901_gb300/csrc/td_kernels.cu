@@ -61,6 +61,15 @@
 /* unit roundoff of binary32 */
 #define TD_U (1.0f / 16777216.0f)
 
+/* Reciprocal by the hardware approximation (rcp.approx.ftz.f32: at most 1 ulp
+ * from 1/x over the normal range, per the PTX ISA). */
+__device__ __forceinline__ float td_rcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 /* int64 -> binary32 off the FP64 pipe: exact-to-nearest when the value fits
  * 32 bits, else hi * 2^32 + lo with two roundings (relative error <= 2u,
  * covered by the error bounds below). */
@@ -908,11 +917,13 @@ __device__ __noinline__ void td_resolve_many(const float *xs, int PS, const int6
  * 2E/s + 24u covers both.  The bucket floor(key * B/2) is certain when
  * floor((key - delta) B/2) == floor((key + delta) B/2) and lies in [0, B). */
 template <int D>
-__device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis<D> &Bs,
+__device__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz, const TdBasis<D> &Bs,
                                  const float (&fa)[D], const float (&fb)[D], float Ea, float Eb,
                                  const TdWarpSmem &W, int blog2, int lane, int best, TdWarpStats &st,
                                  int &t_out, int &nzy_out)
 {
+    (void)PS_unused;
+    constexpr int PS = D <= 4 ? 4 : 8;      /* staged point stride (floats) */
     const int B = 1 << blog2;               /* blog2 >= 7: at least 4 buckets per lane */
     const int lp = blog2 - 5;               /* log2 buckets per lane */
     const int nch = 1 << (lp - 2);          /* chunks of four per lane */
@@ -928,17 +939,33 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
      * rare uncertain points are appended to W.glist under a warp-uniform
      * branch.  All lanes run every round (indices past nnz are masked). */
     constexpr int UNR = 4;
+    constexpr int PQ = PS / 4;                 /* float4 per staged point */
     int nu = 0;
-    for (int i0 = 0; i0 < nnz; i0 += 32 * UNR) {
+    const float4 *xq = reinterpret_cast<const float4 *>(xs);
+    /* One round places 32*UNR points, UNR per lane.  A point whose bucket is
+     * not certified (or a padding lane of the last round) adds its event to
+     * the dummy bucket B, which no scan reads, so the atomic and the bucket
+     * id store need no branch; uncertain points are appended to W.glist
+     * under a warp-uniform branch and placed exactly afterwards. */
+    auto round = [&](int i0, bool tail) {
         bool okv[UNR], vv[UNR];
-        int bl[UNR];
-        uint32_t inc[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             const int i = i0 + 32 * u + lane; /* rows up to a multiple of 128 are staged */
-            vv[u] = i < nnz;
+            vv[u] = !tail || i < nnz;
             float x[D];
-            td_load_point<D>(xs, PS, i, x);
+            {
+                const float4 a4 = xq[(size_t)i * PQ];
+                x[0] = a4.x;
+                if (D > 1) x[1] = a4.y;
+                if (D > 2) x[2] = a4.z;
+                if (D > 3) x[3] = a4.w;
+                if (D > 4) {
+                    const float4 b4 = xq[(size_t)i * PQ + 1];
+                    x[4] = b4.x;
+                    if (D > 5) x[5] = b4.y;
+                }
+            }
             float y1 = fa[0] * x[0], y2 = fb[0] * x[0];
 #pragma unroll
             for (int r = 1; r < D; ++r) {
@@ -948,25 +975,20 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
             /* the orientation rides on the sign of the divisor: with
              * s' = sign(y2) (|y1| + |y2|), key * B/2 = B/2 - y1 * (B/2) / s' */
             const float sg = copysignf(fabsf(y1) + fabsf(y2), y2);
-            const float rr = __fdividef(1.0f, sg);
+            const float rr = td_rcp(sg);
             const float kb = fmaf(-y1, rr * halfB, halfB); /* key * B/2 */
             const float db = fmaf(cE, fabsf(rr), cU);      /* delta * B/2 */
             /* Floors by the magic-constant addition.  When |y1|+|y2| <= 4E the
              * interval is at least B/4 wide, or outside the conversion window,
              * or NaN: it never yields one in-range bucket, so no separate test. */
             const int flo = td_floor_bits(kb - db), fhi = td_floor_bits(kb + db);
-            bl[u] = flo - 0x4B400000;
-            okv[u] = (fabsf(y2) > Eb) & (flo == fhi) & ((unsigned)bl[u] < (unsigned)B);
+            const int bl = flo - 0x4B400000;
+            okv[u] = vv[u] & (fabsf(y2) > Eb) & (flo == fhi) & ((unsigned)bl < (unsigned)B);
+            const int slot = okv[u] ? bl : B;
             /* +1 event (orientation -): 1; -1 event (orientation +): 1 << 16 */
-            inc[u] = (uint32_t)(0x10000 + (__float_as_int(y2) >> 31) * 0xFFFF);
-        }
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            const int i = i0 + 32 * u + lane;
-            if (vv[u] & okv[u]) {
-                W.bid[i] = (uint16_t)bl[u];
-                atomicAdd(&W.hist[bl[u]], inc[u]);
-            }
+            const uint32_t inc = (uint32_t)(0x10000 + (__float_as_int(y2) >> 31) * 0xFFFF);
+            W.bid[i] = (uint16_t)slot;
+            atomicAdd(&W.hist[slot], inc);
         }
         unsigned bad[UNR];
         unsigned any = 0;
@@ -982,7 +1004,10 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
                 nu += __popc(bad[u]);
             }
         }
-    }
+    };
+    const int nfull = nnz & ~(32 * UNR - 1);
+    for (int i0 = 0; i0 < nfull; i0 += 32 * UNR) round(i0, false);
+    if (nfull < nnz) round(nfull, true);
     __syncwarp();
     int t = 0;
     if (nu > 0) {
@@ -1131,8 +1156,8 @@ __device__ int td_sweep_filtered(const float *xs, int PS, int nnz, const TdBasis
                 const int i = i0 + lane;
                 bool g = false;
                 if (i < nnz) {
-                    uint16_t b = W.bid[i];
-                    g = b != TD_SENT && (W.hist[td_phys(b, lp, chm)] >> 31);
+                    const int b = W.bid[i];
+                    g = b < B && (W.hist[td_phys(b, lp, chm)] >> 31);
                 }
                 const unsigned bg = __ballot_sync(TD_FULL, g);
                 if (g) W.glist[Gn + __popc(bg & below)] = (uint16_t)i;
@@ -1353,27 +1378,30 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 1)) td_k_filtered(TdLaunch 
     const int64_t total = prefix[L.nq];
     if (total == 0) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nmaxp = td_pow2_at_least(L.nmax);
-    const int PS = L.pmax <= 4 ? 4 : 8;
+    const int nmaxp = max(128, td_pow2_at_least(L.nmax));
+    const int PSA = L.pmax <= 4 ? 4 : 8;  /* staging area stride (sizing) */
+    constexpr int PS = D <= 4 ? 4 : 8;    /* this dimension's stride */
     const int blog2_cap = L.blog2;
     /* layout: xs [nmax][PS] floats | per warp: hist [B] u32, bid [nmaxp] u16,
      * glist [nmaxp] u16, gcount, basis (qa, qb, meta) */
     float *xs = reinterpret_cast<float *>(smem);
-    const size_t off = (size_t)((L.nmax + 127) & ~127) * PS * 4;
+    const size_t off = (size_t)((L.nmax + 127) & ~127) * PSA * 4;
     const int Bmax = 1 << blog2_cap;
-    const size_t per_warp = ((size_t)Bmax * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    const size_t hbytes = (size_t)(Bmax + 4) * 4;
+    const size_t per_warp = (hbytes + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     unsigned char *wb = smem + off + per_warp * w;
     TdWarpSmem W;
     W.hist = reinterpret_cast<uint32_t *>(wb);
-    W.bid = reinterpret_cast<uint16_t *>(wb + (size_t)Bmax * 4);
+    W.bid = reinterpret_cast<uint16_t *>(wb + hbytes);
     W.glist = W.bid + nmaxp;
     W.gcount = reinterpret_cast<int *>(W.glist + nmaxp);
-    W.qa = reinterpret_cast<int64_t *>(wb + (size_t)Bmax * 4 + (size_t)nmaxp * 4 + 16);
+    W.qa = reinterpret_cast<int64_t *>(wb + hbytes + (size_t)nmaxp * 4 + 16);
     W.qb = W.qa + TD_MAXD;
     W.meta = reinterpret_cast<int *>(W.qb + TD_MAXD);
-    for (int j = lane; j < Bmax; j += 32) W.hist[j] = 0u;
+    for (int j = lane; j < Bmax + 4; j += 32) W.hist[j] = 0u;
     const int gw = blockIdx.x * (blockDim.x >> 5) + w;
-    const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, nmaxp);
+    /* the global scratch keeps the host's sizing (td_scratch_per_warp(nmax)) */
+    const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, td_pow2_at_least(L.nmax));
     TdWarpStats st = { 0, 0, 0, 0, 0, 0, 0 };
     int staged = -1;
     for (;;) {
@@ -1384,7 +1412,7 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 1)) td_k_filtered(TdLaunch 
         const int j = td_query_of_tile(prefix, L.nq, tile);
         const int q = L.order[j];
         if (q != staged) {
-            td_stage_points(L, q, xs, PS, s_tmp);
+            td_stage_points(L, q, xs, PS, s_tmp);  /* this dimension's stride */
             staged = q;
         }
         const TdQuery &Q = L.q[q];
@@ -1605,9 +1633,10 @@ __global__ void td_k_finalize(TdLaunch L)
 size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
 {
     int nmaxp = td_pow2_at_least(nmax);
+    nmaxp = nmaxp < 128 ? 128 : nmaxp;
     int PS = pmax <= 4 ? 4 : 8;
     size_t off = (size_t)((nmax + 127) & ~127) * PS * 4;
-    size_t per_warp = ((size_t)(1 << blog2) * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    size_t per_warp = ((size_t)((1 << blog2) + 4) * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     return off + per_warp * warps;
 }
 

@@ -1367,7 +1367,7 @@ __device__ __forceinline__ int td_query_of_tile(const int64_t *prefix, int nq, i
  * the points of the current query stay staged in shared memory; every warp
  * sweeps its share of the tile's subsets; one atomicMin per tile. */
 template <int D>
-__global__ void __launch_bounds__(256, (D <= 4 ? 3 : 1)) td_k_filtered(TdLaunch L)
+__global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_tile;

@@ -70,6 +70,30 @@ __device__ __forceinline__ float td_rcp(float x)
     return r;
 }
 
+/* Shared-memory accesses of the point loop with 32-bit shared-window
+ * addresses (no 64-bit generic address arithmetic per point). */
+__device__ __forceinline__ unsigned td_saddr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float4 td_lds128(unsigned a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void td_sts16(unsigned a, unsigned short v)
+{
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
+}
+
+__device__ __forceinline__ void td_reds_add(unsigned a, unsigned v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
 /* int64 -> binary32 off the FP64 pipe: exact-to-nearest when the value fits
  * 32 bits, else hi * 2^32 + lo with two roundings (relative error <= 2u,
  * covered by the error bounds below). */
@@ -941,7 +965,9 @@ __device__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz, const 
     constexpr int UNR = 4;
     constexpr int PQ = PS / 4;                 /* float4 per staged point */
     int nu = 0;
-    const float4 *xq = reinterpret_cast<const float4 *>(xs);
+    const unsigned xq = td_saddr(xs) + (unsigned)lane * (16u * PQ);   /* this lane's first point */
+    const unsigned hq = td_saddr(W.hist);
+    const unsigned bq = td_saddr(W.bid) + 2u * (unsigned)lane;
     /* One round places 32*UNR points, UNR per lane.  A point whose bucket is
      * not certified (or a padding lane of the last round) adds its event to
      * the dummy bucket B, which no scan reads, so the atomic and the bucket
@@ -949,23 +975,26 @@ __device__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz, const 
      * under a warp-uniform branch and placed exactly afterwards. */
     auto round = [&](int i0, bool tail) {
         bool okv[UNR], vv[UNR];
+        int slot[UNR];
+        uint32_t inc[UNR];
+        float4 a4[UNR], b4[UNR];
+        /* all loads of the round first (the accesses keep program order) */
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const int i = i0 + 32 * u + lane; /* rows up to a multiple of 128 are staged */
-            vv[u] = !tail || i < nnz;
+            const unsigned pa = xq + (unsigned)(i0 + 32 * u) * (16u * PQ);
+            a4[u] = td_lds128(pa);
+            if (D > 4) b4[u] = td_lds128(pa + 16u);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            vv[u] = !tail || i0 + 32 * u + lane < nnz; /* rows up to a multiple of 128 are staged */
             float x[D];
-            {
-                const float4 a4 = xq[(size_t)i * PQ];
-                x[0] = a4.x;
-                if (D > 1) x[1] = a4.y;
-                if (D > 2) x[2] = a4.z;
-                if (D > 3) x[3] = a4.w;
-                if (D > 4) {
-                    const float4 b4 = xq[(size_t)i * PQ + 1];
-                    x[4] = b4.x;
-                    if (D > 5) x[5] = b4.y;
-                }
-            }
+            x[0] = a4[u].x;
+            if (D > 1) x[1] = a4[u].y;
+            if (D > 2) x[2] = a4[u].z;
+            if (D > 3) x[3] = a4[u].w;
+            if (D > 4) x[4] = b4[u].x;
+            if (D > 5) x[5] = b4[u].y;
             float y1 = fa[0] * x[0], y2 = fb[0] * x[0];
 #pragma unroll
             for (int r = 1; r < D; ++r) {
@@ -984,11 +1013,14 @@ __device__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz, const 
             const int flo = td_floor_bits(kb - db), fhi = td_floor_bits(kb + db);
             const int bl = flo - 0x4B400000;
             okv[u] = vv[u] & (fabsf(y2) > Eb) & (flo == fhi) & ((unsigned)bl < (unsigned)B);
-            const int slot = okv[u] ? bl : B;
+            slot[u] = okv[u] ? bl : B;
             /* +1 event (orientation -): 1; -1 event (orientation +): 1 << 16 */
-            const uint32_t inc = (uint32_t)(0x10000 + (__float_as_int(y2) >> 31) * 0xFFFF);
-            W.bid[i] = (uint16_t)slot;
-            atomicAdd(&W.hist[slot], inc);
+            inc[u] = (uint32_t)(0x10000 + (__float_as_int(y2) >> 31) * 0xFFFF);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            td_sts16(bq + 2u * (unsigned)(i0 + 32 * u), (unsigned short)slot[u]);
+            td_reds_add(hq + 4u * (unsigned)slot[u], inc[u]);
         }
         unsigned bad[UNR];
         unsigned any = 0;

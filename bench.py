@@ -46,6 +46,11 @@ def _args():
     ap.add_argument("--plain-queries", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["W2", "W3", "W4", "W5"], default="W2",
+                    help="W2 (default) is the benchmark line; W3 (256 datasets, one batched call), "
+                         "W4 (p=5 with ties) and W5 (request stream with Poisson arrivals) print "
+                         "their own lines")
+    ap.add_argument("--stream-seconds", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -330,12 +335,88 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_other(a):
+    """Lines for the other workloads (one GPU, inputs from host memory)."""
+    import torch
+    from paper_1409_3901_gb300 import tukey, workloads as W
+    torch.cuda.set_device(0)
+    ctx = tukey.Context(0)
+    if a.workload in ("W3", "W4"):
+        sets = W.w3() if a.workload == "W3" else [W.w4()]
+        batch = [(d.X, d.Zq) for d in sets]
+        for _ in range(max(1, a.warmup - 2)):
+            ctx.depth_batched(batch)
+        ms, sw, ex, pts = [], 0, 0, 0
+        for _ in range(a.steps):
+            ctx.depth_batched(batch)
+            st = ctx.last_stats
+            ms.append(st.ms_sweep)
+            sw += st.sweeps
+            ex += st.exact_points
+            pts += st.exact_points + st.filtered_points
+        t = sum(ms) / 1e3
+        nq = sum(d.m for d in sets)
+        line = {"metric": METRIC, "value": sw / t, "unit": UNIT, "workload": a.workload,
+                "datasets": len(sets), "queries": nq, "queries_per_s": nq * a.steps / t,
+                "sweeps_per_call": sw // a.steps, "ms_per_call": 1e3 * t / a.steps,
+                "exact_point_fraction": ex / max(pts, 1), "steps": a.steps,
+                "note": "sweep-kernel device time (td_stats.ms_sweep), one batched call per step"}
+        print(json.dumps(line), flush=True)
+        return
+    # W5: a stream of requests with Poisson arrivals, bounded sample
+    import random
+    from math import comb
+    reqs = [d for d in W.w5(count=400) if comb(d.n, d.p - 2) * d.n <= 3e8][:120]
+    s = ctx.stream(mem_budget_bytes=8 << 30)
+    # calibration: back-to-back throughput over the whole sample
+    t0 = time.perf_counter()
+    tickets = [s.submit(d.X, d.Zq) for d in reqs]
+    for tk in tickets:
+        s.wait(tk)
+    rate = len(reqs) / (time.perf_counter() - t0)
+    lam = 0.7 * rate
+    rnd = random.Random(5)
+    lat, done_sweeps = [], 0
+    t_start = time.perf_counter()
+    next_t = t_start
+    pending = []
+    k = 0
+    while time.perf_counter() - t_start < a.stream_seconds or pending:
+        now = time.perf_counter()
+        if now >= next_t and now - t_start < a.stream_seconds:
+            d = reqs[k % len(reqs)]
+            k += 1
+            tk = s.submit(d.X, d.Zq)
+            if tk is not None:
+                pending.append((tk, next_t, d))
+            next_t += rnd.expovariate(lam)
+        still = []
+        for tk, ta, d in pending:
+            if s.poll(tk) is not None:
+                lat.append(time.perf_counter() - ta)
+                done_sweeps += comb(d.n, d.p - 2) * d.m
+            else:
+                still.append((tk, ta, d))
+        pending = still
+        time.sleep(0.0002)
+    el = time.perf_counter() - t_start
+    lat.sort()
+    line = {"metric": "stream request latency", "workload": "W5", "unit": "ms",
+            "p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "requests": len(lat), "arrival_rate_per_s": lam, "calibrated_rate_per_s": rate,
+            "throughput_requests_per_s": len(lat) / el, "throughput_sweeps_per_s": done_sweeps / el,
+            "sample": "requests with C(n,p-2)*n <= 3e8 among the first 400 of the stream, cycled"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     if a.warmup < 3:
         a.warmup = 3
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload != "W2":
+        run_other(a)
     else:
         run_ours(a)
 

@@ -86,7 +86,7 @@ struct Work {
 };
 
 struct GraphKey {
-    int nq, nsets, nmax, pmax, grid[TD_NDIM], blog2, spw;
+    int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw;
     size_t smem;
     const void *ptrs[13];
     int64_t shard_index, shard_count;
@@ -109,16 +109,27 @@ struct td_ctx {
     bool gvalid = false;
 };
 
+/* one request of a stream: a copy of its inputs until its batch runs */
 struct td_stream_req {
     uint64_t ticket;
-    Work w;
-    HostBuf hin, hout;
+    int32_t n, p, m;
+    std::vector<int32_t> X, Z;
     int32_t *user_out;
-    int32_t m;
-    cudaEvent_t done;
     size_t bytes;
+    int slot;        /* batch slot running it, -1 while pending */
+    int64_t out_off; /* offset of its outputs in the slot's output */
     bool finished;
     int status;
+};
+
+/* a batch of coalesced requests in flight */
+struct td_stream_slot {
+    Work w;
+    HostBuf hstage, hout;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    int nq = 0;
+    std::vector<td_stream_req *> reqs;
 };
 
 struct td_stream {
@@ -127,7 +138,9 @@ struct td_stream {
     size_t budget, inflight;
     uint64_t next;
     DevBuf scratch;
-    std::vector<td_stream_req *> reqs;
+    std::vector<td_stream_req *> pending;   /* admitted, not yet launched */
+    std::vector<td_stream_req *> reqs;      /* every request not yet reaped */
+    td_stream_slot slot[2];
 };
 
 namespace {
@@ -190,6 +203,7 @@ bool range_ok(const td_dataset &d)
 
 struct Plan {
     int nq = 0, nsets = 0, nmax = 1, pmax = 1;
+    int nmaxD[TD_NDIM] = { 1, 1, 1, 1, 1 }; /* largest n over the datasets with p >= D (D = 2 + i) */
     size_t x_elems = 0;
     std::vector<TdSet> sets;
     std::vector<TdQuery> q;
@@ -210,6 +224,7 @@ Plan make_plan(const td_dataset *sets, int k)
         P.x_elems += (size_t)t.n * t.p;
         P.nmax = std::max(P.nmax, t.n);
         P.pmax = std::max(P.pmax, t.p);
+        for (int D = 2; D <= std::min(t.p, 6); ++D) P.nmaxD[D - 2] = std::max(P.nmaxD[D - 2], t.n);
         double c = 1.0;
         for (int i = 0; i < t.p - 2; ++i) c *= (double)(t.n - i) / (i + 1);
         c *= t.n;
@@ -379,7 +394,15 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
          * node of the graph; outside a capture the flag changes nothing */
         if (ev_a) TDCK(cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
         for (int D = 2; D <= std::min(P.pmax, 6); ++D) {
-            TDCK(td_launch_filtered(D, Lf, w.grid[D - 2], smem, s));
+            /* each dimension's kernel is sized for the datasets that can
+             * hold queries of that dimension (p >= D) */
+            TdLaunch LD = Lf;
+            LD.nmax = P.nmaxD[D - 2];
+            LD.pmax = D;
+            LD.blog2 = blog2_for(LD.nmax, o);
+            LD.scratch_per_warp = td_scratch_per_warp(LD.nmax);
+            const size_t smemD = td_filtered_smem(LD.nmax, D, LD.blog2, kWarpsFiltered);
+            TDCK(td_launch_filtered(D, LD, w.grid[D - 2], smemD, s));
             ++nl;
         }
         if (ev_b) TDCK(cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
@@ -390,21 +413,23 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
     return TD_OK;
 }
 
-/* Persistent grids of the sweep kernels (D = 2 .. min(pmax, 6)); sets the
- * dynamic shared memory attribute of each.  Returns the largest total warp
- * count (for the scratch), or 0 if a kernel cannot be resident. */
-int filtered_grids(td_ctx *ctx, const Plan &P, int blog2, int *grid)
+/* Persistent grids of the sweep kernels (D = 2 .. min(pmax, 6)), each sized
+ * for its own dimension (rows of at most nmaxD points, stride 4 or 8 floats);
+ * sets the dynamic shared memory attribute of each.  Returns the scratch
+ * bytes the largest of them needs, or 0 if a kernel cannot be resident. */
+size_t filtered_grids(td_ctx *ctx, const Plan &P, const td_options &o, int *grid)
 {
-    size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
-    int warps = 0;
+    size_t scratch = 256;
     for (int i = 0; i < TD_NDIM; ++i) grid[i] = 0;
     for (int D = 2; D <= std::min(P.pmax, 6); ++D) {
+        const int nmaxD = P.nmaxD[D - 2];
+        const size_t smem = td_filtered_smem(nmaxD, D, blog2_for(nmaxD, o), kWarpsFiltered);
         int occ = td_filtered_occupancy(D, kWarpsFiltered, smem);
         if (occ < 1) return 0;
         grid[D - 2] = ctx->sms * occ;
-        warps = std::max(warps, grid[D - 2] * kWarpsFiltered);
+        scratch = std::max(scratch, (size_t)grid[D - 2] * kWarpsFiltered * (size_t)td_scratch_per_warp(nmaxD));
     }
-    return std::max(warps, 1);
+    return scratch;
 }
 
 /* One synchronous batched call. */
@@ -433,11 +458,13 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         if (occ < 1) return TD_ERR_INVALID;
         grid = ctx->sms * occ;
         warps_total = grid * kWarpsPlain;
+        TDCK(alloc_work(ctx->w, P, warps_total, true));
     } else {
-        warps_total = filtered_grids(ctx, P, blog2, grids);
-        if (warps_total < 1) return TD_ERR_INVALID;
+        const size_t scratch = filtered_grids(ctx, P, o, grids);
+        if (scratch < 1) return TD_ERR_INVALID;
+        TDCK(alloc_work(ctx->w, P, 0, true));
+        TDCK(grow(ctx->w.scratch, scratch));
     }
-    TDCK(alloc_work(ctx->w, P, warps_total, true));
     memcpy(ctx->w.grid, grids, sizeof(grids));
     const int32_t *x_arena = nullptr;
     int rc = stage_inputs(ctx, ctx->w, ctx->hstage, P, sets, k, devptr, s, &x_arena);
@@ -454,6 +481,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         key.nmax = P.nmax;
         key.pmax = P.pmax;
         memcpy(key.grid, grids, sizeof(grids));
+        memcpy(key.nmaxD, P.nmaxD, sizeof(P.nmaxD));
         key.blog2 = blog2;
         key.spw = o.subsets_per_warp;
         key.smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
@@ -670,38 +698,106 @@ extern "C" int td_depth_batched(td_ctx *ctx, const td_dataset *sets, int32_t k, 
 
 namespace {
 
-size_t request_bytes(const Plan &P)
+size_t request_bytes(int n, int p, int m)
 {
-    return P.x_elems * 4 + (size_t)P.nq * (TD_MAXD * 4 + sizeof(TdQuery) + 4 + 8 + 4 + 4 + 4) + 4096;
+    return (size_t)n * p * 4 + (size_t)m * (TD_MAXD * 4 + sizeof(TdQuery) + 4 + 8 * TD_NDIM + 4 + 4 + 4) + 4096;
 }
 
-void free_req(td_stream_req *r)
+/* Finish a slot whose event completed: hand every request its outputs. */
+void complete_slot(td_stream *s, int k)
 {
-    Work &w = r->w;
-    DevBuf *bufs[] = { &w.X, &w.Zq, &w.sets, &w.q, &w.order, &w.prefix, &w.tsize, &w.ticket, &w.qmin, &w.out, &w.ctr };
-    for (DevBuf *b : bufs)
-        if (b->p) cudaFree(b->p);
-    if (r->hin.p) cudaFreeHost(r->hin.p);
-    if (r->hout.p) cudaFreeHost(r->hout.p);
-    if (r->done) cudaEventDestroy(r->done);
-    delete r;
-}
-
-/* finish a request whose event completed: copy outputs to the user buffer */
-int complete_req(td_stream *s, td_stream_req *r)
-{
-    if (r->finished) return r->status;
-    int32_t *h = (int32_t *)r->hout.p;
-    TdCounters *c = (TdCounters *)(h + r->m);
-    if (c->errors != 0) {
-        r->status = TD_ERR_INTERNAL;
-    } else {
-        memcpy(r->user_out, h, (size_t)r->m * 4);
-        r->status = TD_OK;
+    td_stream_slot &sl = s->slot[k];
+    const int32_t *h = (const int32_t *)sl.hout.p;
+    const TdCounters *c = (const TdCounters *)(h + ((sl.nq + 3) & ~3));
+    const bool ok = c->errors == 0;
+    for (td_stream_req *r : sl.reqs) {
+        if (ok) memcpy(r->user_out, h + r->out_off, (size_t)r->m * 4);
+        r->status = ok ? TD_OK : TD_ERR_INTERNAL;
+        r->finished = true;
+        s->inflight -= r->bytes;
+        r->X.clear();
+        r->X.shrink_to_fit();
+        r->Z.clear();
+        r->Z.shrink_to_fit();
     }
-    r->finished = true;
-    s->inflight -= r->bytes;
-    return r->status;
+    sl.reqs.clear();
+    sl.busy = false;
+}
+
+/* Reap finished slots, then launch the pending requests as one batch into a
+ * free slot.  Returns TD_OK or a CUDA error code. */
+int pump(td_stream *s)
+{
+    td_ctx *ctx = s->ctx;
+    for (int k = 0; k < 2; ++k)
+        if (s->slot[k].busy) {
+            cudaError_t e = cudaEventQuery(s->slot[k].done);
+            if (e == cudaSuccess) complete_slot(s, k);
+            else if (e != cudaErrorNotReady) return fail_cuda(ctx, e, "cudaEventQuery");
+        }
+    if (s->pending.empty()) return TD_OK;
+    int k = !s->slot[0].busy ? 0 : (!s->slot[1].busy ? 1 : -1);
+    if (k < 0) return TD_OK;
+    td_stream_slot &sl = s->slot[k];
+    std::vector<td_dataset> sets;
+    sets.reserve(s->pending.size());
+    int64_t off = 0;
+    for (td_stream_req *r : s->pending) {
+        td_dataset d;
+        d.n = r->n;
+        d.p = r->p;
+        d.X = r->X.data();
+        d.m = r->m;
+        d.Z = r->Z.data();
+        d.out = nullptr;
+        sets.push_back(d);
+        r->slot = k;
+        r->out_off = off;
+        off += r->m;
+    }
+    Plan P = make_plan(sets.data(), (int)sets.size());
+    td_options o = ctx->opt;
+    o.mode = TD_MODE_FILTERED;
+    o.device_pointers = 0;
+    o.shard_count = 1;
+    o.shard_index = 0;
+    const int blog2 = blog2_for(P.nmax, o);
+    (void)cudaGetLastError();
+    int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
+    const size_t scratch = filtered_grids(ctx, P, o, grids);
+    if (scratch < 1) return TD_ERR_INVALID;
+    cudaError_t e = alloc_work(sl.w, P, 0, true);
+    if (e == cudaSuccess) e = grow(s->scratch, scratch);
+    if (e == cudaSuccess && !sl.done) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    const size_t outb = (size_t)((P.nq + 3) & ~3) * 4 + sizeof(TdCounters);
+    if (e == cudaSuccess) e = grow_host(sl.hout, outb);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "stream batch buffers");
+    memcpy(sl.w.grid, grids, sizeof(grids));
+    const int32_t *x_arena = nullptr;
+    int rc = stage_inputs(ctx, sl.w, sl.hstage, P, sets.data(), (int)sets.size(), false, s->s, &x_arena);
+    if (rc != TD_OK) return rc;
+    TdLaunch L = make_launch(sl.w, P, x_arena, o, kWarpsFiltered, blog2);
+    L.scratch = (char *)s->scratch.p;
+    TDCK(cudaMemsetAsync(sl.w.ctr.p, 0, sizeof(TdCounters), s->s));
+    int nl = 0;
+    rc = enqueue_kernels(ctx, sl.w, P, L, o, blog2, s->s, &nl);
+    if (rc != TD_OK) return rc;
+    TDCK(cudaMemcpyAsync(sl.hout.p, sl.w.out.p, (size_t)P.nq * 4, cudaMemcpyDeviceToHost, s->s));
+    TDCK(cudaMemcpyAsync((int32_t *)sl.hout.p + ((P.nq + 3) & ~3), sl.w.ctr.p, sizeof(TdCounters),
+                         cudaMemcpyDeviceToHost, s->s));
+    TDCK(cudaEventRecord(sl.done, s->s));
+    sl.reqs.swap(s->pending);
+    s->pending.clear();
+    sl.nq = P.nq;
+    sl.busy = true;
+    return TD_OK;
+}
+
+td_stream_req *find_req(td_stream *s, uint64_t ticket)
+{
+    for (td_stream_req *r : s->reqs)
+        if (r->ticket == ticket) return r;
+    return nullptr;
 }
 
 }  // namespace
@@ -735,90 +831,31 @@ extern "C" int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *tic
     if (v != TD_OK) return v;
     if (!range_ok(*d)) return TD_ERR_RANGE;
     cudaSetDevice(ctx->device);
-    /* reap finished requests first (frees budget) */
-    for (td_stream_req *r : s->reqs)
-        if (!r->finished && cudaEventQuery(r->done) == cudaSuccess) complete_req(s, r);
-    Plan P = make_plan(d, 1);
-    size_t bytes = request_bytes(P);
+    int rc = pump(s); /* reaps finished batches first (frees budget) */
+    if (rc != TD_OK) return rc;
+    const size_t bytes = request_bytes(d->n, d->p, d->m);
     if (s->inflight + bytes > s->budget) return TD_ERR_BUSY;
     td_stream_req *r = new (std::nothrow) td_stream_req();
     if (!r) return TD_ERR_OOM;
-    r->ticket = s->next;
-    r->user_out = d->out;
+    r->ticket = s->next++;
+    r->n = d->n;
+    r->p = d->p;
     r->m = d->m;
+    r->X.assign(d->X, d->X + (size_t)d->n * d->p); /* the caller may reuse its inputs on return */
+    if (d->m > 0) r->Z.assign(d->Z, d->Z + (size_t)d->m * d->p);
+    r->user_out = d->out;
     r->bytes = bytes;
-    r->finished = false;
+    r->slot = -1;
+    r->out_off = 0;
+    r->finished = d->m == 0;
     r->status = TD_OK;
-    r->done = nullptr;
-    td_options o = ctx->opt;
-    o.mode = TD_MODE_FILTERED;
-    o.device_pointers = 0;
-    const int blog2 = blog2_for(P.nmax, o);
-    int grid = 0;
-    (void)cudaGetLastError();
-    int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
-    if (P.nq > 0) {
-        grid = filtered_grids(ctx, P, blog2, grids);
-        if (grid < 1) {
-            delete r;
-            return TD_ERR_INVALID;
-        }
-    }
-    cudaError_t e = alloc_work(r->w, P, 0, true);
-    if (e == cudaSuccess) {
-        size_t sc = (size_t)grid * (size_t)td_scratch_per_warp(TD_MAX_N);
-        e = grow(s->scratch, sc);
-    }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = grow_host(r->hout, (size_t)P.nq * 4 + sizeof(TdCounters) + 64);
-    if (e != cudaSuccess) {
-        free_req(r);
-        return fail_cuda(ctx, e, "td_stream_submit");
-    }
-    memcpy(r->w.grid, grids, sizeof(grids));
-    const int32_t *x_arena = nullptr;
-    int rc = TD_OK;
-    if (P.nq > 0) {
-        rc = stage_inputs(ctx, r->w, r->hin, P, d, 1, false, s->s, &x_arena);
-        if (rc == TD_OK) {
-            TdLaunch L = make_launch(r->w, P, x_arena, o, kWarpsFiltered, blog2);
-            L.scratch = (char *)s->scratch.p;
-            L.scratch_per_warp = td_scratch_per_warp(TD_MAX_N);
-            /* scratch sized for TD_MAX_N points per warp */
-            L.nmax = P.nmax;
-            e = cudaMemsetAsync(r->w.ctr.p, 0, sizeof(TdCounters), s->s);
-            if (e == cudaSuccess) {
-                int nl = 0;
-                TdLaunch L2 = L;
-                rc = enqueue_kernels(ctx, r->w, P, L2, o, blog2, s->s, &nl);
-            } else {
-                rc = fail_cuda(ctx, e, "cudaMemsetAsync");
-            }
-            if (rc == TD_OK) {
-                e = cudaMemcpyAsync(r->hout.p, r->w.out.p, (size_t)P.nq * 4, cudaMemcpyDeviceToHost, s->s);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync((int32_t *)r->hout.p + P.nq, r->w.ctr.p, sizeof(TdCounters),
-                                        cudaMemcpyDeviceToHost, s->s);
-                if (e != cudaSuccess) rc = fail_cuda(ctx, e, "cudaMemcpyAsync");
-            }
-        }
-    } else {
-        memset(r->hout.p, 0, sizeof(TdCounters) + 64);
-    }
-    if (rc == TD_OK) {
-        e = cudaEventRecord(r->done, s->s);
-        if (e != cudaSuccess) rc = fail_cuda(ctx, e, "cudaEventRecord");
-    }
-    /* the host inputs were copied into the request's pinned buffer by
-     * stage_inputs, so the caller may reuse them as soon as this returns */
-    if (rc != TD_OK) {
-        cudaStreamSynchronize(s->s);
-        free_req(r);
-        return rc;
-    }
-    s->inflight += bytes;
-    s->next++;
     s->reqs.push_back(r);
+    if (!r->finished) {
+        s->inflight += bytes;
+        s->pending.push_back(r);
+        rc = pump(s);
+        if (rc != TD_OK) return rc;
+    }
     *ticket = r->ticket;
     return TD_OK;
 }
@@ -826,22 +863,20 @@ extern "C" int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *tic
 extern "C" int td_stream_poll(td_stream *s, uint64_t ticket, int *done)
 {
     if (!s || !done) return TD_ERR_INVALID;
-    for (td_stream_req *r : s->reqs) {
-        if (r->ticket != ticket) continue;
-        if (r->finished) {
-            *done = 1;
-            return r->status;
-        }
-        cudaError_t e = cudaEventQuery(r->done);
-        if (e == cudaSuccess) {
-            *done = 1;
-            return complete_req(s, r);
-        }
-        if (e != cudaErrorNotReady) return fail_cuda(s->ctx, e, "cudaEventQuery");
-        *done = 0;
-        return TD_OK;
+    td_stream_req *r = find_req(s, ticket);
+    if (!r) return TD_ERR_NOTFOUND;
+    if (!r->finished) {
+        cudaSetDevice(s->ctx->device);
+        int rc = pump(s);
+        if (rc != TD_OK) return rc;
     }
-    return TD_ERR_NOTFOUND;
+    *done = r->finished ? 1 : 0;
+    if (!r->finished) return TD_OK;
+    /* reported: the ticket is forgotten */
+    const int status = r->status;
+    s->reqs.erase(std::find(s->reqs.begin(), s->reqs.end(), r));
+    delete r;
+    return status;
 }
 
 extern "C" int td_stream_wait(td_stream *s, uint64_t ticket, int64_t timeout_us)
@@ -865,7 +900,17 @@ extern "C" int td_stream_destroy(td_stream *s)
     if (!s) return TD_ERR_INVALID;
     cudaSetDevice(s->ctx->device);
     cudaStreamSynchronize(s->s);
-    for (td_stream_req *r : s->reqs) free_req(r);
+    for (td_stream_req *r : s->reqs) delete r;
+    for (int k = 0; k < 2; ++k) {
+        td_stream_slot &sl = s->slot[k];
+        Work &w = sl.w;
+        DevBuf *bufs[] = { &w.X, &w.Zq, &w.sets, &w.q, &w.order, &w.prefix, &w.tsize, &w.ticket, &w.qmin, &w.out, &w.ctr, &w.scratch };
+        for (DevBuf *b : bufs)
+            if (b->p) cudaFree(b->p);
+        if (sl.hstage.p) cudaFreeHost(sl.hstage.p);
+        if (sl.hout.p) cudaFreeHost(sl.hout.p);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
     if (s->scratch.p) cudaFree(s->scratch.p);
     cudaStreamDestroy(s->s);
     delete s;

@@ -232,6 +232,7 @@ class Stream:
         self.ptr = ctypes.c_void_p()
         _check(td_stream_create(ctx.ptr, ctypes.c_size_t(int(mem_budget_bytes)), ctypes.byref(self.ptr)), ctx.ptr)
         self.pending = {}
+        self.done = {}
 
     def submit(self, X, Z):
         """Returns a ticket, or None when admission is refused (TD_ERR_BUSY)."""
@@ -250,12 +251,20 @@ class Stream:
         return t.value
 
     def poll(self, ticket):
+        """The request's outputs once it is done (the library then forgets the
+        ticket), else None."""
+        if ticket in self.done:
+            return self.done.pop(ticket)
         done = ctypes.c_int(0)
         _check(td_stream_poll(self.ptr, ticket, ctypes.byref(done)), self.ctx.ptr)
-        return bool(done.value)
+        if not done.value:
+            return None
+        return self.pending.pop(ticket)
 
     def wait(self, ticket, timeout_us=-1):
         """The request's outputs, or raises TdError(TD_ERR_TIMEOUT)."""
+        if ticket in self.done:
+            return self.done.pop(ticket)
         _check(td_stream_wait(self.ptr, ticket, int(timeout_us)), self.ctx.ptr)
         return self.pending.pop(ticket)
 

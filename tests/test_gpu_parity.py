@@ -177,6 +177,39 @@ def test_stream_api(td):
     assert tiny.submit(reqs[0][1], reqs[0][2]) is None
 
 
+def test_stream_polling_and_ticket_lifetime(td):
+    """Requests submitted while a batch runs are coalesced into the next
+    one; poll returns outputs once, after which the library forgets the
+    ticket; a zero-query request completes at once."""
+    import ctypes
+    rng = np.random.default_rng(12)
+    ctx = td.Context(0)
+    s = ctx.stream(mem_budget_bytes=1 << 30)
+    items = []
+    for i in range(20):
+        p = int(rng.integers(3, 5))
+        X = random_case(rng, p, int(rng.integers(20, 50)), 40)
+        Z = np.vstack([X[:1], rng.integers(-40, 41, size=(2, p))]).astype(np.int32)
+        items.append((s.submit(X, Z), X, Z))
+    got = {}
+    for _ in range(200000):
+        for t, X, Z in items:
+            if t not in got:
+                o = s.poll(t)
+                if o is not None:
+                    got[t] = o
+        if len(got) == len(items):
+            break
+    assert len(got) == len(items)
+    for t, X, Z in items:
+        assert np.array_equal(got[t], oracle.depth_many(X, Z))
+    done = ctypes.c_int(0)
+    assert td.td_stream_poll(s.ptr, items[0][0], ctypes.byref(done)) == td.TD_ERR_NOTFOUND
+    X = random_case(rng, 3, 10, 5)
+    t0 = s.submit(X, np.zeros((0, 3), np.int32))
+    assert s.wait(t0, timeout_us=1_000_000).shape == (0,)
+
+
 def test_errors_leave_outputs_untouched(ctx, td):
     X = np.array([[0, 0, 0], [2 ** 22, 0, 0]], np.int32)
     Z = np.zeros((1, 3), np.int32)

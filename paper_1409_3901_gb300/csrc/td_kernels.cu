@@ -777,41 +777,111 @@ __device__ __forceinline__ int td_phys(int b, int lp, int chm)
     return b;
 }
 
-/* Exact placement of the points the FP32 filter could not certify (their ids
- * are in W.glist[0..nu)): exact projection from the published basis; zero
- * projections are tight points, the others go to their exact bucket. */
+/* the two basis columns from the warp's shared block (32-bit words: qa at
+ * [0, D), qb at [8, 8 + D), 16-byte aligned) */
 template <int D>
-__device__ __forceinline__ void td_exact_pass(const float *xs, int PS, int lp, int chm,
-                                           uint32_t *hist, uint16_t *bid, const uint16_t *list, int nu,
-                                           const int64_t *qa, const int64_t *qb, int B, int lane,
-                                           int *t_out)
+__device__ __forceinline__ void td_load_pair(const void *src, uint32_t (&a)[D], uint32_t (&b)[D])
 {
-    int t = 0;
-    for (int l = lane; l < nu; l += 32) {
-        int i = list[l];
-        const float *xp = xs + (size_t)i * PS;
-        int64_t Y1 = 0, Y2 = 0;
-#pragma unroll
-        for (int r = 0; r < D; ++r) {
-            const int64_t xv = td_f2i(xp[r]);
-            Y1 += qa[r] * xv;
-            Y2 += qb[r] * xv;
-        }
-        if (Y1 == 0 && Y2 == 0) {
-            bid[i] = (uint16_t)TD_SENT;
-            ++t;
-            continue;
-        }
-        int64_t h1, h2;
-        bool plus = td_normalise(Y1, Y2, h1, h2);
-        float key = td_key(td_i64_to_f32(h1), td_i64_to_f32(h2));
-        int bb = (int)(key * (float)(B >> 1));
-        bb = max(0, min(bb, B - 1));
-        int b = td_exact_bucket(h1, h2, bb, B);
-        bid[i] = (uint16_t)b;
-        atomicAdd(&hist[td_phys(b, lp, chm)], plus ? 0x10000u : 1u);
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    const uint4 a4 = s4[0], b4 = s4[2];
+    a[0] = a4.x;
+    b[0] = b4.x;
+    if (D > 1) { a[1] = a4.y; b[1] = b4.y; }
+    if (D > 2) { a[2] = a4.z; b[2] = b4.z; }
+    if (D > 3) { a[3] = a4.w; b[3] = b4.w; }
+    if (D > 4) {
+        const uint2 a2 = reinterpret_cast<const uint2 *>(src)[2], b2 = reinterpret_cast<const uint2 *>(src)[6];
+        a[4] = a2.x;
+        b[4] = b2.x;
+        if (D > 5) { a[5] = a2.y; b[5] = b2.y; }
     }
-    *t_out = td_wsum(t);
+}
+
+/* Exact placement of the points the FP32 filter could not certify (their ids
+ * are in list[0..nu)), one point per lane.  The projection is exact: in int32
+ * when the coefficient bounds A_a, A_b (sums of |q_t| max|x_t|, which bound
+ * every partial sum) are below 2^31 ("narrow"), else in int64.  A zero
+ * projection is a tight point.  Otherwise the bucket floor(key B/2) of the
+ * exact direction h is read from binary32: the conversions of h (at most 2u
+ * each), the sum, the reciprocal (1 ulp) and the product and fma put the
+ * computed key within about 11u of the exact one, so when the interval of
+ * +-32u around it stays inside one bucket that bucket is the exact one.
+ * Keys that close to a boundary (and exact boundary directions) take the
+ * exact search td_exact_bucket.  Returns the number of tight points. */
+template <int D>
+__device__ __forceinline__ int td_exact_pass(const float *xs, int lp, int chm, uint32_t *hist, uint16_t *bid,
+                                             const uint16_t *list, int nu, const int64_t *qa, const int64_t *qb,
+                                             const int32_t *q32, bool narrow, int B, int lane)
+{
+    constexpr int PS = D <= 4 ? 4 : 8;
+    const float halfB = (float)(B >> 1);
+    const float dB = 32.0f * TD_U * halfB;
+    int t = 0;
+    for (int l0 = 0; l0 < nu; l0 += 32) {
+        const int l = l0 + lane;
+        const bool act = l < nu;
+        const int i = act ? (int)list[l] : 0;
+        float x[D];
+        td_load_point<D>(xs, PS, i, x);
+        int64_t Y1, Y2;
+        float f1, f2;
+        bool plus;
+        int64_t h1, h2;
+        if (narrow) {
+            uint32_t qa32[D], qb32[D];
+            td_load_pair<D>(q32, qa32, qb32);
+            int32_t a = 0, b = 0;
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                const int32_t xv = td_f2i(x[r]);
+                a += (int32_t)qa32[r] * xv;
+                b += (int32_t)qb32[r] * xv;
+            }
+            plus = (b > 0) || (b == 0 && a > 0);
+            const int32_t g1 = plus ? a : -a, g2 = plus ? b : -b;
+            f1 = __int2float_rn(g1);
+            f2 = __int2float_rn(g2);
+            Y1 = a;
+            Y2 = b;
+            h1 = g1;
+            h2 = g2;
+        } else {
+            Y1 = 0;
+            Y2 = 0;
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                const int64_t xv = td_f2i(x[r]);
+                Y1 += qa[r] * xv;
+                Y2 += qb[r] * xv;
+            }
+            plus = td_normalise(Y1, Y2, h1, h2);
+            f1 = td_i64_to_f32(h1);
+            f2 = td_i64_to_f32(h2);
+        }
+        const bool zero = (Y1 == 0) & (Y2 == 0);
+        /* h != 0 gives |f1| + f2 > 0, so rr and kb are finite */
+        const float rr = td_rcp(fabsf(f1) + f2);
+        const float kb = fmaf(-f1, rr * halfB, halfB);
+        const int flo = td_floor_bits(kb - dB), fhi = td_floor_bits(kb + dB);
+        int b = flo - 0x4B400000;
+        const bool need = act & !zero & !((flo == fhi) & ((unsigned)b < (unsigned)B));
+        if (__any_sync(TD_FULL, need)) {
+            if (need) {
+                const int bb = td_floor_bits(kb) - 0x4B400000;
+                b = td_exact_bucket(h1, h2, max(0, min(bb, B - 1)), B);
+            }
+        }
+        if (act) {
+            if (zero) {
+                bid[i] = (uint16_t)TD_SENT;
+                ++t;
+            } else {
+                bid[i] = (uint16_t)b;
+                atomicAdd(&hist[td_phys(b, lp, chm)], plus ? 0x10000u : 1u);
+            }
+        }
+    }
+    return td_wsum(t);
 }
 
 /* exact normalised projection of point i from the published basis */
@@ -835,11 +905,100 @@ struct TdWarpSmem {
     uint16_t *bid;    /* bucket of each point (TD_SENT = tight) */
     uint16_t *glist;  /* uncertain points, then gathered items */
     int *gcount;
-    int64_t *qa, *qb; /* exact basis of the current subset (for the out-of-line paths) */
+    int64_t *qa, *qb; /* exact basis of the current subset */
     int *meta;        /* rows[0..3] (intrinsic coordinates), sub[4..7] (subset point ids) */
+    float *fab;       /* basis rounded to binary32: fa at [0, D), fb at [8, 8 + D) */
+    int32_t *q32;     /* basis truncated to int32 (exact when narrow): qa at [0, D), qb at [8, 8 + D) */
 };
 
-#define TD_WARP_META_BYTES (2 * TD_MAXD * 8 + 8 * 4)
+/* qa, qb (2 x 6 int64), meta (8 int), fab (16 float), q32 (16 int) */
+#define TD_WARP_META_BYTES (2 * TD_MAXD * 8 + 8 * 4 + 16 * 4 + 16 * 4)
+
+/* Cooperative subset basis, published to the warp's shared block.  Lane l <
+ * C(D,2) computes the Plucker coordinate P of the l-th row pair (i, j) in
+ * lexicographic order: the entries Q_ij = P, Q_ji = -P of the antisymmetric
+ * integer matrix whose columns are functionals vanishing on span S.  The warp
+ * picks a pair (a, b) with P_ab != 0 and |P_ab| largest up to binary32
+ * rounding (one max-reduction of a 32-bit key; any nonzero P_ab gives a
+ * valid basis), and the lanes whose pair holds a or b write columns a and b:
+ * exact, truncated to int32, and rounded to binary32.  Lanes 16.. write the
+ * intrinsic coordinates (the rows other than a and b) and the subset.
+ * Returns false (uniformly) when every P vanishes (rank < K). */
+template <int D>
+__device__ __forceinline__ bool td_basis_publish(const float *xs, int PS, const int (&c)[D > 2 ? D - 2 : 1],
+                                                 int lane, const TdWarpSmem &W)
+{
+    constexpr int K = D - 2;
+    constexpr int NP = D * (D - 1) / 2;
+    int pi = 0, pj = 1;
+    {
+        int l = lane < NP ? lane : 0;
+#pragma unroll
+        for (int aa = 0; aa < D - 1; ++aa) {
+            const int cnt = D - 1 - aa;
+            if (l >= 0 && l < cnt) {
+                pi = aa;
+                pj = aa + 1 + l;
+            }
+            l -= cnt;
+        }
+    }
+    int64_t m[K > 0 ? K : 1][K > 0 ? K : 1];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        int r = i;
+        r += (r >= pi);
+        r += (r >= pj);
+#pragma unroll
+        for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[(size_t)c[j] * PS + r]);
+    }
+    const int64_t M = td_detk<K>(m);
+    int64_t P = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
+    if (lane >= NP) P = 0;
+    const uint32_t key =
+        P != 0 ? ((__float_as_uint(td_i64_to_f32(P < 0 ? -P : P)) & ~31u) | (uint32_t)(31 - lane)) : 0u;
+    const uint32_t kmax = __reduce_max_sync(TD_FULL, key);
+    if (kmax == 0u) return false;
+    const int wl = 31 - (int)(kmax & 31u);
+    const int a = __shfl_sync(TD_FULL, pi, wl), b = __shfl_sync(TD_FULL, pj, wl);
+    __syncwarp();
+    if (lane < NP) {
+        if (pi == a || pj == a) {
+            const int t = pi == a ? pj : pi;
+            const int64_t v = t < a ? P : -P;
+            W.qa[t] = v;
+            W.q32[t] = (int32_t)v;
+            W.fab[t] = td_i64_to_f32(v);
+        }
+        if (pi == b || pj == b) {
+            const int t = pi == b ? pj : pi;
+            const int64_t v = t < b ? P : -P;
+            W.qb[t] = v;
+            W.q32[8 + t] = (int32_t)v;
+            W.fab[8 + t] = td_i64_to_f32(v);
+        }
+    }
+    if (lane == 31) {
+        W.qa[a] = 0;
+        W.qb[b] = 0;
+        W.q32[a] = 0;
+        W.q32[8 + b] = 0;
+        W.fab[a] = 0.0f;
+        W.fab[8 + b] = 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        if (lane == 16 + r) {
+            int rr = r;
+            rr += (rr >= a);
+            rr += (rr >= b);
+            W.meta[r] = rr;
+        }
+        if (lane == 20 + r) W.meta[4 + r] = c[r];
+    }
+    __syncwarp();
+    return true;
+}
 
 /* Publish the exact basis and the subset to the warp's shared area. */
 template <int D>
@@ -933,18 +1092,23 @@ __device__ __noinline__ void td_resolve_many(const float *xs, int PS, const int6
  * points (nonzero points of span S) and the number of nonzero projections.
  *
  * FP32 certification of a point's bucket: with E >= |y_f - y| (both
- * coordinates), |y2_f| > E fixes the orientation, and for s = |y1_f|+|y2_f| > 4E
- * the pseudo-angle key = 1 - h1/(|h1|+h2) of the exact point differs from the
+ * coordinates), for s = |y1_f|+|y2_f| > 4E and a correct orientation the
+ * pseudo-angle key = 1 - h1/(|h1|+h2) of the exact point differs from the
  * computed one by at most E/(s-2E) <= 2E/s (the key is 1/s-Lipschitz in the
  * max norm of its argument) plus at most ~10 rounding errors of values <= 2
  * (reciprocal within 2 ulp, products, sums, the +-delta below); delta =
  * 2E/s + 24u covers both.  The bucket floor(key * B/2) is certain when
- * floor((key - delta) B/2) == floor((key + delta) B/2) and lies in [0, B). */
+ * floor((key - delta) B/2) == floor((key + delta) B/2) and lies in [0, B).
+ * That test also fixes the orientation: it can be wrong only when
+ * |y2_f| <= E, and then the computed key lies within E/s (plus rounding) of
+ * 0 or of 2, so key - delta < 0 or key + delta > 2 and the two floors differ
+ * (for y1_f = 0 the interval is wider than B; s = 0 gives NaN or an
+ * infinite key, which fails the range test). */
 template <int D>
-__device__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz, const TdBasis<D> &Bs,
-                                 const float (&fa)[D], const float (&fb)[D], float Ea, float Eb,
-                                 const TdWarpSmem &W, int blog2, int lane, int best, TdWarpStats &st,
-                                 int &t_out, int &nzy_out)
+__device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz,
+                                                 const float (&fa)[D], const float (&fb)[D], float Ea, float Eb,
+                                                 bool narrow, const TdWarpSmem &W, int blog2, int lane, int best,
+                                                 uint64_t &n_exact, uint32_t &n_resolved, int &t_out, int &nzy_out)
 {
     (void)PS_unused;
     constexpr int PS = D <= 4 ? 4 : 8;      /* staged point stride (floats) */
@@ -1012,7 +1176,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz, const 
              * or NaN: it never yields one in-range bucket, so no separate test. */
             const int flo = td_floor_bits(kb - db), fhi = td_floor_bits(kb + db);
             const int bl = flo - 0x4B400000;
-            okv[u] = vv[u] & (fabsf(y2) > Eb) & (flo == fhi) & ((unsigned)bl < (unsigned)B);
+            okv[u] = vv[u] & (flo == fhi) & ((unsigned)bl < (unsigned)B);
             slot[u] = okv[u] ? bl : B;
             /* +1 event (orientation -): 1; -1 event (orientation +): 1 << 16 */
             inc[u] = (uint32_t)(0x10000 + (__float_as_int(y2) >> 31) * 0xFFFF);
@@ -1044,12 +1208,9 @@ __device__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz, const 
     int t = 0;
     if (nu > 0) {
         __syncwarp();
-        td_exact_pass<D>(xs, PS, lp, chm, W.hist, W.bid, W.glist, nu, W.qa, W.qb, B, lane, &t);
+        t = td_exact_pass<D>(xs, lp, chm, W.hist, W.bid, W.glist, nu, W.qa, W.qb, W.q32, narrow, B, lane);
     }
-    if (lane == 0) {
-        st.exact += nu;
-        st.filtered += nnz - nu;
-    }
+    n_exact += (uint64_t)nu;
     const int nzy = nnz - t;
     t_out = t;
     nzy_out = nzy;
@@ -1143,7 +1304,7 @@ __device__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz, const 
         if (need_lo) mn2 = mn;
         if (need_hi) mx2 = mx;
         if (need_lo || need_hi) {
-            if (lane == 0) st.resolved++;
+            ++n_resolved;
             /* flag the candidate buckets with their start value (counts stay
              * below 2^15, so bit 31 is free) */
             auto cand = [&](int Pb, int cp, int cm) -> bool {
@@ -1203,11 +1364,8 @@ __device__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz, const 
                 int64_t h1 = 0, h2 = 0;
                 if (lane < Gn) {
                     const int i = W.glist[lane];
-                    float xg[D];
-                    td_load_point<D>(xs, PS, i, xg);
-                    int64_t Y1, Y2;
-                    td_exact_y<D>(Bs, xg, Y1, Y2);
-                    const bool pl = td_normalise(Y1, Y2, h1, h2);
+                    bool pl;
+                    td_exact_h<D>(xs, PS, i, W.qa, W.qb, h1, h2, pl);
                     e = pl ? -1 : 1;
                     bk = W.bid[i];
                     Pb = (int)(W.hist[td_phys(bk, lp, chm)] & 0xFFFFu);
@@ -1329,11 +1487,14 @@ __device__ __noinline__ int td_tight_correction(const int *meta, const float *xs
     }
 }
 
-/* Process subset positions [r0, r1) of query q with one warp (filtered). */
+/* Process subset positions [r0, r1) of query q with one warp (filtered).
+ * The warp's counters ws[] (sweeps, dependent, filtered points, exact
+ * points, tight corrections, resolved sweeps, errors) live in shared memory;
+ * the subset loop keeps 32-bit tile counts and lane 0 adds them at the end. */
 template <int D>
 __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int PS, int nnz,
                                  uint64_t r0, uint64_t r1, const TdWarpSmem &W, const TdScratch &scr,
-                                 int blog2, int lane, int &best, TdWarpStats &st)
+                                 int blog2, int lane, int &best, unsigned long long *ws)
 {
     constexpr int K = D - 2;
     if (r0 >= r1) return;
@@ -1341,41 +1502,56 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     int c[K > 0 ? K : 1];
     c[0] = 0;
     td_unrank_colex<K>(r0, nnz, c);
-    int mx[D];
+    float mxf[D];
 #pragma unroll
-    for (int r = 0; r < D; ++r) mx[r] = Q.mx[r];
+    for (int r = 0; r < D; ++r) mxf[r] = (float)Q.mx[r]; /* < 2^22: exact */
+    uint32_t n_dep = 0, n_tight = 0, n_res = 0;
+    uint64_t n_exact = 0;
+    /* forward error bound of the FP32 projection: the fma chain adds at most
+     * D u sum |q_i x_i|, the rounded coefficients (at most 2u each, see
+     * td_i64_to_f32) 2u more; taken as (D + 3) u, applied to A = sum |q_i|
+     * max|x_i| computed in binary32 from the rounded coefficients (relative
+     * error below (D + 2) u), the extra factor 1 + 2^-10 covering that and
+     * the rounding of the products below */
+    const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
     for (uint64_t r = r0; r < r1; ++r) {
         if (r > r0) td_next_colex<K>(c);
-        TdBasis<D> Bs;
-        if (!td_make_basis_coop<D>(xs, PS, c, lane, Bs)) {
-            if (lane == 0) st.dependent++;
+        if (!td_basis_publish<D>(xs, PS, c, lane, W)) {
+            ++n_dep;
             continue;
         }
-        if (lane == 0) st.sweeps++;
-        td_publish_basis<D>(Bs, c, W.qa, W.qb, W.meta, lane);
+        uint32_t ua[D], ub[D];
+        td_load_pair<D>(W.fab, ua, ub);
         float fa[D], fb[D];
-        int64_t Aa = 0, Ab = 0;
+        float Aa = 0.0f, Ab = 0.0f;
 #pragma unroll
         for (int t = 0; t < D; ++t) {
-            fa[t] = td_i64_to_f32(Bs.qa[t]);
-            fb[t] = td_i64_to_f32(Bs.qb[t]);
-            Aa += (Bs.qa[t] < 0 ? -Bs.qa[t] : Bs.qa[t]) * (int64_t)mx[t];
-            Ab += (Bs.qb[t] < 0 ? -Bs.qb[t] : Bs.qb[t]) * (int64_t)mx[t];
+            fa[t] = __uint_as_float(ua[t]);
+            fb[t] = __uint_as_float(ub[t]);
+            Aa = fmaf(fabsf(fa[t]), mxf[t], Aa);
+            Ab = fmaf(fabsf(fb[t]), mxf[t], Ab);
         }
-        /* forward error bound of the FP32 projection: the fma chain adds at
-         * most D u sum |q_i x_i|, the rounded coefficients (at most 2u each,
-         * see td_i64_to_f32) 2u more; taken as (D + 3) u, with the rounding of
-         * the bound itself covered by the extra factor 1 + 2^-10 */
-        const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
-        const float Ea = td_i64_to_f32(Aa) * cst, Eb = td_i64_to_f32(Ab) * cst;
+        const float Ea = Aa * cst, Eb = Ab * cst;
+        /* exact bounds below 2^31 (the binary32 sums are within (D + 2) u) */
+        const bool narrow = fmaxf(Aa, Ab) < 2145386496.0f; /* 2^31 (1 - 2^-10) */
         int t, nzy;
-        const int G = td_sweep_filtered<D>(xs, PS, nnz, Bs, fa, fb, Ea, Eb, W, blog2, lane, best, st, t, nzy);
+        const int G = td_sweep_filtered<D>(xs, PS, nnz, fa, fb, Ea, Eb, narrow, W, blog2, lane, best, n_exact,
+                                           n_res, t, nzy);
         int V = G;
         if (t > K && G < best) {
-            if (lane == 0) st.tight++;
+            ++n_tight;
             V = G + td_tight_correction<D>(W.meta, xs, PS, nullptr, 0, nnz, W.bid, nullptr, scr, W.gcount, lane);
         }
         best = min(best, V);
+    }
+    if (lane == 0) {
+        const uint64_t sw = (r1 - r0) - n_dep;
+        ws[0] += sw;
+        ws[1] += n_dep;
+        ws[2] += sw * (uint64_t)nnz - n_exact;
+        ws[3] += n_exact;
+        ws[4] += n_tight;
+        ws[5] += n_res;
     }
 }
 
@@ -1405,6 +1581,7 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
     __shared__ int64_t s_tile;
     __shared__ int s_tmp[32];
     __shared__ int s_best[TD_WARPS_MAX];
+    __shared__ unsigned long long s_stats[TD_WARPS_MAX][8];
     const int64_t *prefix = L.tile_prefix + (int64_t)(D - 2) * (L.nq + 1);
     unsigned long long *ticket = L.ticket + (D - 2) * TD_TICKET_STRIDE;
     const int64_t total = prefix[L.nq];
@@ -1430,11 +1607,14 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
     W.qa = reinterpret_cast<int64_t *>(wb + hbytes + (size_t)nmaxp * 4 + 16);
     W.qb = W.qa + TD_MAXD;
     W.meta = reinterpret_cast<int *>(W.qb + TD_MAXD);
+    W.fab = reinterpret_cast<float *>(W.meta + 8);
+    W.q32 = reinterpret_cast<int32_t *>(W.fab + 16);
     for (int j = lane; j < Bmax + 4; j += 32) W.hist[j] = 0u;
     const int gw = blockIdx.x * (blockDim.x >> 5) + w;
     /* the global scratch keeps the host's sizing (td_scratch_per_warp(nmax)) */
     const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, td_pow2_at_least(L.nmax));
-    TdWarpStats st = { 0, 0, 0, 0, 0, 0, 0 };
+    unsigned long long *ws = s_stats[w];
+    if (lane < 8) ws[lane] = 0ull;
     int staged = -1;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(ticket, 1ull);
@@ -1459,9 +1639,9 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
         while ((2 << blog2) < nnz && blog2 < blog2_cap) ++blog2;
         int best = L.qmin[q];
         if (Q.d == D && blog2 <= blog2_cap && nnz <= L.nmax)
-            td_warp_filtered<D>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, st);
+            td_warp_filtered<D>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, ws);
         else if (lane == 0)
-            st.errors++; /* inconsistent sizes: skip, the host reports TD_ERR_INTERNAL */
+            ws[6]++; /* inconsistent sizes: skip, the host reports TD_ERR_INTERNAL */
         if (lane == 0) s_best[w] = best;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1471,13 +1651,13 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
         }
     }
     if (lane == 0) {
-        atomicAdd(&L.ctr->sweeps, st.sweeps);
-        atomicAdd(&L.ctr->dependent, st.dependent);
-        atomicAdd(&L.ctr->filtered_points, st.filtered);
-        atomicAdd(&L.ctr->exact_points, st.exact);
-        atomicAdd(&L.ctr->tight, st.tight);
-        atomicAdd(&L.ctr->resolved, st.resolved);
-        atomicAdd(&L.ctr->errors, st.errors);
+        atomicAdd(&L.ctr->sweeps, ws[0]);
+        atomicAdd(&L.ctr->dependent, ws[1]);
+        atomicAdd(&L.ctr->filtered_points, ws[2]);
+        atomicAdd(&L.ctr->exact_points, ws[3]);
+        atomicAdd(&L.ctr->tight, ws[4]);
+        atomicAdd(&L.ctr->resolved, ws[5]);
+        atomicAdd(&L.ctr->errors, ws[6]);
     }
 }
 

@@ -84,6 +84,13 @@ __device__ __forceinline__ float4 td_lds128(unsigned a)
     return v;
 }
 
+__device__ __forceinline__ unsigned td_ldsu16(unsigned a)
+{
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+
 __device__ __forceinline__ void td_sts16(unsigned a, unsigned short v)
 {
     asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
@@ -777,6 +784,20 @@ __device__ __forceinline__ int td_phys(int b, int lp, int chm)
     return b;
 }
 
+struct TdWarpSmem {
+    uint32_t *hist;   /* B packed counters: low 16 bits +1 events, high 16 bits -1 events */
+    uint16_t *bid;    /* bucket of each point (TD_SENT = tight) */
+    uint16_t *glist;  /* uncertain points, then gathered items */
+    int *gcount;
+    int64_t *qa, *qb; /* exact basis of the current subset */
+    int *meta;        /* rows[0..3] (intrinsic coordinates), sub[4..7] (subset point ids) */
+    float *fab;       /* basis rounded to binary32: fa at [0, D), fb at [8, 8 + D) */
+    int32_t *q32;     /* basis truncated to int32 (exact when narrow): qa at [0, D), qb at [8, 8 + D) */
+};
+
+/* qa, qb (2 x 6 int64), meta (8 int), fab (16 float), q32 (16 int) */
+#define TD_WARP_META_BYTES (2 * TD_MAXD * 8 + 8 * 4 + 16 * 4 + 16 * 4)
+
 /* the two basis columns from the warp's shared block (32-bit words: qa at
  * [0, D), qb at [8, 8 + D), 16-byte aligned) */
 template <int D>
@@ -798,38 +819,48 @@ __device__ __forceinline__ void td_load_pair(const void *src, uint32_t (&a)[D], 
 }
 
 /* Exact placement of the points the FP32 filter could not certify (their ids
- * are in list[0..nu)), one point per lane.  The projection is exact: in int32
- * when the coefficient bounds A_a, A_b (sums of |q_t| max|x_t|, which bound
- * every partial sum) are below 2^31 ("narrow"), else in int64.  A zero
- * projection is a tight point.  Otherwise the bucket floor(key B/2) of the
- * exact direction h is read from binary32: the conversions of h (at most 2u
- * each), the sum, the reciprocal (1 ulp) and the product and fma put the
- * computed key within about 11u of the exact one, so when the interval of
- * +-32u around it stays inside one bucket that bucket is the exact one.
- * Keys that close to a boundary (and exact boundary directions) take the
- * exact search td_exact_bucket.  Returns the number of tight points. */
-template <int D>
-__device__ __forceinline__ int td_exact_pass(const float *xs, int lp, int chm, uint32_t *hist, uint16_t *bid,
-                                             const uint16_t *list, int nu, const int64_t *qa, const int64_t *qb,
-                                             const int32_t *q32, bool narrow, int B, int lane)
+ * are in W.glist[0..nu)), one point per lane.  The projection is exact: in
+ * int32 when the coefficient bounds A_a, A_b (sums of |q_t| max|x_t|, which
+ * bound every partial sum) are below 2^31 (NARROW), else in int64.  A zero
+ * projection is a tight point.  Otherwise the bucket of the exact direction
+ * h is j = floor(B (s - h1) / (2 s)) with s = |h1| + h2, i.e. floor(key B/2).
+ * The binary32 key is within about 11u of the exact one (conversions of h,
+ * the sum, the reciprocal, the fma), far less than a bucket, so its floor j0
+ * is j, j - 1 or j + 1; one exact comparison of B (s - h1) with 2 s j0 and
+ * 2 s (j0 + 1) (64-bit products when NARROW, 128-bit otherwise) settles it.
+ * The boundary search td_exact_bucket remains as a guard that never runs
+ * while that error bound holds.  Returns the number of tight points. */
+template <int D, bool NARROW>
+__device__ __forceinline__ int td_exact_pass(const float *xs, const TdWarpSmem &W, int nu, int blog2, int lane)
 {
-    constexpr int PS = D <= 4 ? 4 : 8;
-    const float halfB = (float)(B >> 1);
-    const float dB = 32.0f * TD_U * halfB;
+    constexpr unsigned PB = D <= 4 ? 16u : 32u; /* staged point stride in bytes */
+    const int B = 1 << blog2;
+    const float Mb = __int_as_float(0x4B400000 - ((blog2 - 1) << 23)); /* spacing 2/B, see td_sweep_filtered */
+    const int Mbits = __float_as_int(Mb);
+    const unsigned xq = td_saddr(xs), lq = td_saddr(W.glist), hq = td_saddr(W.hist), bq = td_saddr(W.bid);
     int t = 0;
     for (int l0 = 0; l0 < nu; l0 += 32) {
         const int l = l0 + lane;
         const bool act = l < nu;
-        const int i = act ? (int)list[l] : 0;
+        const unsigned i = act ? td_ldsu16(lq + 2u * (unsigned)l) : 0u;
+        const float4 a4 = td_lds128(xq + i * PB);
         float x[D];
-        td_load_point<D>(xs, PS, i, x);
-        int64_t Y1, Y2;
+        x[0] = a4.x;
+        if (D > 1) x[1] = a4.y;
+        if (D > 2) x[2] = a4.z;
+        if (D > 3) x[3] = a4.w;
+        if (D > 4) {
+            const float4 b4 = td_lds128(xq + i * PB + 16u);
+            x[4] = b4.x;
+            if (D > 5) x[5] = b4.y;
+        }
+        bool plus, zero, ok;
         float f1, f2;
-        bool plus;
         int64_t h1, h2;
-        if (narrow) {
+        int j;
+        if constexpr (NARROW) {
             uint32_t qa32[D], qb32[D];
-            td_load_pair<D>(q32, qa32, qb32);
+            td_load_pair<D>(W.q32, qa32, qb32);
             int32_t a = 0, b = 0;
 #pragma unroll
             for (int r = 0; r < D; ++r) {
@@ -837,48 +868,62 @@ __device__ __forceinline__ int td_exact_pass(const float *xs, int lp, int chm, u
                 a += (int32_t)qa32[r] * xv;
                 b += (int32_t)qb32[r] * xv;
             }
+            zero = (a | b) == 0;
             plus = (b > 0) || (b == 0 && a > 0);
             const int32_t g1 = plus ? a : -a, g2 = plus ? b : -b;
             f1 = __int2float_rn(g1);
             f2 = __int2float_rn(g2);
-            Y1 = a;
-            Y2 = b;
+            const float kb = fmaf(-f1, td_rcp(fabsf(f1) + f2), 1.0f);
+            j = min(max(__float_as_int(__fadd_rd(kb, Mb)) - Mbits, 0), B - 1);
+            /* s < 2^32, s - h1 < 2^33: num < 2^44, den * (j + 1) < 2^45 */
+            const int64_t s = (int64_t)(g1 < 0 ? -g1 : g1) + g2;
+            const int64_t num = (s - g1) << blog2, den = 2 * s;
+            int64_t lo = den * j;
+            if (num < lo) {
+                --j;
+                lo -= den;
+            } else if (num >= lo + den) {
+                ++j;
+                lo += den;
+            }
+            ok = zero || (lo <= num && num < lo + den);
             h1 = g1;
             h2 = g2;
         } else {
-            Y1 = 0;
-            Y2 = 0;
+            int64_t Y1 = 0, Y2 = 0;
 #pragma unroll
             for (int r = 0; r < D; ++r) {
                 const int64_t xv = td_f2i(x[r]);
-                Y1 += qa[r] * xv;
-                Y2 += qb[r] * xv;
+                Y1 += W.qa[r] * xv;
+                Y2 += W.qb[r] * xv;
             }
+            zero = (Y1 | Y2) == 0;
             plus = td_normalise(Y1, Y2, h1, h2);
             f1 = td_i64_to_f32(h1);
             f2 = td_i64_to_f32(h2);
-        }
-        const bool zero = (Y1 == 0) & (Y2 == 0);
-        /* h != 0 gives |f1| + f2 > 0, so rr and kb are finite */
-        const float rr = td_rcp(fabsf(f1) + f2);
-        const float kb = fmaf(-f1, rr * halfB, halfB);
-        const int flo = td_floor_bits(kb - dB), fhi = td_floor_bits(kb + dB);
-        int b = flo - 0x4B400000;
-        const bool need = act & !zero & !((flo == fhi) & ((unsigned)b < (unsigned)B));
-        if (__any_sync(TD_FULL, need)) {
-            if (need) {
-                const int bb = td_floor_bits(kb) - 0x4B400000;
-                b = td_exact_bucket(h1, h2, max(0, min(bb, B - 1)), B);
+            const float kb = fmaf(-f1, td_rcp(fabsf(f1) + f2), 1.0f);
+            j = min(max(__float_as_int(__fadd_rd(kb, Mb)) - Mbits, 0), B - 1);
+            /* |h| < 2^62: exact in 128 bits */
+            const td_i128 s = (td_i128)(h1 < 0 ? -h1 : h1) + h2;
+            const td_i128 num = (s - h1) << blog2, den = 2 * s;
+            td_i128 lo = den * j;
+            if (num < lo) {
+                --j;
+                lo -= den;
+            } else if (num >= lo + den) {
+                ++j;
+                lo += den;
             }
+            ok = zero || (lo <= num && num < lo + den);
+        }
+        const bool need = act & !ok;
+        if (__any_sync(TD_FULL, need)) {
+            if (need) j = td_exact_bucket(h1, h2, max(0, min(j, B - 1)), B);
         }
         if (act) {
-            if (zero) {
-                bid[i] = (uint16_t)TD_SENT;
-                ++t;
-            } else {
-                bid[i] = (uint16_t)b;
-                atomicAdd(&hist[td_phys(b, lp, chm)], plus ? 0x10000u : 1u);
-            }
+            td_sts16(bq + 2u * i, (unsigned short)(zero ? TD_SENT : (unsigned)j));
+            if (!zero) td_reds_add(hq + 4u * (unsigned)j, plus ? 0x10000u : 1u);
+            t += zero;
         }
     }
     return td_wsum(t);
@@ -900,19 +945,6 @@ __device__ __forceinline__ void td_exact_h(const float *xs, int PS, int i, const
     plus = td_normalise(Y1, Y2, h1, h2);
 }
 
-struct TdWarpSmem {
-    uint32_t *hist;   /* B packed counters: low 16 bits +1 events, high 16 bits -1 events */
-    uint16_t *bid;    /* bucket of each point (TD_SENT = tight) */
-    uint16_t *glist;  /* uncertain points, then gathered items */
-    int *gcount;
-    int64_t *qa, *qb; /* exact basis of the current subset */
-    int *meta;        /* rows[0..3] (intrinsic coordinates), sub[4..7] (subset point ids) */
-    float *fab;       /* basis rounded to binary32: fa at [0, D), fb at [8, 8 + D) */
-    int32_t *q32;     /* basis truncated to int32 (exact when narrow): qa at [0, D), qb at [8, 8 + D) */
-};
-
-/* qa, qb (2 x 6 int64), meta (8 int), fab (16 float), q32 (16 int) */
-#define TD_WARP_META_BYTES (2 * TD_MAXD * 8 + 8 * 4 + 16 * 4 + 16 * 4)
 
 /* Cooperative subset basis, published to the warp's shared block.  Lane l <
  * C(D,2) computes the Plucker coordinate P of the l-th row pair (i, j) in
@@ -1116,12 +1148,17 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
     const int lp = blog2 - 5;               /* log2 buckets per lane */
     const int nch = 1 << (lp - 2);          /* chunks of four per lane */
     const int chm = nch - 1;
-    const float halfB = (float)(B >> 1);
     const float E = fmaxf(Ea, Eb);
-    const float cE = 2.0f * E * halfB;
-    const float cU = 24.0f * TD_U * halfB;
+    const float cE = 2.0f * E;
+    const float cU = 24.0f * TD_U;
+    /* Bucket floors by the magic-constant addition on the unscaled key: in
+     * the binade of Mb = 1.5 * 2^23 / (B/2) the spacing of binary32 is 2/B,
+     * so bits(round_down(v + Mb)) - bits(Mb) = floor(v B/2) for v in
+     * (-Mb/3, 2 Mb/3).  This is the scaled-by-(B/2) computation with every
+     * rounding scaled by the same power of two. */
+    const float Mb = __int_as_float(0x4B400000 - ((blog2 - 1) << 23));
+    const int Mbits = __float_as_int(Mb);
     const unsigned below = (1u << lane) - 1u;
-    (void)below;
     /* Placement of UNR points per lane per round: the common path (certified
      * bucket: one bucket id store and one shared atomic) is predicated; the
      * rare uncertain points are appended to W.glist under a warp-uniform
@@ -1166,16 +1203,16 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
                 y2 = fmaf(fb[r], x[r], y2);
             }
             /* the orientation rides on the sign of the divisor: with
-             * s' = sign(y2) (|y1| + |y2|), key * B/2 = B/2 - y1 * (B/2) / s' */
+             * s' = sign(y2) (|y1| + |y2|), key = 1 - y1 / s' */
             const float sg = copysignf(fabsf(y1) + fabsf(y2), y2);
             const float rr = td_rcp(sg);
-            const float kb = fmaf(-y1, rr * halfB, halfB); /* key * B/2 */
-            const float db = fmaf(cE, fabsf(rr), cU);      /* delta * B/2 */
-            /* Floors by the magic-constant addition.  When |y1|+|y2| <= 4E the
-             * interval is at least B/4 wide, or outside the conversion window,
-             * or NaN: it never yields one in-range bucket, so no separate test. */
-            const int flo = td_floor_bits(kb - db), fhi = td_floor_bits(kb + db);
-            const int bl = flo - 0x4B400000;
+            const float kb = fmaf(-y1, rr, 1.0f);     /* key */
+            const float db = fmaf(cE, fabsf(rr), cU); /* delta */
+            /* When |y1|+|y2| <= 4E the interval is at least 1/2 wide, or
+             * outside the conversion window, or NaN: it never yields one
+             * in-range bucket, so no separate test. */
+            const int flo = __float_as_int(__fadd_rd(kb - db, Mb)), fhi = __float_as_int(__fadd_rd(kb + db, Mb));
+            const int bl = flo - Mbits;
             okv[u] = vv[u] & (flo == fhi) & ((unsigned)bl < (unsigned)B);
             slot[u] = okv[u] ? bl : B;
             /* +1 event (orientation -): 1; -1 event (orientation +): 1 << 16 */
@@ -1186,18 +1223,15 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
             td_sts16(bq + 2u * (unsigned)(i0 + 32 * u), (unsigned short)slot[u]);
             td_reds_add(hq + 4u * (unsigned)slot[u], inc[u]);
         }
-        unsigned bad[UNR];
-        unsigned any = 0;
+        bool badl = false;
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            bad[u] = __ballot_sync(TD_FULL, vv[u] & !okv[u]);
-            any |= bad[u];
-        }
-        if (any) {
+        for (int u = 0; u < UNR; ++u) badl |= vv[u] & !okv[u];
+        if (__any_sync(TD_FULL, badl)) {
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
-                if ((bad[u] >> lane) & 1u) W.glist[nu + __popc(bad[u] & below)] = (uint16_t)(i0 + 32 * u + lane);
-                nu += __popc(bad[u]);
+                const unsigned bad = __ballot_sync(TD_FULL, vv[u] & !okv[u]);
+                if ((bad >> lane) & 1u) W.glist[nu + __popc(bad & below)] = (uint16_t)(i0 + 32 * u + lane);
+                nu += __popc(bad);
             }
         }
     };
@@ -1208,7 +1242,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
     int t = 0;
     if (nu > 0) {
         __syncwarp();
-        t = td_exact_pass<D>(xs, lp, chm, W.hist, W.bid, W.glist, nu, W.qa, W.qb, W.q32, narrow, B, lane);
+        t = narrow ? td_exact_pass<D, true>(xs, W, nu, blog2, lane) : td_exact_pass<D, false>(xs, W, nu, blog2, lane);
     }
     n_exact += (uint64_t)nu;
     const int nzy = nnz - t;

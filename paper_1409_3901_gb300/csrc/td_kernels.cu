@@ -96,6 +96,13 @@ __device__ __forceinline__ void td_sts16(unsigned a, unsigned short v)
     asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned td_atoms_add(unsigned a, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ void td_reds_add(unsigned a, unsigned v)
 {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
@@ -956,34 +963,46 @@ __device__ __forceinline__ void td_exact_h(const float *xs, int PS, int i, const
  * exact, truncated to int32, and rounded to binary32.  Lanes 16.. write the
  * intrinsic coordinates (the rows other than a and b) and the subset.
  * Returns false (uniformly) when every P vanishes (rank < K). */
+/* The row pair (pi, pj) of lane l < C(D,2) in lexicographic order, and the
+ * other K rows lr[] (those of its minor); lanes past C(D,2) get pair (0, 1). */
 template <int D>
-__device__ __forceinline__ bool td_basis_publish(const float *xs, int PS, const int (&c)[D > 2 ? D - 2 : 1],
-                                                 int lane, const TdWarpSmem &W)
+__device__ __forceinline__ void td_lane_pair(int lane, int &pi, int &pj, int (&lr)[D > 2 ? D - 2 : 1])
 {
-    constexpr int K = D - 2;
     constexpr int NP = D * (D - 1) / 2;
-    int pi = 0, pj = 1;
-    {
-        int l = lane < NP ? lane : 0;
+    pi = 0;
+    pj = 1;
+    int l = lane < NP ? lane : 0;
 #pragma unroll
-        for (int aa = 0; aa < D - 1; ++aa) {
-            const int cnt = D - 1 - aa;
-            if (l >= 0 && l < cnt) {
-                pi = aa;
-                pj = aa + 1 + l;
-            }
-            l -= cnt;
+    for (int aa = 0; aa < D - 1; ++aa) {
+        const int cnt = D - 1 - aa;
+        if (l >= 0 && l < cnt) {
+            pi = aa;
+            pj = aa + 1 + l;
         }
+        l -= cnt;
     }
-    int64_t m[K > 0 ? K : 1][K > 0 ? K : 1];
+    lr[0] = 0;
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
+    for (int i = 0; i < D - 2; ++i) {
         int r = i;
         r += (r >= pi);
         r += (r >= pj);
-#pragma unroll
-        for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[(size_t)c[j] * PS + r]);
+        lr[i] = r;
     }
+}
+
+template <int D>
+__device__ __forceinline__ bool td_basis_publish(const float *xs, int PS, const int (&c)[D > 2 ? D - 2 : 1],
+                                                 int lane, int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
+                                                 const TdWarpSmem &W)
+{
+    constexpr int K = D - 2;
+    constexpr int NP = D * (D - 1) / 2;
+    int64_t m[K > 0 ? K : 1][K > 0 ? K : 1];
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[(size_t)c[j] * PS + lr[i]]);
     const int64_t M = td_detk<K>(m);
     int64_t P = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
     if (lane >= NP) P = 0;
@@ -1165,7 +1184,9 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
      * branch.  All lanes run every round (indices past nnz are masked). */
     constexpr int UNR = 4;
     constexpr int PQ = PS / 4;                 /* float4 per staged point */
-    int nu = 0;
+    /* uncertain points are appended to W.glist through the counter
+     * W.gcount[0] (zero between sweeps) */
+    const unsigned gq = td_saddr(W.glist), cq = td_saddr(W.gcount);
     const unsigned xq = td_saddr(xs) + (unsigned)lane * (16u * PQ);   /* this lane's first point */
     const unsigned hq = td_saddr(W.hist);
     const unsigned bq = td_saddr(W.bid) + 2u * (unsigned)lane;
@@ -1228,20 +1249,17 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
         for (int u = 0; u < UNR; ++u) badl |= vv[u] & !okv[u];
         if (__any_sync(TD_FULL, badl)) {
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const unsigned bad = __ballot_sync(TD_FULL, vv[u] & !okv[u]);
-                if ((bad >> lane) & 1u) W.glist[nu + __popc(bad & below)] = (uint16_t)(i0 + 32 * u + lane);
-                nu += __popc(bad);
-            }
+            for (int u = 0; u < UNR; ++u)
+                if (vv[u] & !okv[u]) td_sts16(gq + 2u * td_atoms_add(cq, 1u), (unsigned short)(i0 + 32 * u + lane));
         }
     };
     const int nfull = nnz & ~(32 * UNR - 1);
     for (int i0 = 0; i0 < nfull; i0 += 32 * UNR) round(i0, false);
     if (nfull < nnz) round(nfull, true);
     __syncwarp();
+    const int nu = *(volatile int *)W.gcount;
     int t = 0;
     if (nu > 0) {
-        __syncwarp();
         t = narrow ? td_exact_pass<D, true>(xs, W, nu, blog2, lane) : td_exact_pass<D, false>(xs, W, nu, blog2, lane);
     }
     n_exact += (uint64_t)nu;
@@ -1459,6 +1477,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
     }
     __syncwarp();
     for (int k = 0; k < nch; ++k) h4[(k + rot) & chm] = make_uint4(0u, 0u, 0u, 0u);
+    if (lane == 0) W.gcount[0] = 0;
     __syncwarp();
     return G;
 }
@@ -1548,9 +1567,11 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
      * error below (D + 2) u), the extra factor 1 + 2^-10 covering that and
      * the rounding of the products below */
     const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
+    int pi, pj, lr[K > 0 ? K : 1];
+    td_lane_pair<D>(lane, pi, pj, lr);
     for (uint64_t r = r0; r < r1; ++r) {
         if (r > r0) td_next_colex<K>(c);
-        if (!td_basis_publish<D>(xs, PS, c, lane, W)) {
+        if (!td_basis_publish<D>(xs, PS, c, lane, pi, pj, lr, W)) {
             ++n_dep;
             continue;
         }
@@ -1638,6 +1659,7 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
     W.bid = reinterpret_cast<uint16_t *>(wb + hbytes);
     W.glist = W.bid + nmaxp;
     W.gcount = reinterpret_cast<int *>(W.glist + nmaxp);
+    if (lane == 0) W.gcount[0] = 0;
     W.qa = reinterpret_cast<int64_t *>(wb + hbytes + (size_t)nmaxp * 4 + 16);
     W.qb = W.qa + TD_MAXD;
     W.meta = reinterpret_cast<int *>(W.qb + TD_MAXD);

@@ -1258,15 +1258,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
     if (nfull < nnz) round(nfull, true);
     __syncwarp();
     const int nu = *(volatile int *)W.gcount;
-    int t = 0;
-    if (nu > 0) {
-        t = narrow ? td_exact_pass<D, true>(xs, W, nu, blog2, lane) : td_exact_pass<D, false>(xs, W, nu, blog2, lane);
-    }
     n_exact += (uint64_t)nu;
-    const int nzy = nnz - t;
-    t_out = t;
-    nzy_out = nzy;
-    __syncwarp();
 
     /* Pass 1: per-lane totals of the +1/-1 events, i.e. a histogram of 32
      * coarse buckets.  Inside lane l's range the walk stays within
@@ -1274,18 +1266,38 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
     uint4 *h4 = reinterpret_cast<uint4 *>(W.hist) + lane * nch;
     const int rot = lane & chm;
     const int per = B >> 5;
-    uint32_t acc = 0;
-    for (int k = 0; k < nch; ++k) {
-        const uint4 v = h4[(k + rot) & chm];
-        acc += v.x + v.y + v.z + v.w;
+    int Pl, lol, hil;
+    auto pass1 = [&](int nz) -> int {
+        uint32_t acc = 0;
+        for (int k = 0; k < nch; ++k) {
+            const uint4 v = h4[(k + rot) & chm];
+            acc += v.x + v.y + v.z + v.w;
+        }
+        const int cpl = (int)(acc & 0xFFFFu), cml = (int)(acc >> 16);
+        const int A = td_wsum(cml); /* orientation + points: one -1 event each */
+        const int netl = cpl - cml;
+        const int excl = td_wscan_incl(netl, lane) - netl;
+        Pl = A + excl;
+        lol = Pl - cml;
+        hil = Pl + cpl;
+        return min(td_wmin(lol), nz - td_wmax(hil));
+    };
+    /* First without the uncertain points (not yet in the histogram): for
+     * every direction the walk value w over all nonzero points is w_c + w_u
+     * with 0 <= w_u <= (uncertain nonzero points), so min(w, nzy - w) >=
+     * min(w_c, n_c - w_c) over the n_c = nnz - nu certified points.  Only
+     * when that bound does not reach best are the uncertain points placed
+     * exactly (and the tight points counted). */
+    int G = pass1(nnz - nu);
+    int t = 0;
+    if (G < best && nu > 0) {
+        t = narrow ? td_exact_pass<D, true>(xs, W, nu, blog2, lane) : td_exact_pass<D, false>(xs, W, nu, blog2, lane);
+        __syncwarp();
+        G = pass1(nnz - t);
     }
-    const int cpl = (int)(acc & 0xFFFFu), cml = (int)(acc >> 16);
-    const int A = td_wsum(cml); /* orientation + points: one -1 event each */
-    const int netl = cpl - cml;
-    const int excl = td_wscan_incl(netl, lane) - netl;
-    const int Pl = A + excl;
-    const int lol = Pl - cml, hil = Pl + cpl;
-    int G = min(td_wmin(lol), nzy - td_wmax(hil));
+    const int nzy = nnz - t;
+    t_out = t;
+    nzy_out = nzy;
     if (G < best) {
         /* Pass 2, only over the lanes whose range could hold a walk value
          * giving less than best (cooperatively, one bucket per lane, when

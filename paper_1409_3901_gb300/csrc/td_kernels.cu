@@ -1136,6 +1136,64 @@ __device__ __noinline__ void td_resolve_many(const float *xs, int PS, const int6
     *mx_io = max(*mx_io, lmx);
 }
 
+/* The FP32 bucket of one point (see the certification argument below):
+ * floor(key B/2) when the interval key +- delta lies in one bucket, else B
+ * (uncertain).  inc is the packed event of the point: 1 (+1 event,
+ * orientation -) or 1 << 16 (-1 event, orientation +).  Every operation is
+ * an explicitly rounded one, so the sweep loop and the rebuild of the bucket
+ * ids (td_refresh_bid) take the same decisions. */
+template <int D>
+__device__ __forceinline__ int td_point_slot(const float (&x)[D], const float (&fa)[D], const float (&fb)[D],
+                                             float cE, float cU, float Mb, int Mbits, int B, uint32_t &inc)
+{
+    float y1 = __fmul_rn(fa[0], x[0]), y2 = __fmul_rn(fb[0], x[0]);
+#pragma unroll
+    for (int r = 1; r < D; ++r) {
+        y1 = __fmaf_rn(fa[r], x[r], y1);
+        y2 = __fmaf_rn(fb[r], x[r], y2);
+    }
+    /* the orientation rides on the sign of the divisor: with
+     * s' = sign(y2) (|y1| + |y2|), key = 1 - y1 / s' */
+    const float sg = copysignf(__fadd_rn(fabsf(y1), fabsf(y2)), y2);
+    const float rr = td_rcp(sg);
+    const float kb = __fmaf_rn(-y1, rr, 1.0f);     /* key */
+    const float db = __fmaf_rn(cE, fabsf(rr), cU); /* delta */
+    /* When |y1|+|y2| <= 4E the interval is at least 1/2 wide, or outside the
+     * conversion window, or NaN: it never yields one in-range bucket, so no
+     * separate test. */
+    const int flo = __float_as_int(__fadd_rd(__fsub_rn(kb, db), Mb));
+    const int fhi = __float_as_int(__fadd_rd(__fadd_rn(kb, db), Mb));
+    const int bl = flo - Mbits;
+    inc = (uint32_t)(0x10000 + (__float_as_int(y2) >> 31) * 0xFFFF);
+    return ((flo == fhi) & ((unsigned)bl < (unsigned)B)) ? bl : B;
+}
+
+/* Rebuild the bucket ids of the certified points (the sweep loop does not
+ * store them); the ids of the uncertain points are the exact pass's.  The
+ * coefficients are the published binary32 basis, as in the sweep loop. */
+template <int D>
+__device__ __noinline__ void td_refresh_bid(const float *xs, int nnz, const TdWarpSmem &W, float cE, float cU,
+                                            float Mb, int Mbits, int B, int lane)
+{
+    constexpr int PS = D <= 4 ? 4 : 8;
+    uint32_t ua[D], ub[D];
+    td_load_pair<D>(W.fab, ua, ub);
+    float fa[D], fb[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+        fa[t] = __uint_as_float(ua[t]);
+        fb[t] = __uint_as_float(ub[t]);
+    }
+    for (int i = lane; i < nnz; i += 32) {
+        float x[D];
+        td_load_point<D>(xs, PS, i, x);
+        uint32_t inc;
+        const int s = td_point_slot<D>(x, fa, fb, cE, cU, Mb, Mbits, B, inc);
+        if (s < B) W.bid[i] = (uint16_t)s;
+    }
+    __syncwarp();
+}
+
 /* G(S) for one subset, FP32-filtered (the basis must be published to
  * W.qa/W.qb first).  Returns G(S) exactly whenever G(S) < best; otherwise it
  * may return any value >= best (the subset cannot lower the minimum, so the
@@ -1189,12 +1247,12 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
     const unsigned gq = td_saddr(W.glist), cq = td_saddr(W.gcount);
     const unsigned xq = td_saddr(xs) + (unsigned)lane * (16u * PQ);   /* this lane's first point */
     const unsigned hq = td_saddr(W.hist);
-    const unsigned bq = td_saddr(W.bid) + 2u * (unsigned)lane;
     /* One round places 32*UNR points, UNR per lane.  A point whose bucket is
      * not certified (or a padding lane of the last round) adds its event to
-     * the dummy bucket B, which no scan reads, so the atomic and the bucket
-     * id store need no branch; uncertain points are appended to W.glist
-     * under a warp-uniform branch and placed exactly afterwards. */
+     * the dummy bucket B, which no scan reads, so the atomic needs no branch;
+     * uncertain points are appended to W.glist under a warp-uniform branch
+     * and placed exactly afterwards.  Bucket ids are not stored here: the
+     * rare paths that read them rebuild them (td_refresh_bid). */
     auto round = [&](int i0, bool tail) {
         bool okv[UNR], vv[UNR];
         int slot[UNR];
@@ -1217,33 +1275,12 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
             if (D > 3) x[3] = a4[u].w;
             if (D > 4) x[4] = b4[u].x;
             if (D > 5) x[5] = b4[u].y;
-            float y1 = fa[0] * x[0], y2 = fb[0] * x[0];
-#pragma unroll
-            for (int r = 1; r < D; ++r) {
-                y1 = fmaf(fa[r], x[r], y1);
-                y2 = fmaf(fb[r], x[r], y2);
-            }
-            /* the orientation rides on the sign of the divisor: with
-             * s' = sign(y2) (|y1| + |y2|), key = 1 - y1 / s' */
-            const float sg = copysignf(fabsf(y1) + fabsf(y2), y2);
-            const float rr = td_rcp(sg);
-            const float kb = fmaf(-y1, rr, 1.0f);     /* key */
-            const float db = fmaf(cE, fabsf(rr), cU); /* delta */
-            /* When |y1|+|y2| <= 4E the interval is at least 1/2 wide, or
-             * outside the conversion window, or NaN: it never yields one
-             * in-range bucket, so no separate test. */
-            const int flo = __float_as_int(__fadd_rd(kb - db, Mb)), fhi = __float_as_int(__fadd_rd(kb + db, Mb));
-            const int bl = flo - Mbits;
-            okv[u] = vv[u] & (flo == fhi) & ((unsigned)bl < (unsigned)B);
-            slot[u] = okv[u] ? bl : B;
-            /* +1 event (orientation -): 1; -1 event (orientation +): 1 << 16 */
-            inc[u] = (uint32_t)(0x10000 + (__float_as_int(y2) >> 31) * 0xFFFF);
+            slot[u] = td_point_slot<D>(x, fa, fb, cE, cU, Mb, Mbits, B, inc[u]);
+            okv[u] = slot[u] < B;
+            if (tail && !vv[u]) slot[u] = B;
         }
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            td_sts16(bq + 2u * (unsigned)(i0 + 32 * u), (unsigned short)slot[u]);
-            td_reds_add(hq + 4u * (unsigned)slot[u], inc[u]);
-        }
+        for (int u = 0; u < UNR; ++u) td_reds_add(hq + 4u * (unsigned)slot[u], inc[u]);
         bool badl = false;
 #pragma unroll
         for (int u = 0; u < UNR; ++u) badl |= vv[u] & !okv[u];
@@ -1290,6 +1327,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
      * exactly (and the tight points counted). */
     int G = pass1(nnz - nu);
     int t = 0;
+    bool fresh = false; /* bucket ids rebuilt for this sweep */
     if (G < best && nu > 0) {
         t = narrow ? td_exact_pass<D, true>(xs, W, nu, blog2, lane) : td_exact_pass<D, false>(xs, W, nu, blog2, lane);
         __syncwarp();
@@ -1408,6 +1446,8 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
                 }
             }
             __syncwarp();
+            td_refresh_bid<D>(xs, nnz, W, cE, cU, Mb, Mbits, B, lane);
+            fresh = true;
             int Gn = 0;
             for (int i0 = 0; i0 < nnz; i0 += 32) {
                 const int i = i0 + lane;
@@ -1487,6 +1527,8 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
         }
         G = min(mn2, nzy - mx2);
     }
+    /* the tight-set correction reads the bucket ids */
+    if (t > D - 2 && G < best && !fresh) td_refresh_bid<D>(xs, nnz, W, cE, cU, Mb, Mbits, B, lane);
     __syncwarp();
     for (int k = 0; k < nch; ++k) h4[(k + rot) & chm] = make_uint4(0u, 0u, 0u, 0u);
     if (lane == 0) W.gcount[0] = 0;

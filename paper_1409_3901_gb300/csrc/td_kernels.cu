@@ -108,6 +108,72 @@ __device__ __forceinline__ void td_reds_add(unsigned a, unsigned v)
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
+/* Two binary32 values in one 64-bit register pair (low, high), operated on by
+ * the packed f32x2 instructions: each half is rounded exactly as the scalar
+ * operation would round it. */
+typedef unsigned long long td_f2x;
+
+__device__ __forceinline__ td_f2x td_pk(float lo, float hi)
+{
+    td_f2x r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void td_upk(td_f2x v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ td_f2x td_mul2(td_f2x a, td_f2x b)
+{
+    td_f2x d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ td_f2x td_fma2(td_f2x a, td_f2x b, td_f2x c)
+{
+    td_f2x d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ td_f2x td_add2(td_f2x a, td_f2x b)
+{
+    td_f2x d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ td_f2x td_sub2(td_f2x a, td_f2x b)
+{
+    td_f2x d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+/* addition rounded toward +infinity */
+__device__ __forceinline__ td_f2x td_add2_rp(td_f2x a, td_f2x b)
+{
+    td_f2x d;
+    asm("add.rp.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+/* ---- staged point layout of the filtered kernel --------------------------
+ * Points are staged in pairs: pair j holds points p = 64 (j / 32) + j % 32
+ * and q = p + 32 (the two points one lane takes in consecutive quarters of a
+ * 128-point round).  Plane c (c < ceil(D/2)) of pair j is one float4
+ * (x_2c(p), x_2c(q), x_2c+1(p), x_2c+1(q)), so one 128-bit load yields two
+ * packed operand pairs.  Planes are npc pairs apart. */
+__device__ __forceinline__ int td_pair_of(int i) { return ((i >> 6) << 5) | (i & 31); }
+
+__device__ __forceinline__ int td_xidx(int npc, int i, int r)
+{
+    return (((r >> 1) * npc + td_pair_of(i)) << 2) + ((r & 1) << 1) + ((i >> 5) & 1);
+}
+
 /* int64 -> binary32 off the FP64 pipe: exact-to-nearest when the value fits
  * 32 bits, else hi * 2^32 + lo with two roundings (relative error <= 2u,
  * covered by the error bounds below). */
@@ -649,9 +715,10 @@ __global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
 /* ====================================================================== */
 
 /* Stage the nonzero projected centred points of query q, in the order of the
- * data, into xs (float, stride PS) -- exact, the coordinates are integers
- * below 2^24.  Returns the number staged (== Q.nnz). */
-__device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int PS, int *s_tmp)
+ * data, into xs in the pair layout (td_xidx, nplanes planes npc pairs apart)
+ * -- exact, the coordinates are integers below 2^24.  Returns the number
+ * staged (== Q.nnz). */
+__device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int npc, int nplanes, int *s_tmp)
 {
     const TdQuery &Q = L.q[q];
     const TdSet S = L.sets[Q.set];
@@ -691,17 +758,17 @@ __device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int PS, int 
         bool nz = false;
         for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != zc[c];
         if (!nz) continue;
-        float *dst = xs + (size_t)o * PS;
-        for (int c = 0; c < PS; ++c) {
+        for (int c = 0; c < 2 * nplanes; ++c) {
             float v = 0.f;
             if (c < d) v = (float)((int64_t)X[(int64_t)i * p + pv[c]] - zc[pv[c]]);
-            dst[c] = v;
+            xs[td_xidx(npc, o, c)] = v;
         }
         ++o;
     }
-    /* zero rows up to the next multiple of 128 (the sweep loads them unmasked) */
+    /* zero points up to the next multiple of 128 (the sweep loads them unmasked) */
     const int nnz = Q.nnz, npad = (nnz + 127) & ~127;
-    for (int k = nnz * PS + (int)threadIdx.x; k < npad * PS; k += T) xs[k] = 0.f;
+    for (int o2 = nnz + (int)threadIdx.x; o2 < npad; o2 += T)
+        for (int c = 0; c < 2 * nplanes; ++c) xs[td_xidx(npc, o2, c)] = 0.f;
     __syncthreads();
     return Q.nnz;
 }
@@ -715,19 +782,11 @@ struct TdWarpStats {
 };
 
 template <int D>
-__device__ __forceinline__ void td_load_point(const float *xs, int PS, int i, float (&x)[D])
+__device__ __forceinline__ void td_load_point(const float *xs, int npc, int i, float (&x)[D])
 {
-    const float4 *p4 = reinterpret_cast<const float4 *>(xs + (size_t)i * PS);
-    float4 a = p4[0];
-    x[0] = a.x;
-    if (D > 1) x[1] = a.y;
-    if (D > 2) x[2] = a.z;
-    if (D > 3) x[3] = a.w;
-    if (D > 4) {
-        float4 b = p4[1];
-        x[4] = b.x;
-        if (D > 5) x[5] = b.y;
-    }
+    const float *b = xs + td_xidx(npc, i, 0);
+#pragma unroll
+    for (int r = 0; r < D; ++r) x[r] = b[(((r >> 1) * npc) << 2) + ((r & 1) << 1)];
 }
 
 /* Bucket boundary direction D_j for B buckets (pseudo-angle key 2j/B). */
@@ -838,29 +897,20 @@ __device__ __forceinline__ void td_load_pair(const void *src, uint32_t (&a)[D], 
  * The boundary search td_exact_bucket remains as a guard that never runs
  * while that error bound holds.  Returns the number of tight points. */
 template <int D, bool NARROW>
-__device__ __forceinline__ int td_exact_pass(const float *xs, const TdWarpSmem &W, int nu, int blog2, int lane)
+__device__ __forceinline__ int td_exact_pass(const float *xs, int npc, const TdWarpSmem &W, int nu, int blog2,
+                                             int lane)
 {
-    constexpr unsigned PB = D <= 4 ? 16u : 32u; /* staged point stride in bytes */
     const int B = 1 << blog2;
     const float Mb = __int_as_float(0x4B400000 - ((blog2 - 1) << 23)); /* spacing 2/B, see td_sweep_filtered */
     const int Mbits = __float_as_int(Mb);
-    const unsigned xq = td_saddr(xs), lq = td_saddr(W.glist), hq = td_saddr(W.hist), bq = td_saddr(W.bid);
+    const unsigned lq = td_saddr(W.glist), hq = td_saddr(W.hist), bq = td_saddr(W.bid);
     int t = 0;
     for (int l0 = 0; l0 < nu; l0 += 32) {
         const int l = l0 + lane;
         const bool act = l < nu;
         const unsigned i = act ? td_ldsu16(lq + 2u * (unsigned)l) : 0u;
-        const float4 a4 = td_lds128(xq + i * PB);
         float x[D];
-        x[0] = a4.x;
-        if (D > 1) x[1] = a4.y;
-        if (D > 2) x[2] = a4.z;
-        if (D > 3) x[3] = a4.w;
-        if (D > 4) {
-            const float4 b4 = td_lds128(xq + i * PB + 16u);
-            x[4] = b4.x;
-            if (D > 5) x[5] = b4.y;
-        }
+        td_load_point<D>(xs, npc, (int)i, x);
         bool plus, zero, ok;
         float f1, f2;
         int64_t h1, h2;
@@ -938,10 +988,11 @@ __device__ __forceinline__ int td_exact_pass(const float *xs, const TdWarpSmem &
 
 /* exact normalised projection of point i from the published basis */
 template <int D>
-__device__ __forceinline__ void td_exact_h(const float *xs, int PS, int i, const int64_t *qa, const int64_t *qb,
+__device__ __forceinline__ void td_exact_h(const float *xs, int npc, int i, const int64_t *qa, const int64_t *qb,
                                            int64_t &h1, int64_t &h2, bool &plus)
 {
-    const float *xp = xs + (size_t)i * PS;
+    float xp[D];
+    td_load_point<D>(xs, npc, i, xp);
     int64_t Y1 = 0, Y2 = 0;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
@@ -992,7 +1043,7 @@ __device__ __forceinline__ void td_lane_pair(int lane, int &pi, int &pj, int (&l
 }
 
 template <int D>
-__device__ __forceinline__ bool td_basis_publish(const float *xs, int PS, const int (&c)[D > 2 ? D - 2 : 1],
+__device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const int (&c)[D > 2 ? D - 2 : 1],
                                                  int lane, int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
                                                  const TdWarpSmem &W)
 {
@@ -1002,7 +1053,7 @@ __device__ __forceinline__ bool td_basis_publish(const float *xs, int PS, const 
 #pragma unroll
     for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[(size_t)c[j] * PS + lr[i]]);
+        for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[td_xidx(npc, c[j], lr[i])]);
     const int64_t M = td_detk<K>(m);
     int64_t P = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
     if (lane >= NP) P = 0;
@@ -1136,46 +1187,100 @@ __device__ __noinline__ void td_resolve_many(const float *xs, int PS, const int6
     *mx_io = max(*mx_io, lmx);
 }
 
-/* The FP32 bucket of one point (see the certification argument below):
- * floor(key B/2) when the interval key +- delta lies in one bucket, else B
- * (uncertain).  inc is the packed event of the point: 1 (+1 event,
- * orientation -) or 1 << 16 (-1 event, orientation +).  Every operation is
- * an explicitly rounded one, so the sweep loop and the rebuild of the bucket
- * ids (td_refresh_bid) take the same decisions. */
+/* Per-sweep constants of the FP32 bucket test, packed for f32x2. */
 template <int D>
-__device__ __forceinline__ int td_point_slot(const float (&x)[D], const float (&fa)[D], const float (&fb)[D],
-                                             float cE, float cU, float Mb, int Mbits, int B, uint32_t &inc)
+struct TdPairCoef {
+    td_f2x fa[D], fb[D]; /* (fa_r, fa_r), (fb_r, fb_r) */
+    td_f2x cE, cU;       /* (2E, 2E), (24u, 24u) */
+    td_f2x nMb, m1;      /* (-Mb, -Mb), (-1, -1) */
+    uint32_t moff;       /* 2^31 - bits(Mb) */
+    int B;
+};
+
+template <int D>
+__device__ __forceinline__ TdPairCoef<D> td_pair_coef(const float (&fa)[D], const float (&fb)[D], float E, int blog2)
 {
-    float y1 = __fmul_rn(fa[0], x[0]), y2 = __fmul_rn(fb[0], x[0]);
+    TdPairCoef<D> C;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        C.fa[r] = td_pk(fa[r], fa[r]);
+        C.fb[r] = td_pk(fb[r], fb[r]);
+    }
+    const float cE = 2.0f * E, cU = 24.0f * TD_U;
+    /* Mb = 1.5 * 2^23 / (B/2): binary32 spacing 2/B in its binade */
+    const float Mb = __int_as_float(0x4B400000 - ((blog2 - 1) << 23));
+    C.cE = td_pk(cE, cE);
+    C.cU = td_pk(cU, cU);
+    C.nMb = td_pk(-Mb, -Mb);
+    C.m1 = td_pk(-1.0f, -1.0f);
+    C.moff = 0x80000000u - (uint32_t)__float_as_int(Mb);
+    C.B = 1 << blog2;
+    return C;
+}
+
+/* The FP32 buckets of the two points of one staged pair (planes pl[]), see
+ * the certification argument below: floor(key B/2) when the interval
+ * key +- delta lies in one bucket, else B (uncertain).  inc is the packed
+ * event of the point: 1 (+1 event, orientation -) or 1 << 16 (-1 event,
+ * orientation +).
+ *
+ * The key is carried negated, kn = y1 rr - 1 = -key with rr = sign(y2) /
+ * (|y1| + |y2|), so that every step is one packed f32x2 operation for both
+ * points: the floors are round_up(kn -+ delta - Mb) = -round_down(key +- delta
+ * + Mb), since rounding to nearest is odd-symmetric and rounding up is
+ * rounding down mirrored.  The bucket is then bits(.) + 2^31 - bits(Mb) (the
+ * sign flip adds 2^31 to the bit pattern) and the two floors agree iff
+ * their bit patterns do.  The sweep loop and td_refresh_bid both use this
+ * function, so they take the same decisions. */
+template <int D>
+__device__ __forceinline__ void td_pair_slots(const float4 (&pl)[(D + 1) / 2], const TdPairCoef<D> &C, int &sp,
+                                              int &sq, uint32_t &ip, uint32_t &iq)
+{
+    td_f2x X[D];
+#pragma unroll
+    for (int c = 0; c < (D + 1) / 2; ++c) {
+        X[2 * c] = td_pk(pl[c].x, pl[c].y);
+        if (2 * c + 1 < D) X[2 * c + 1] = td_pk(pl[c].z, pl[c].w);
+    }
+    td_f2x Y1 = td_mul2(C.fa[0], X[0]), Y2 = td_mul2(C.fb[0], X[0]);
 #pragma unroll
     for (int r = 1; r < D; ++r) {
-        y1 = __fmaf_rn(fa[r], x[r], y1);
-        y2 = __fmaf_rn(fb[r], x[r], y2);
+        Y1 = td_fma2(C.fa[r], X[r], Y1);
+        Y2 = td_fma2(C.fb[r], X[r], Y2);
     }
-    /* the orientation rides on the sign of the divisor: with
-     * s' = sign(y2) (|y1| + |y2|), key = 1 - y1 / s' */
-    const float sg = copysignf(__fadd_rn(fabsf(y1), fabsf(y2)), y2);
-    const float rr = td_rcp(sg);
-    const float kb = __fmaf_rn(-y1, rr, 1.0f);     /* key */
-    const float db = __fmaf_rn(cE, fabsf(rr), cU); /* delta */
+    float y1p, y1q, y2p, y2q;
+    td_upk(Y1, y1p, y1q);
+    td_upk(Y2, y2p, y2q);
+    const float rap = td_rcp(__fadd_rn(fabsf(y1p), fabsf(y2p)));
+    const float raq = td_rcp(__fadd_rn(fabsf(y1q), fabsf(y2q)));
+    const td_f2x RA = td_pk(rap, raq);
+    const td_f2x RR = td_pk(copysignf(rap, y2p), copysignf(raq, y2q));
+    const td_f2x KN = td_fma2(Y1, RR, C.m1);  /* -key */
+    const td_f2x DB = td_fma2(C.cE, RA, C.cU); /* delta */
     /* When |y1|+|y2| <= 4E the interval is at least 1/2 wide, or outside the
      * conversion window, or NaN: it never yields one in-range bucket, so no
      * separate test. */
-    const int flo = __float_as_int(__fadd_rd(__fsub_rn(kb, db), Mb));
-    const int fhi = __float_as_int(__fadd_rd(__fadd_rn(kb, db), Mb));
-    const int bl = flo - Mbits;
-    inc = (uint32_t)(0x10000 + (__float_as_int(y2) >> 31) * 0xFFFF);
-    return ((flo == fhi) & ((unsigned)bl < (unsigned)B)) ? bl : B;
+    const td_f2x FL = td_add2_rp(td_add2(KN, DB), C.nMb); /* -floor((key - delta) B/2) */
+    const td_f2x FH = td_add2_rp(td_sub2(KN, DB), C.nMb); /* -floor((key + delta) B/2) */
+    float flp, flq, fhp, fhq;
+    td_upk(FL, flp, flq);
+    td_upk(FH, fhp, fhq);
+    const uint32_t blp = (uint32_t)__float_as_int(flp) + C.moff, blq = (uint32_t)__float_as_int(flq) + C.moff;
+    sp = ((__float_as_int(flp) == __float_as_int(fhp)) & (blp < (uint32_t)C.B)) ? (int)blp : C.B;
+    sq = ((__float_as_int(flq) == __float_as_int(fhq)) & (blq < (uint32_t)C.B)) ? (int)blq : C.B;
+    ip = (uint32_t)(0x10000 + (__float_as_int(y2p) >> 31) * 0xFFFF);
+    iq = (uint32_t)(0x10000 + (__float_as_int(y2q) >> 31) * 0xFFFF);
 }
 
 /* Rebuild the bucket ids of the certified points (the sweep loop does not
  * store them); the ids of the uncertain points are the exact pass's.  The
- * coefficients are the published binary32 basis, as in the sweep loop. */
+ * constants are rebuilt from the same inputs as the sweep loop's: the
+ * published binary32 basis, E and the bucket count. */
 template <int D>
-__device__ __noinline__ void td_refresh_bid(const float *xs, int nnz, const TdWarpSmem &W, float cE, float cU,
-                                            float Mb, int Mbits, int B, int lane)
+__device__ __noinline__ void td_refresh_bid(const float *xs, int npc, int nnz, const TdWarpSmem &W, float E,
+                                            int blog2, int lane)
 {
-    constexpr int PS = D <= 4 ? 4 : 8;
+    constexpr int NPL = (D + 1) / 2;
     uint32_t ua[D], ub[D];
     td_load_pair<D>(W.fab, ua, ub);
     float fa[D], fb[D];
@@ -1184,12 +1289,19 @@ __device__ __noinline__ void td_refresh_bid(const float *xs, int nnz, const TdWa
         fa[t] = __uint_as_float(ua[t]);
         fb[t] = __uint_as_float(ub[t]);
     }
-    for (int i = lane; i < nnz; i += 32) {
-        float x[D];
-        td_load_point<D>(xs, PS, i, x);
-        uint32_t inc;
-        const int s = td_point_slot<D>(x, fa, fb, cE, cU, Mb, Mbits, B, inc);
-        if (s < B) W.bid[i] = (uint16_t)s;
+    const TdPairCoef<D> C = td_pair_coef<D>(fa, fb, E, blog2);
+    const int npairs = ((nnz + 127) & ~127) >> 1;
+    const float4 *x4 = reinterpret_cast<const float4 *>(xs);
+    for (int j = lane; j < npairs; j += 32) {
+        float4 pl[NPL];
+#pragma unroll
+        for (int c = 0; c < NPL; ++c) pl[c] = x4[c * npc + j];
+        int sp, sq;
+        uint32_t ip, iq;
+        td_pair_slots<D>(pl, C, sp, sq, ip, iq);
+        const int p = ((j >> 5) << 6) | (j & 31), q = p + 32;
+        if (p < nnz && sp < C.B) W.bid[p] = (uint16_t)sp;
+        if (q < nnz && sq < C.B) W.bid[q] = (uint16_t)sq;
     }
     __syncwarp();
 }
@@ -1214,68 +1326,55 @@ __device__ __noinline__ void td_refresh_bid(const float *xs, int nnz, const TdWa
  * (for y1_f = 0 the interval is wider than B; s = 0 gives NaN or an
  * infinite key, which fails the range test). */
 template <int D>
-__device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused, int nnz,
+__device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int nnz,
                                                  const float (&fa)[D], const float (&fb)[D], float Ea, float Eb,
                                                  bool narrow, const TdWarpSmem &W, int blog2, int lane, int best,
                                                  uint64_t &n_exact, uint32_t &n_resolved, int &t_out, int &nzy_out)
 {
-    (void)PS_unused;
-    constexpr int PS = D <= 4 ? 4 : 8;      /* staged point stride (floats) */
+    constexpr int NPL = (D + 1) / 2;        /* planes of the pair layout */
     const int B = 1 << blog2;               /* blog2 >= 7: at least 4 buckets per lane */
     const int lp = blog2 - 5;               /* log2 buckets per lane */
     const int nch = 1 << (lp - 2);          /* chunks of four per lane */
     const int chm = nch - 1;
-    const float E = fmaxf(Ea, Eb);
-    const float cE = 2.0f * E;
-    const float cU = 24.0f * TD_U;
     /* Bucket floors by the magic-constant addition on the unscaled key: in
      * the binade of Mb = 1.5 * 2^23 / (B/2) the spacing of binary32 is 2/B,
      * so bits(round_down(v + Mb)) - bits(Mb) = floor(v B/2) for v in
      * (-Mb/3, 2 Mb/3).  This is the scaled-by-(B/2) computation with every
      * rounding scaled by the same power of two. */
-    const float Mb = __int_as_float(0x4B400000 - ((blog2 - 1) << 23));
-    const int Mbits = __float_as_int(Mb);
+    const TdPairCoef<D> C = td_pair_coef<D>(fa, fb, fmaxf(Ea, Eb), blog2);
     const unsigned below = (1u << lane) - 1u;
-    /* Placement of UNR points per lane per round: the common path (certified
-     * bucket: one bucket id store and one shared atomic) is predicated; the
-     * rare uncertain points are appended to W.glist under a warp-uniform
-     * branch.  All lanes run every round (indices past nnz are masked). */
-    constexpr int UNR = 4;
-    constexpr int PQ = PS / 4;                 /* float4 per staged point */
     /* uncertain points are appended to W.glist through the counter
      * W.gcount[0] (zero between sweeps) */
     const unsigned gq = td_saddr(W.glist), cq = td_saddr(W.gcount);
-    const unsigned xq = td_saddr(xs) + (unsigned)lane * (16u * PQ);   /* this lane's first point */
+    const unsigned xq = td_saddr(xs) + 16u * (unsigned)lane; /* this lane's pair in the first block */
+    const unsigned pstride = 16u * (unsigned)npc;            /* bytes between planes */
     const unsigned hq = td_saddr(W.hist);
-    /* One round places 32*UNR points, UNR per lane.  A point whose bucket is
-     * not certified (or a padding lane of the last round) adds its event to
-     * the dummy bucket B, which no scan reads, so the atomic needs no branch;
-     * uncertain points are appended to W.glist under a warp-uniform branch
-     * and placed exactly afterwards.  Bucket ids are not stored here: the
-     * rare paths that read them rebuild them (td_refresh_bid). */
+    /* One round places 128 points, two staged pairs per lane: points
+     * i0 + l, i0 + 32 + l (pair i0/2 + l) and i0 + 64 + l, i0 + 96 + l (pair
+     * i0/2 + 32 + l).  A point whose bucket is not certified (or a padding
+     * point of the last round) adds its event to the dummy bucket B, which
+     * no scan reads, so the atomic needs no branch; uncertain points are
+     * appended to W.glist under a warp-uniform branch and placed exactly
+     * afterwards.  Bucket ids are not stored here: the rare paths that read
+     * them rebuild them (td_refresh_bid). */
+    constexpr int UNR = 4;
     auto round = [&](int i0, bool tail) {
         bool okv[UNR], vv[UNR];
         int slot[UNR];
         uint32_t inc[UNR];
-        float4 a4[UNR], b4[UNR];
+        float4 pa[NPL], pb[NPL];
         /* all loads of the round first (the accesses keep program order) */
+        const unsigned ba = xq + 8u * (unsigned)i0; /* pair i0/2 + l */
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            const unsigned pa = xq + (unsigned)(i0 + 32 * u) * (16u * PQ);
-            a4[u] = td_lds128(pa);
-            if (D > 4) b4[u] = td_lds128(pa + 16u);
+        for (int c = 0; c < NPL; ++c) {
+            pa[c] = td_lds128(ba + c * pstride);
+            pb[c] = td_lds128(ba + 512u + c * pstride);
         }
+        td_pair_slots<D>(pa, C, slot[0], slot[1], inc[0], inc[1]);
+        td_pair_slots<D>(pb, C, slot[2], slot[3], inc[2], inc[3]);
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            vv[u] = !tail || i0 + 32 * u + lane < nnz; /* rows up to a multiple of 128 are staged */
-            float x[D];
-            x[0] = a4[u].x;
-            if (D > 1) x[1] = a4[u].y;
-            if (D > 2) x[2] = a4[u].z;
-            if (D > 3) x[3] = a4[u].w;
-            if (D > 4) x[4] = b4[u].x;
-            if (D > 5) x[5] = b4[u].y;
-            slot[u] = td_point_slot<D>(x, fa, fb, cE, cU, Mb, Mbits, B, inc[u]);
+            vv[u] = !tail || i0 + 32 * u + lane < nnz; /* points up to a multiple of 128 are staged */
             okv[u] = slot[u] < B;
             if (tail && !vv[u]) slot[u] = B;
         }
@@ -1329,7 +1428,8 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
     int t = 0;
     bool fresh = false; /* bucket ids rebuilt for this sweep */
     if (G < best && nu > 0) {
-        t = narrow ? td_exact_pass<D, true>(xs, W, nu, blog2, lane) : td_exact_pass<D, false>(xs, W, nu, blog2, lane);
+        t = narrow ? td_exact_pass<D, true>(xs, npc, W, nu, blog2, lane)
+                   : td_exact_pass<D, false>(xs, npc, W, nu, blog2, lane);
         __syncwarp();
         G = pass1(nnz - t);
     }
@@ -1446,7 +1546,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
                 }
             }
             __syncwarp();
-            td_refresh_bid<D>(xs, nnz, W, cE, cU, Mb, Mbits, B, lane);
+            td_refresh_bid<D>(xs, npc, nnz, W, fmaxf(Ea, Eb), blog2, lane);
             fresh = true;
             int Gn = 0;
             for (int i0 = 0; i0 < nnz; i0 += 32) {
@@ -1469,7 +1569,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
                 if (lane < Gn) {
                     const int i = W.glist[lane];
                     bool pl;
-                    td_exact_h<D>(xs, PS, i, W.qa, W.qb, h1, h2, pl);
+                    td_exact_h<D>(xs, npc, i, W.qa, W.qb, h1, h2, pl);
                     e = pl ? -1 : 1;
                     bk = W.bid[i];
                     Pb = (int)(W.hist[td_phys(bk, lp, chm)] & 0xFFFFu);
@@ -1522,13 +1622,13 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
                 mn2 = min(mn2, td_wmin(vmn));
                 mx2 = max(mx2, td_wmax(vmx));
             } else {
-                td_resolve_many<D>(xs, PS, W.qa, W.qb, W.hist, W.bid, W.glist, Gn, lp, chm, lane, &mn2, &mx2);
+                td_resolve_many<D>(xs, npc, W.qa, W.qb, W.hist, W.bid, W.glist, Gn, lp, chm, lane, &mn2, &mx2);
             }
         }
         G = min(mn2, nzy - mx2);
     }
     /* the tight-set correction reads the bucket ids */
-    if (t > D - 2 && G < best && !fresh) td_refresh_bid<D>(xs, nnz, W, cE, cU, Mb, Mbits, B, lane);
+    if (t > D - 2 && G < best && !fresh) td_refresh_bid<D>(xs, npc, nnz, W, fmaxf(Ea, Eb), blog2, lane);
     __syncwarp();
     for (int k = 0; k < nch; ++k) h4[(k + rot) & chm] = make_uint4(0u, 0u, 0u, 0u);
     if (lane == 0) W.gcount[0] = 0;
@@ -1538,7 +1638,8 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int PS_unused,
 
 /* Tight-set correction m_S after a sweep.  Tight points are those with bucket
  * id TD_SENT (filtered kernel, bid != NULL) or a zero projection H (plain
- * kernel); coordinates come from xs (float, filtered) or xi (int, plain).
+ * kernel); coordinates come from xs (float, filtered, pair layout with PS
+ * pairs per plane, see td_xidx) or xi (int, plain, stride PSI).
  * The subset's rows and point ids are in meta (published basis). */
 template <int D>
 __device__ __noinline__ int td_tight_correction(const int *meta, const float *xs, int PS, const int32_t *xi,
@@ -1554,7 +1655,7 @@ __device__ __noinline__ int td_tight_correction(const int *meta, const float *xs
             return H[2 * i] == 0 && H[2 * i + 1] == 0;
         };
         auto coord = [&](int i, int r) -> int64_t {
-            if (xs) return td_f2i(xs[(size_t)i * PS + r]);
+            if (xs) return td_f2i(xs[td_xidx(PS, i, r)]);
             return (int64_t)xi[(size_t)i * PSI + r];
         };
         int rows[K];
@@ -1599,7 +1700,7 @@ __device__ __noinline__ int td_tight_correction(const int *meta, const float *xs
  * points, tight corrections, resolved sweeps, errors) live in shared memory;
  * the subset loop keeps 32-bit tile counts and lane 0 adds them at the end. */
 template <int D>
-__device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int PS, int nnz,
+__device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int npc, int nnz,
                                  uint64_t r0, uint64_t r1, const TdWarpSmem &W, const TdScratch &scr,
                                  int blog2, int lane, int &best, unsigned long long *ws)
 {
@@ -1625,7 +1726,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     td_lane_pair<D>(lane, pi, pj, lr);
     for (uint64_t r = r0; r < r1; ++r) {
         if (r > r0) td_next_colex<K>(c);
-        if (!td_basis_publish<D>(xs, PS, c, lane, pi, pj, lr, W)) {
+        if (!td_basis_publish<D>(xs, npc, c, lane, pi, pj, lr, W)) {
             ++n_dep;
             continue;
         }
@@ -1644,12 +1745,12 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
         /* exact bounds below 2^31 (the binary32 sums are within (D + 2) u) */
         const bool narrow = fmaxf(Aa, Ab) < 2145386496.0f; /* 2^31 (1 - 2^-10) */
         int t, nzy;
-        const int G = td_sweep_filtered<D>(xs, PS, nnz, fa, fb, Ea, Eb, narrow, W, blog2, lane, best, n_exact,
+        const int G = td_sweep_filtered<D>(xs, npc, nnz, fa, fb, Ea, Eb, narrow, W, blog2, lane, best, n_exact,
                                            n_res, t, nzy);
         int V = G;
         if (t > K && G < best) {
             ++n_tight;
-            V = G + td_tight_correction<D>(W.meta, xs, PS, nullptr, 0, nnz, W.bid, nullptr, scr, W.gcount, lane);
+            V = G + td_tight_correction<D>(W.meta, xs, npc, nullptr, 0, nnz, W.bid, nullptr, scr, W.gcount, lane);
         }
         best = min(best, V);
     }
@@ -1697,13 +1798,15 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
     if (total == 0) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nmaxp = max(128, td_pow2_at_least(L.nmax));
-    const int PSA = L.pmax <= 4 ? 4 : 8;  /* staging area stride (sizing) */
-    constexpr int PS = D <= 4 ? 4 : 8;    /* this dimension's stride */
+    /* staging area: ceil(pmax/2) planes of npc pairs (sizing); this
+     * dimension uses the first ceil(D/2) */
+    const int npc = ((L.nmax + 127) & ~127) >> 1;
+    const int nplanes_max = (L.pmax + 1) >> 1;
     const int blog2_cap = L.blog2;
     /* layout: xs [nmax][PS] floats | per warp: hist [B] u32, bid [nmaxp] u16,
      * glist [nmaxp] u16, gcount, basis (qa, qb, meta) */
     float *xs = reinterpret_cast<float *>(smem);
-    const size_t off = (size_t)((L.nmax + 127) & ~127) * PSA * 4;
+    const size_t off = (size_t)nplanes_max * npc * 16;
     const int Bmax = 1 << blog2_cap;
     const size_t hbytes = (size_t)(Bmax + 4) * 4;
     const size_t per_warp = (hbytes + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
@@ -1734,7 +1837,7 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
         const int j = td_query_of_tile(prefix, L.nq, tile);
         const int q = L.order[j];
         if (q != staged) {
-            td_stage_points(L, q, xs, PS, s_tmp);  /* this dimension's stride */
+            td_stage_points(L, q, xs, npc, (D + 1) >> 1, s_tmp);
             staged = q;
         }
         const TdQuery &Q = L.q[q];
@@ -1749,7 +1852,7 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
         while ((2 << blog2) < nnz && blog2 < blog2_cap) ++blog2;
         int best = L.qmin[q];
         if (Q.d == D && blog2 <= blog2_cap && nnz <= L.nmax)
-            td_warp_filtered<D>(L, q, xs, PS, nnz, r0, r1, W, scr, blog2, lane, best, ws);
+            td_warp_filtered<D>(L, q, xs, npc, nnz, r0, r1, W, scr, blog2, lane, best, ws);
         else if (lane == 0)
             ws[6]++; /* inconsistent sizes: skip, the host reports TD_ERR_INTERNAL */
         if (lane == 0) s_best[w] = best;
@@ -1956,8 +2059,8 @@ size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
 {
     int nmaxp = td_pow2_at_least(nmax);
     nmaxp = nmaxp < 128 ? 128 : nmaxp;
-    int PS = pmax <= 4 ? 4 : 8;
-    size_t off = (size_t)((nmax + 127) & ~127) * PS * 4;
+    /* ceil(pmax/2) planes of (nmax rounded up to 128)/2 pairs, 16 bytes each */
+    size_t off = (size_t)((pmax + 1) / 2) * (size_t)(((nmax + 127) & ~127) / 2) * 16;
     size_t per_warp = ((size_t)((1 << blog2) + 4) * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     return off + per_warp * warps;
 }

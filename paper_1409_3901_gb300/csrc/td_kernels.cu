@@ -96,13 +96,6 @@ __device__ __forceinline__ void td_sts16(unsigned a, unsigned short v)
     asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
 }
 
-__device__ __forceinline__ unsigned td_atoms_add(unsigned a, unsigned v)
-{
-    unsigned old;
-    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
-    return old;
-}
-
 __device__ __forceinline__ void td_reds_add(unsigned a, unsigned v)
 {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
@@ -1230,7 +1223,7 @@ __device__ __forceinline__ TdPairCoef<D> td_pair_coef(const float (&fa)[D], cons
  * + Mb), since rounding to nearest is odd-symmetric and rounding up is
  * rounding down mirrored.  The bucket is then bits(.) + 2^31 - bits(Mb) (the
  * sign flip adds 2^31 to the bit pattern) and the two floors agree iff
- * their bit patterns do.  The sweep loop and td_refresh_bid both use this
+ * their bit patterns do.  The sweep loop and td_rescan both use this
  * function, so they take the same decisions. */
 template <int D>
 __device__ __forceinline__ void td_pair_slots(const float4 (&pl)[(D + 1) / 2], const TdPairCoef<D> &C, int &sp,
@@ -1272,13 +1265,16 @@ __device__ __forceinline__ void td_pair_slots(const float4 (&pl)[(D + 1) / 2], c
     iq = (uint32_t)(0x10000 + (__float_as_int(y2q) >> 31) * 0xFFFF);
 }
 
-/* Rebuild the bucket ids of the certified points (the sweep loop does not
- * store them); the ids of the uncertain points are the exact pass's.  The
- * constants are rebuilt from the same inputs as the sweep loop's: the
- * published binary32 basis, E and the bucket count. */
+/* Rescan of a sweep's points, for the few sweeps whose bound over the
+ * certified points does not reach best: rebuilds the bucket ids of the
+ * certified points (the sweep loop stores none) and lists the uncertain
+ * ones in W.glist (the sweep loop only counts them).  The constants are
+ * rebuilt from the sweep loop's inputs (the published binary32 basis, E and
+ * the bucket count) and td_pair_slots takes the same decisions.  Returns the
+ * number of uncertain points listed. */
 template <int D>
-__device__ __noinline__ void td_refresh_bid(const float *xs, int npc, int nnz, const TdWarpSmem &W, float E,
-                                            int blog2, int lane)
+__device__ __noinline__ int td_rescan(const float *xs, int npc, int nnz, const TdWarpSmem &W, float E, int blog2,
+                                      int lane)
 {
     constexpr int NPL = (D + 1) / 2;
     uint32_t ua[D], ub[D];
@@ -1290,9 +1286,12 @@ __device__ __noinline__ void td_refresh_bid(const float *xs, int npc, int nnz, c
         fb[t] = __uint_as_float(ub[t]);
     }
     const TdPairCoef<D> C = td_pair_coef<D>(fa, fb, E, blog2);
-    const int npairs = ((nnz + 127) & ~127) >> 1;
+    const int npairs = ((nnz + 127) & ~127) >> 1; /* a multiple of 64 */
+    const unsigned below = (1u << lane) - 1u;
     const float4 *x4 = reinterpret_cast<const float4 *>(xs);
-    for (int j = lane; j < npairs; j += 32) {
+    int cnt = 0;
+    for (int j0 = 0; j0 < npairs; j0 += 32) {
+        const int j = j0 + lane;
         float4 pl[NPL];
 #pragma unroll
         for (int c = 0; c < NPL; ++c) pl[c] = x4[c * npc + j];
@@ -1300,10 +1299,18 @@ __device__ __noinline__ void td_refresh_bid(const float *xs, int npc, int nnz, c
         uint32_t ip, iq;
         td_pair_slots<D>(pl, C, sp, sq, ip, iq);
         const int p = ((j >> 5) << 6) | (j & 31), q = p + 32;
-        if (p < nnz && sp < C.B) W.bid[p] = (uint16_t)sp;
-        if (q < nnz && sq < C.B) W.bid[q] = (uint16_t)sq;
+        const bool vp = p < nnz, vq = q < nnz;
+        if (vp && sp < C.B) W.bid[p] = (uint16_t)sp;
+        if (vq && sq < C.B) W.bid[q] = (uint16_t)sq;
+        const bool up = vp && sp == C.B, uq = vq && sq == C.B;
+        const unsigned bp = __ballot_sync(TD_FULL, up), bq = __ballot_sync(TD_FULL, uq);
+        if (up) W.glist[cnt + __popc(bp & below)] = (uint16_t)p;
+        cnt += __popc(bp);
+        if (uq) W.glist[cnt + __popc(bq & below)] = (uint16_t)q;
+        cnt += __popc(bq);
     }
     __syncwarp();
+    return cnt;
 }
 
 /* G(S) for one subset, FP32-filtered (the basis must be published to
@@ -1343,23 +1350,19 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
      * rounding scaled by the same power of two. */
     const TdPairCoef<D> C = td_pair_coef<D>(fa, fb, fmaxf(Ea, Eb), blog2);
     const unsigned below = (1u << lane) - 1u;
-    /* uncertain points are appended to W.glist through the counter
-     * W.gcount[0] (zero between sweeps) */
-    const unsigned gq = td_saddr(W.glist), cq = td_saddr(W.gcount);
     const unsigned xq = td_saddr(xs) + 16u * (unsigned)lane; /* this lane's pair in the first block */
     const unsigned pstride = 16u * (unsigned)npc;            /* bytes between planes */
     const unsigned hq = td_saddr(W.hist);
     /* One round places 128 points, two staged pairs per lane: points
      * i0 + l, i0 + 32 + l (pair i0/2 + l) and i0 + 64 + l, i0 + 96 + l (pair
-     * i0/2 + 32 + l).  A point whose bucket is not certified (or a padding
-     * point of the last round) adds its event to the dummy bucket B, which
-     * no scan reads, so the atomic needs no branch; uncertain points are
-     * appended to W.glist under a warp-uniform branch and placed exactly
-     * afterwards.  Bucket ids are not stored here: the rare paths that read
-     * them rebuild them (td_refresh_bid). */
+     * i0/2 + 32 + l).  A point whose bucket is not certified adds its event
+     * to the dummy bucket B, which the bucket scans do not read, so the
+     * atomic needs no branch, and the dummy's packed count is the number of
+     * uncertain points (a padding point of the last round adds nothing).
+     * Neither bucket ids nor the uncertain points are recorded here: the
+     * few sweeps that need them rescan (td_rescan). */
     constexpr int UNR = 4;
     auto round = [&](int i0, bool tail) {
-        bool okv[UNR], vv[UNR];
         int slot[UNR];
         uint32_t inc[UNR];
         float4 pa[NPL], pb[NPL];
@@ -1372,28 +1375,23 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
         }
         td_pair_slots<D>(pa, C, slot[0], slot[1], inc[0], inc[1]);
         td_pair_slots<D>(pb, C, slot[2], slot[3], inc[2], inc[3]);
+        if (tail) {
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            vv[u] = !tail || i0 + 32 * u + lane < nnz; /* points up to a multiple of 128 are staged */
-            okv[u] = slot[u] < B;
-            if (tail && !vv[u]) slot[u] = B;
+            for (int u = 0; u < UNR; ++u)
+                if (i0 + 32 * u + lane >= nnz) { /* points up to a multiple of 128 are staged */
+                    slot[u] = B;
+                    inc[u] = 0u;
+                }
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) td_reds_add(hq + 4u * (unsigned)slot[u], inc[u]);
-        bool badl = false;
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) badl |= vv[u] & !okv[u];
-        if (__any_sync(TD_FULL, badl)) {
-#pragma unroll
-            for (int u = 0; u < UNR; ++u)
-                if (vv[u] & !okv[u]) td_sts16(gq + 2u * td_atoms_add(cq, 1u), (unsigned short)(i0 + 32 * u + lane));
-        }
     };
     const int nfull = nnz & ~(32 * UNR - 1);
     for (int i0 = 0; i0 < nfull; i0 += 32 * UNR) round(i0, false);
     if (nfull < nnz) round(nfull, true);
     __syncwarp();
-    const int nu = *(volatile int *)W.gcount;
+    const uint32_t hB = W.hist[B];
+    const int nu = (int)(hB & 0xFFFFu) + (int)(hB >> 16); /* uncertain points */
     n_exact += (uint64_t)nu;
 
     /* Pass 1: per-lane totals of the +1/-1 events, i.e. a histogram of 32
@@ -1426,12 +1424,17 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
      * exactly (and the tight points counted). */
     int G = pass1(nnz - nu);
     int t = 0;
-    bool fresh = false; /* bucket ids rebuilt for this sweep */
-    if (G < best && nu > 0) {
-        t = narrow ? td_exact_pass<D, true>(xs, npc, W, nu, blog2, lane)
-                   : td_exact_pass<D, false>(xs, npc, W, nu, blog2, lane);
-        __syncwarp();
-        G = pass1(nnz - t);
+    if (G < best) {
+        /* bucket ids and the list of uncertain points, then their exact
+         * placement; every later step (pass 2, resolution, tight-set
+         * correction) runs only when this one has */
+        const int nl = td_rescan<D>(xs, npc, nnz, W, fmaxf(Ea, Eb), blog2, lane);
+        if (nl > 0) {
+            t = narrow ? td_exact_pass<D, true>(xs, npc, W, nl, blog2, lane)
+                       : td_exact_pass<D, false>(xs, npc, W, nl, blog2, lane);
+            __syncwarp();
+            G = pass1(nnz - t);
+        }
     }
     const int nzy = nnz - t;
     t_out = t;
@@ -1546,8 +1549,6 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
                 }
             }
             __syncwarp();
-            td_refresh_bid<D>(xs, npc, nnz, W, fmaxf(Ea, Eb), blog2, lane);
-            fresh = true;
             int Gn = 0;
             for (int i0 = 0; i0 < nnz; i0 += 32) {
                 const int i = i0 + lane;
@@ -1627,11 +1628,9 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
         }
         G = min(mn2, nzy - mx2);
     }
-    /* the tight-set correction reads the bucket ids */
-    if (t > D - 2 && G < best && !fresh) td_refresh_bid<D>(xs, npc, nnz, W, fmaxf(Ea, Eb), blog2, lane);
     __syncwarp();
     for (int k = 0; k < nch; ++k) h4[(k + rot) & chm] = make_uint4(0u, 0u, 0u, 0u);
-    if (lane == 0) W.gcount[0] = 0;
+    if (lane == 0) W.hist[B] = 0u; /* the dummy bucket's count */
     __syncwarp();
     return G;
 }
@@ -1816,7 +1815,6 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
     W.bid = reinterpret_cast<uint16_t *>(wb + hbytes);
     W.glist = W.bid + nmaxp;
     W.gcount = reinterpret_cast<int *>(W.glist + nmaxp);
-    if (lane == 0) W.gcount[0] = 0;
     W.qa = reinterpret_cast<int64_t *>(wb + hbytes + (size_t)nmaxp * 4 + 16);
     W.qb = W.qa + TD_MAXD;
     W.meta = reinterpret_cast<int *>(W.qb + TD_MAXD);

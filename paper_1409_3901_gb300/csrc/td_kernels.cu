@@ -854,6 +854,13 @@ struct TdWarpSmem {
     int32_t *q32;     /* basis truncated to int32 (exact when narrow): qa at [0, D), qb at [8, 8 + D) */
 };
 
+/* Lane-private coarse histogram of the sweep loop: row c (c < 32 the lane
+ * ranges of buckets, 32 the uncertain points) column l at word 32 c + l, so
+ * the 32 lanes of one shared reduction always hit 32 different banks.  It
+ * shares its storage with the fine histogram, bucket ids and lists, which
+ * only the few sweeps that go past the coarse bound build. */
+#define TD_COARSE_WORDS (33 * 32)
+
 /* qa, qb (2 x 6 int64), meta (8 int), fab (16 float), q32 (16 int) */
 #define TD_WARP_META_BYTES (2 * TD_MAXD * 8 + 8 * 4 + 16 * 4 + 16 * 4)
 
@@ -1266,9 +1273,10 @@ __device__ __forceinline__ void td_pair_slots(const float4 (&pl)[(D + 1) / 2], c
 }
 
 /* Rescan of a sweep's points, for the few sweeps whose bound over the
- * certified points does not reach best: rebuilds the bucket ids of the
- * certified points (the sweep loop stores none) and lists the uncertain
- * ones in W.glist (the sweep loop only counts them).  The constants are
+ * certified points does not reach best: builds the fine histogram of the
+ * certified points' events (W.hist, zero on entry) and their bucket ids
+ * (the sweep loop keeps only the coarse histogram) and lists the uncertain
+ * points in W.glist (the sweep loop only counts them).  The constants are
  * rebuilt from the sweep loop's inputs (the published binary32 basis, E and
  * the bucket count) and td_pair_slots takes the same decisions.  Returns the
  * number of uncertain points listed. */
@@ -1289,6 +1297,7 @@ __device__ __noinline__ int td_rescan(const float *xs, int npc, int nnz, const T
     const int npairs = ((nnz + 127) & ~127) >> 1; /* a multiple of 64 */
     const unsigned below = (1u << lane) - 1u;
     const float4 *x4 = reinterpret_cast<const float4 *>(xs);
+    const unsigned hq = td_saddr(W.hist);
     int cnt = 0;
     for (int j0 = 0; j0 < npairs; j0 += 32) {
         const int j = j0 + lane;
@@ -1300,8 +1309,14 @@ __device__ __noinline__ int td_rescan(const float *xs, int npc, int nnz, const T
         td_pair_slots<D>(pl, C, sp, sq, ip, iq);
         const int p = ((j >> 5) << 6) | (j & 31), q = p + 32;
         const bool vp = p < nnz, vq = q < nnz;
-        if (vp && sp < C.B) W.bid[p] = (uint16_t)sp;
-        if (vq && sq < C.B) W.bid[q] = (uint16_t)sq;
+        if (vp && sp < C.B) {
+            W.bid[p] = (uint16_t)sp;
+            td_reds_add(hq + 4u * (unsigned)sp, ip);
+        }
+        if (vq && sq < C.B) {
+            W.bid[q] = (uint16_t)sq;
+            td_reds_add(hq + 4u * (unsigned)sq, iq);
+        }
         const bool up = vp && sp == C.B, uq = vq && sq == C.B;
         const unsigned bp = __ballot_sync(TD_FULL, up), bq = __ballot_sync(TD_FULL, uq);
         if (up) W.glist[cnt + __popc(bp & below)] = (uint16_t)p;
@@ -1352,16 +1367,24 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     const unsigned below = (1u << lane) - 1u;
     const unsigned xq = td_saddr(xs) + 16u * (unsigned)lane; /* this lane's pair in the first block */
     const unsigned pstride = 16u * (unsigned)npc;            /* bytes between planes */
-    const unsigned hq = td_saddr(W.hist);
+    const unsigned cq = td_saddr(W.hist) + 4u * (unsigned)lane; /* this lane's coarse column */
     /* One round places 128 points, two staged pairs per lane: points
      * i0 + l, i0 + 32 + l (pair i0/2 + l) and i0 + 64 + l, i0 + 96 + l (pair
-     * i0/2 + 32 + l).  A point whose bucket is not certified adds its event
-     * to the dummy bucket B, which the bucket scans do not read, so the
-     * atomic needs no branch, and the dummy's packed count is the number of
+     * i0/2 + 32 + l).  Each event goes to the lane's column of the coarse
+     * histogram, row bucket / (B/32); a point whose bucket is not certified
+     * has bucket B, i.e. row 32, whose packed count is then the number of
      * uncertain points (a padding point of the last round adds nothing).
-     * Neither bucket ids nor the uncertain points are recorded here: the
-     * few sweeps that need them rescan (td_rescan). */
+     * Neither the fine histogram, bucket ids nor the uncertain points are
+     * recorded here: the few sweeps that need them rescan (td_rescan). */
     constexpr int UNR = 4;
+    /* the coarse histogram starts at zero (its storage holds the previous
+     * sweep's fine histogram, bucket ids or lists when that one went past
+     * the coarse bound; those stay readable until the sweep's caller is done) */
+    {
+        uint4 *z4 = reinterpret_cast<uint4 *>(W.hist);
+        for (int j = lane; j < (TD_COARSE_WORDS >> 2); j += 32) z4[j] = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
+    }
     auto round = [&](int i0, bool tail) {
         int slot[UNR];
         uint32_t inc[UNR];
@@ -1384,29 +1407,27 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
                 }
         }
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) td_reds_add(hq + 4u * (unsigned)slot[u], inc[u]);
+        for (int u = 0; u < UNR; ++u) td_reds_add(cq + (((unsigned)slot[u] >> lp) << 7), inc[u]);
     };
     const int nfull = nnz & ~(32 * UNR - 1);
     for (int i0 = 0; i0 < nfull; i0 += 32 * UNR) round(i0, false);
     if (nfull < nnz) round(nfull, true);
     __syncwarp();
-    const uint32_t hB = W.hist[B];
-    const int nu = (int)(hB & 0xFFFFu) + (int)(hB >> 16); /* uncertain points */
+    const uint32_t hU = W.hist[32 * 32 + lane];
+    const int nu = td_wsum((int)(hU & 0xFFFFu) + (int)(hU >> 16)); /* uncertain points */
     n_exact += (uint64_t)nu;
 
     /* Pass 1: per-lane totals of the +1/-1 events, i.e. a histogram of 32
      * coarse buckets.  Inside lane l's range the walk stays within
-     * [P_l - c-_l, P_l + c+_l], which bounds G from below. */
+     * [P_l - c-_l, P_l + c+_l], which bounds G from below.  The totals come
+     * from row l of the coarse histogram (each lane reads its row's quads in
+     * a rotated order, so a quarter warp touches distinct banks) or, after
+     * the rescan, from lane l's chunks of the fine histogram. */
     uint4 *h4 = reinterpret_cast<uint4 *>(W.hist) + lane * nch;
     const int rot = lane & chm;
     const int per = B >> 5;
     int Pl, lol, hil;
-    auto pass1 = [&](int nz) -> int {
-        uint32_t acc = 0;
-        for (int k = 0; k < nch; ++k) {
-            const uint4 v = h4[(k + rot) & chm];
-            acc += v.x + v.y + v.z + v.w;
-        }
+    auto pass1 = [&](uint32_t acc, int nz) -> int {
         const int cpl = (int)(acc & 0xFFFFu), cml = (int)(acc >> 16);
         const int A = td_wsum(cml); /* orientation + points: one -1 event each */
         const int netl = cpl - cml;
@@ -1416,25 +1437,42 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
         hil = Pl + cpl;
         return min(td_wmin(lol), nz - td_wmax(hil));
     };
-    /* First without the uncertain points (not yet in the histogram): for
+    uint32_t acc = 0;
+    {
+        const uint4 *row = reinterpret_cast<const uint4 *>(W.hist) + lane * 8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint4 v = row[(k + lane) & 7];
+            acc += v.x + v.y + v.z + v.w;
+        }
+    }
+    /* First without the uncertain points (not yet in any histogram): for
      * every direction the walk value w over all nonzero points is w_c + w_u
      * with 0 <= w_u <= (uncertain nonzero points), so min(w, nzy - w) >=
      * min(w_c, n_c - w_c) over the n_c = nnz - nu certified points.  Only
-     * when that bound does not reach best are the uncertain points placed
-     * exactly (and the tight points counted). */
-    int G = pass1(nnz - nu);
+     * when that bound does not reach best are the fine histogram, the bucket
+     * ids and the exact placement of the uncertain points (and the tight
+     * count) built. */
+    int G = pass1(acc, nnz - nu);
     int t = 0;
     if (G < best) {
-        /* bucket ids and the list of uncertain points, then their exact
-         * placement; every later step (pass 2, resolution, tight-set
-         * correction) runs only when this one has */
+        /* the fine histogram shares the coarse one's storage: clear it */
+        uint4 *z4 = reinterpret_cast<uint4 *>(W.hist);
+        const int nclr4 = max(B + 4, TD_COARSE_WORDS) >> 2;
+        __syncwarp();
+        for (int j = lane; j < nclr4; j += 32) z4[j] = make_uint4(0u, 0u, 0u, 0u);
+        __syncwarp();
         const int nl = td_rescan<D>(xs, npc, nnz, W, fmaxf(Ea, Eb), blog2, lane);
-        if (nl > 0) {
+        if (nl > 0)
             t = narrow ? td_exact_pass<D, true>(xs, npc, W, nl, blog2, lane)
                        : td_exact_pass<D, false>(xs, npc, W, nl, blog2, lane);
-            __syncwarp();
-            G = pass1(nnz - t);
+        __syncwarp();
+        acc = 0;
+        for (int k = 0; k < nch; ++k) {
+            const uint4 v = h4[(k + rot) & chm];
+            acc += v.x + v.y + v.z + v.w;
         }
+        G = pass1(acc, nnz - t);
     }
     const int nzy = nnz - t;
     t_out = t;
@@ -1629,9 +1667,6 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
         G = min(mn2, nzy - mx2);
     }
     __syncwarp();
-    for (int k = 0; k < nch; ++k) h4[(k + rot) & chm] = make_uint4(0u, 0u, 0u, 0u);
-    if (lane == 0) W.hist[B] = 0u; /* the dummy bucket's count */
-    __syncwarp();
     return G;
 }
 
@@ -1802,25 +1837,27 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
     const int npc = ((L.nmax + 127) & ~127) >> 1;
     const int nplanes_max = (L.pmax + 1) >> 1;
     const int blog2_cap = L.blog2;
-    /* layout: xs [nmax][PS] floats | per warp: hist [B] u32, bid [nmaxp] u16,
-     * glist [nmaxp] u16, gcount, basis (qa, qb, meta) */
+    /* layout: xs (pair planes) | per warp: region { hist [Bmax + 4] u32,
+     * bid [nmaxp] u16, glist [nmaxp] u16 } or the coarse histogram, whichever
+     * is larger | gcount | basis (qa, qb, meta, fab, q32) */
     float *xs = reinterpret_cast<float *>(smem);
     const size_t off = (size_t)nplanes_max * npc * 16;
     const int Bmax = 1 << blog2_cap;
     const size_t hbytes = (size_t)(Bmax + 4) * 4;
-    const size_t per_warp = (hbytes + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    const size_t rbytes = max((size_t)TD_COARSE_WORDS * 4, hbytes + (size_t)nmaxp * 4);
+    const size_t per_warp = (rbytes + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     unsigned char *wb = smem + off + per_warp * w;
     TdWarpSmem W;
     W.hist = reinterpret_cast<uint32_t *>(wb);
     W.bid = reinterpret_cast<uint16_t *>(wb + hbytes);
     W.glist = W.bid + nmaxp;
-    W.gcount = reinterpret_cast<int *>(W.glist + nmaxp);
-    W.qa = reinterpret_cast<int64_t *>(wb + hbytes + (size_t)nmaxp * 4 + 16);
+    W.gcount = reinterpret_cast<int *>(wb + rbytes);
+    W.qa = reinterpret_cast<int64_t *>(wb + rbytes + 16);
     W.qb = W.qa + TD_MAXD;
     W.meta = reinterpret_cast<int *>(W.qb + TD_MAXD);
     W.fab = reinterpret_cast<float *>(W.meta + 8);
     W.q32 = reinterpret_cast<int32_t *>(W.fab + 16);
-    for (int j = lane; j < Bmax + 4; j += 32) W.hist[j] = 0u;
+    for (int j = lane; j < max(Bmax + 4, TD_COARSE_WORDS); j += 32) W.hist[j] = 0u;
     const int gw = blockIdx.x * (blockDim.x >> 5) + w;
     /* the global scratch keeps the host's sizing (td_scratch_per_warp(nmax)) */
     const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, td_pow2_at_least(L.nmax));
@@ -2059,7 +2096,10 @@ size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
     nmaxp = nmaxp < 128 ? 128 : nmaxp;
     /* ceil(pmax/2) planes of (nmax rounded up to 128)/2 pairs, 16 bytes each */
     size_t off = (size_t)((pmax + 1) / 2) * (size_t)(((nmax + 127) & ~127) / 2) * 16;
-    size_t per_warp = ((size_t)((1 << blog2) + 4) * 4 + (size_t)nmaxp * 4 + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    const size_t hbytes = (size_t)((1 << blog2) + 4) * 4;
+    size_t rbytes = hbytes + (size_t)nmaxp * 4;
+    if (rbytes < (size_t)TD_COARSE_WORDS * 4) rbytes = (size_t)TD_COARSE_WORDS * 4;
+    size_t per_warp = (rbytes + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     return off + per_warp * warps;
 }
 

@@ -179,6 +179,16 @@ __device__ __forceinline__ float td_i64_to_f32(int64_t v)
     return __fadd_rn(__int2float_rn(hi) * 4294967296.0f, __uint2float_rn(lo));
 }
 
+/* The same conversion without a branch: |v| as hi * 2^32 + lo, one rounding
+ * of hi and one of the fma (lo below 2^32 is rounded once when hi == 0), so
+ * the relative error stays within 2u; the sign is copied back. */
+__device__ __forceinline__ float td_i64_to_f32_bf(int64_t v)
+{
+    const uint64_t a = (uint64_t)(v < 0 ? -v : v);
+    const float m = __fmaf_rn(__uint2float_rn((uint32_t)(a >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)a));
+    return v < 0 ? -m : m;
+}
+
 /* ====================================================================== */
 /* per-warp global scratch for the exact tight-set path                    */
 /* ====================================================================== */
@@ -848,9 +858,10 @@ struct TdWarpSmem {
     uint16_t *bid;    /* bucket of each point (TD_SENT = tight) */
     uint16_t *glist;  /* uncertain points, then gathered items */
     int *gcount;
-    int64_t *qa, *qb; /* exact basis of the current subset */
+    int64_t *qa, *qb; /* exact basis of the current subset (qb = qa + 8) */
     int *meta;        /* rows[0..3] (intrinsic coordinates), sub[4..7] (subset point ids) */
-    float *fab;       /* basis rounded to binary32: fa at [0, D), fb at [8, 8 + D) */
+    td_f2x *fab2;     /* basis rounded to binary32, each value twice (packed f32x2):
+                         fa at [0, D), fb at [8, 8 + D) */
     int32_t *q32;     /* basis truncated to int32 (exact when narrow): qa at [0, D), qb at [8, 8 + D) */
 };
 
@@ -861,8 +872,9 @@ struct TdWarpSmem {
  * only the few sweeps that go past the coarse bound build. */
 #define TD_COARSE_WORDS (33 * 32)
 
-/* qa, qb (2 x 6 int64), meta (8 int), fab (16 float), q32 (16 int) */
-#define TD_WARP_META_BYTES (2 * TD_MAXD * 8 + 8 * 4 + 16 * 4 + 16 * 4)
+/* q64 (16 int64: qa, qb) at 0, q32 (16 int) at 128, fab2 (16 packed pairs)
+ * at 192, meta (8 int) at 320 */
+#define TD_WARP_META_BYTES 352
 
 /* the two basis columns from the warp's shared block (32-bit words: qa at
  * [0, D), qb at [8, 8 + D), 16-byte aligned) */
@@ -881,6 +893,24 @@ __device__ __forceinline__ void td_load_pair(const void *src, uint32_t (&a)[D], 
         a[4] = a2.x;
         b[4] = b2.x;
         if (D > 5) { a[5] = a2.y; b[5] = b2.y; }
+    }
+}
+
+/* the two binary32 basis columns as packed pairs (v, v) from the warp's
+ * shared block (fa at [0, D), fb at [8, 8 + D), 16-byte aligned) */
+template <int D>
+__device__ __forceinline__ void td_load_coef2(const td_f2x *src, td_f2x (&A)[D], td_f2x (&Bv)[D])
+{
+    const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(src);
+#pragma unroll
+    for (int r = 0; r < D; r += 2) {
+        const ulonglong2 u = s2[r >> 1], w = s2[4 + (r >> 1)];
+        A[r] = u.x;
+        Bv[r] = w.x;
+        if (r + 1 < D) {
+            A[r + 1] = u.y;
+            Bv[r + 1] = w.y;
+        }
     }
 }
 
@@ -1004,16 +1034,6 @@ __device__ __forceinline__ void td_exact_h(const float *xs, int npc, int i, cons
 }
 
 
-/* Cooperative subset basis, published to the warp's shared block.  Lane l <
- * C(D,2) computes the Plucker coordinate P of the l-th row pair (i, j) in
- * lexicographic order: the entries Q_ij = P, Q_ji = -P of the antisymmetric
- * integer matrix whose columns are functionals vanishing on span S.  The warp
- * picks a pair (a, b) with P_ab != 0 and |P_ab| largest up to binary32
- * rounding (one max-reduction of a 32-bit key; any nonzero P_ab gives a
- * valid basis), and the lanes whose pair holds a or b write columns a and b:
- * exact, truncated to int32, and rounded to binary32.  Lanes 16.. write the
- * intrinsic coordinates (the rows other than a and b) and the subset.
- * Returns false (uniformly) when every P vanishes (rank < K). */
 /* The row pair (pi, pj) of lane l < C(D,2) in lexicographic order, and the
  * other K rows lr[] (those of its minor); lanes past C(D,2) get pair (0, 1). */
 template <int D>
@@ -1042,6 +1062,17 @@ __device__ __forceinline__ void td_lane_pair(int lane, int &pi, int &pj, int (&l
     }
 }
 
+/* Cooperative subset basis, published to the warp's shared block.  Lane l <
+ * C(D,2) computes the Plucker coordinate P of the l-th row pair (i, j) in
+ * lexicographic order: the entries Q_ij = P, Q_ji = -P of the antisymmetric
+ * integer matrix whose columns are functionals vanishing on span S.  The warp
+ * picks a pair (a, b) with P_ab != 0 and |P_ab| largest up to binary32
+ * rounding (one max-reduction of a 32-bit key; any nonzero P_ab gives a
+ * valid basis).  Lane e < 16 then writes entry t = e % 8 of column a (e < 8)
+ * or b: exact, truncated to int32 and rounded to binary32 (twice, packed),
+ * fetching its P with one shuffle; every lane writes the same intrinsic
+ * coordinates (the rows other than a and b) and subset ids.  Returns false
+ * (uniformly) when every P vanishes (rank < K). */
 template <int D>
 __device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const int (&c)[D > 2 ? D - 2 : 1],
                                                  int lane, int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
@@ -1057,46 +1088,31 @@ __device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const
     const int64_t M = td_detk<K>(m);
     int64_t P = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
     if (lane >= NP) P = 0;
-    const uint32_t key =
-        P != 0 ? ((__float_as_uint(td_i64_to_f32(P < 0 ? -P : P)) & ~31u) | (uint32_t)(31 - lane)) : 0u;
+    const uint32_t key = P != 0 ? ((__float_as_uint(fabsf(td_i64_to_f32_bf(P))) & ~31u) | (uint32_t)(31 - lane)) : 0u;
     const uint32_t kmax = __reduce_max_sync(TD_FULL, key);
     if (kmax == 0u) return false;
     const int wl = 31 - (int)(kmax & 31u);
     const int a = __shfl_sync(TD_FULL, pi, wl), b = __shfl_sync(TD_FULL, pj, wl);
+    /* entry t of column col: Q_t,col = +-P of the pair (min, max), 0 for t == col */
+    const int e = lane & 15, t = e & 7, col = (e >> 3) ? b : a;
+    const int x = min(t, col), y = max(t, col);
+    const int src = x * (2 * D - x - 1) / 2 + (y - x - 1);
+    const int64_t Pv = __shfl_sync(TD_FULL, P, t == col ? 0 : src);
+    const int64_t v = t == col ? 0 : (t < col ? Pv : -Pv);
     __syncwarp();
-    if (lane < NP) {
-        if (pi == a || pj == a) {
-            const int t = pi == a ? pj : pi;
-            const int64_t v = t < a ? P : -P;
-            W.qa[t] = v;
-            W.q32[t] = (int32_t)v;
-            W.fab[t] = td_i64_to_f32(v);
-        }
-        if (pi == b || pj == b) {
-            const int t = pi == b ? pj : pi;
-            const int64_t v = t < b ? P : -P;
-            W.qb[t] = v;
-            W.q32[8 + t] = (int32_t)v;
-            W.fab[8 + t] = td_i64_to_f32(v);
-        }
-    }
-    if (lane == 31) {
-        W.qa[a] = 0;
-        W.qb[b] = 0;
-        W.q32[a] = 0;
-        W.q32[8 + b] = 0;
-        W.fab[a] = 0.0f;
-        W.fab[8 + b] = 0.0f;
+    if (lane < 16 && t < D) {
+        const float f = td_i64_to_f32_bf(v);
+        W.qa[e] = v;
+        W.q32[e] = (int32_t)v;
+        W.fab2[e] = td_pk(f, f);
     }
 #pragma unroll
     for (int r = 0; r < K; ++r) {
-        if (lane == 16 + r) {
-            int rr = r;
-            rr += (rr >= a);
-            rr += (rr >= b);
-            W.meta[r] = rr;
-        }
-        if (lane == 20 + r) W.meta[4 + r] = c[r];
+        int rr = r;
+        rr += (rr >= a);
+        rr += (rr >= b);
+        W.meta[r] = rr;        /* the same value from every lane */
+        W.meta[4 + r] = c[r];
     }
     __syncwarp();
     return true;
@@ -1198,13 +1214,13 @@ struct TdPairCoef {
 };
 
 template <int D>
-__device__ __forceinline__ TdPairCoef<D> td_pair_coef(const float (&fa)[D], const float (&fb)[D], float E, int blog2)
+__device__ __forceinline__ TdPairCoef<D> td_pair_coef(const td_f2x (&FA)[D], const td_f2x (&FB)[D], float E, int blog2)
 {
     TdPairCoef<D> C;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-        C.fa[r] = td_pk(fa[r], fa[r]);
-        C.fb[r] = td_pk(fb[r], fb[r]);
+        C.fa[r] = FA[r];
+        C.fb[r] = FB[r];
     }
     const float cE = 2.0f * E, cU = 24.0f * TD_U;
     /* Mb = 1.5 * 2^23 / (B/2): binary32 spacing 2/B in its binade */
@@ -1285,15 +1301,9 @@ __device__ __noinline__ int td_rescan(const float *xs, int npc, int nnz, const T
                                       int lane)
 {
     constexpr int NPL = (D + 1) / 2;
-    uint32_t ua[D], ub[D];
-    td_load_pair<D>(W.fab, ua, ub);
-    float fa[D], fb[D];
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-        fa[t] = __uint_as_float(ua[t]);
-        fb[t] = __uint_as_float(ub[t]);
-    }
-    const TdPairCoef<D> C = td_pair_coef<D>(fa, fb, E, blog2);
+    td_f2x FA[D], FB[D];
+    td_load_coef2<D>(W.fab2, FA, FB);
+    const TdPairCoef<D> C = td_pair_coef<D>(FA, FB, E, blog2);
     const int npairs = ((nnz + 127) & ~127) >> 1; /* a multiple of 64 */
     const unsigned below = (1u << lane) - 1u;
     const float4 *x4 = reinterpret_cast<const float4 *>(xs);
@@ -1349,7 +1359,7 @@ __device__ __noinline__ int td_rescan(const float *xs, int npc, int nnz, const T
  * infinite key, which fails the range test). */
 template <int D>
 __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int nnz,
-                                                 const float (&fa)[D], const float (&fb)[D], float Ea, float Eb,
+                                                 const td_f2x (&FA)[D], const td_f2x (&FB)[D], float Ea, float Eb,
                                                  bool narrow, const TdWarpSmem &W, int blog2, int lane, int best,
                                                  uint64_t &n_exact, uint32_t &n_resolved, int &t_out, int &nzy_out)
 {
@@ -1363,7 +1373,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
      * so bits(round_down(v + Mb)) - bits(Mb) = floor(v B/2) for v in
      * (-Mb/3, 2 Mb/3).  This is the scaled-by-(B/2) computation with every
      * rounding scaled by the same power of two. */
-    const TdPairCoef<D> C = td_pair_coef<D>(fa, fb, fmaxf(Ea, Eb), blog2);
+    const TdPairCoef<D> C = td_pair_coef<D>(FA, FB, fmaxf(Ea, Eb), blog2);
     const unsigned below = (1u << lane) - 1u;
     const unsigned xq = td_saddr(xs) + 16u * (unsigned)lane; /* this lane's pair in the first block */
     const unsigned pstride = 16u * (unsigned)npc;            /* bytes between planes */
@@ -1442,7 +1452,8 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
         const uint4 *row = reinterpret_cast<const uint4 *>(W.hist) + lane * 8;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const uint4 v = row[(k + lane) & 7];
+            const int j = (k + lane) & 7;
+            const uint4 v = row[j];
             acc += v.x + v.y + v.z + v.w;
         }
     }
@@ -1758,28 +1769,29 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
     int pi, pj, lr[K > 0 ? K : 1];
     td_lane_pair<D>(lane, pi, pj, lr);
-    for (uint64_t r = r0; r < r1; ++r) {
-        if (r > r0) td_next_colex<K>(c);
+    const uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
+    for (uint32_t r = 0; r < nr; ++r) {
+        if (r > 0) td_next_colex<K>(c);
         if (!td_basis_publish<D>(xs, npc, c, lane, pi, pj, lr, W)) {
             ++n_dep;
             continue;
         }
-        uint32_t ua[D], ub[D];
-        td_load_pair<D>(W.fab, ua, ub);
-        float fa[D], fb[D];
+        td_f2x FA[D], FB[D];
+        td_load_coef2<D>(W.fab2, FA, FB);
         float Aa = 0.0f, Ab = 0.0f;
 #pragma unroll
         for (int t = 0; t < D; ++t) {
-            fa[t] = __uint_as_float(ua[t]);
-            fb[t] = __uint_as_float(ub[t]);
-            Aa = fmaf(fabsf(fa[t]), mxf[t], Aa);
-            Ab = fmaf(fabsf(fb[t]), mxf[t], Ab);
+            float fa, fb, dummy;
+            td_upk(FA[t], fa, dummy);
+            td_upk(FB[t], fb, dummy);
+            Aa = fmaf(fabsf(fa), mxf[t], Aa);
+            Ab = fmaf(fabsf(fb), mxf[t], Ab);
         }
         const float Ea = Aa * cst, Eb = Ab * cst;
         /* exact bounds below 2^31 (the binary32 sums are within (D + 2) u) */
         const bool narrow = fmaxf(Aa, Ab) < 2145386496.0f; /* 2^31 (1 - 2^-10) */
         int t, nzy;
-        const int G = td_sweep_filtered<D>(xs, npc, nnz, fa, fb, Ea, Eb, narrow, W, blog2, lane, best, n_exact,
+        const int G = td_sweep_filtered<D>(xs, npc, nnz, FA, FB, Ea, Eb, narrow, W, blog2, lane, best, n_exact,
                                            n_res, t, nzy);
         int V = G;
         if (t > K && G < best) {
@@ -1819,7 +1831,7 @@ __device__ __forceinline__ int td_query_of_tile(const int64_t *prefix, int nq, i
  * the points of the current query stay staged in shared memory; every warp
  * sweeps its share of the tile's subsets; one atomicMin per tile. */
 template <int D>
-__global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch L)
+__global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_tile;
@@ -1853,10 +1865,10 @@ __global__ void __launch_bounds__(256, (D <= 4 ? 3 : 2)) td_k_filtered(TdLaunch 
     W.glist = W.bid + nmaxp;
     W.gcount = reinterpret_cast<int *>(wb + rbytes);
     W.qa = reinterpret_cast<int64_t *>(wb + rbytes + 16);
-    W.qb = W.qa + TD_MAXD;
-    W.meta = reinterpret_cast<int *>(W.qb + TD_MAXD);
-    W.fab = reinterpret_cast<float *>(W.meta + 8);
-    W.q32 = reinterpret_cast<int32_t *>(W.fab + 16);
+    W.qb = W.qa + 8;
+    W.q32 = reinterpret_cast<int32_t *>(wb + rbytes + 16 + 128);
+    W.fab2 = reinterpret_cast<td_f2x *>(wb + rbytes + 16 + 192);
+    W.meta = reinterpret_cast<int *>(wb + rbytes + 16 + 320);
     for (int j = lane; j < max(Bmax + 4, TD_COARSE_WORDS); j += 32) W.hist[j] = 0u;
     const int gw = blockIdx.x * (blockDim.x >> 5) + w;
     /* the global scratch keeps the host's sizing (td_scratch_per_warp(nmax)) */

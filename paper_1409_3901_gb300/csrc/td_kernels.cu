@@ -56,6 +56,9 @@
 #include "td_exact.cuh"
 
 #define TD_WARPS_MAX 8
+/* points per round of the sweep loop (four per lane, two staged pairs);
+ * the staged points are padded to a multiple of it */
+#define TD_ROUND 128
 #define TD_SENT 0xFFFFu
 
 /* unit roundoff of binary32 */
@@ -769,7 +772,7 @@ __device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int npc, int
         ++o;
     }
     /* zero points up to the next multiple of 128 (the sweep loads them unmasked) */
-    const int nnz = Q.nnz, npad = (nnz + 127) & ~127;
+    const int nnz = Q.nnz, npad = (nnz + TD_ROUND - 1) & ~(TD_ROUND - 1);
     for (int o2 = nnz + (int)threadIdx.x; o2 < npad; o2 += T)
         for (int c = 0; c < 2 * nplanes; ++c) xs[td_xidx(npc, o2, c)] = 0.f;
     __syncthreads();
@@ -1211,6 +1214,8 @@ struct TdPairCoef {
     td_f2x nMb, m1;      /* (-Mb, -Mb), (-1, -1) */
     uint32_t moff;       /* 2^31 - bits(Mb) */
     int B;
+    td_f2x nMc;          /* (-Mc, -Mc), Mc = 1.5 * 2^19: binary32 spacing 1/16 */
+    uint32_t moffc;      /* 2^31 - bits(Mc) */
 };
 
 template <int D>
@@ -1231,6 +1236,9 @@ __device__ __forceinline__ TdPairCoef<D> td_pair_coef(const td_f2x (&FA)[D], con
     C.m1 = td_pk(-1.0f, -1.0f);
     C.moff = 0x80000000u - (uint32_t)__float_as_int(Mb);
     C.B = 1 << blog2;
+    const float Mc = 786432.0f;
+    C.nMc = td_pk(-Mc, -Mc);
+    C.moffc = 0x80000000u - (uint32_t)__float_as_int(Mc);
     return C;
 }
 
@@ -1288,6 +1296,50 @@ __device__ __forceinline__ void td_pair_slots(const float4 (&pl)[(D + 1) / 2], c
     iq = (uint32_t)(0x10000 + (__float_as_int(y2q) >> 31) * 0xFFFF);
 }
 
+/* The coarse rows of the two points of one staged pair: floor(key * 16), the
+ * lane range of buckets the point's event falls in (row j holds buckets
+ * [j B/32, (j + 1) B/32)), when the interval key +- delta lies in one row,
+ * else 32 (uncertain at this level).  The same computation as
+ * td_pair_slots with the magic constant of spacing 1/16, so the same
+ * certification argument holds with 32 buckets. */
+template <int D>
+__device__ __forceinline__ void td_pair_rows(const float4 (&pl)[(D + 1) / 2], const TdPairCoef<D> &C, int &rp,
+                                             int &rq, uint32_t &ip, uint32_t &iq)
+{
+    td_f2x X[D];
+#pragma unroll
+    for (int c = 0; c < (D + 1) / 2; ++c) {
+        X[2 * c] = td_pk(pl[c].x, pl[c].y);
+        if (2 * c + 1 < D) X[2 * c + 1] = td_pk(pl[c].z, pl[c].w);
+    }
+    td_f2x Y1 = td_mul2(C.fa[0], X[0]), Y2 = td_mul2(C.fb[0], X[0]);
+#pragma unroll
+    for (int r = 1; r < D; ++r) {
+        Y1 = td_fma2(C.fa[r], X[r], Y1);
+        Y2 = td_fma2(C.fb[r], X[r], Y2);
+    }
+    float y1p, y1q, y2p, y2q;
+    td_upk(Y1, y1p, y1q);
+    td_upk(Y2, y2p, y2q);
+    const float rap = td_rcp(__fadd_rn(fabsf(y1p), fabsf(y2p)));
+    const float raq = td_rcp(__fadd_rn(fabsf(y1q), fabsf(y2q)));
+    const td_f2x RA = td_pk(rap, raq);
+    const td_f2x RR = td_pk(copysignf(rap, y2p), copysignf(raq, y2q));
+    const td_f2x KN = td_fma2(Y1, RR, C.m1);  /* -key */
+    const td_f2x DB = td_fma2(C.cE, RA, C.cU); /* delta */
+    const td_f2x FL = td_add2_rp(td_add2(KN, DB), C.nMc); /* -floor((key - delta) 16) */
+    const td_f2x FH = td_add2_rp(td_sub2(KN, DB), C.nMc); /* -floor((key + delta) 16) */
+    float flp, flq, fhp, fhq;
+    td_upk(FL, flp, flq);
+    td_upk(FH, fhp, fhq);
+    const uint32_t blp = min((uint32_t)__float_as_int(flp) + C.moffc, 32u);
+    const uint32_t blq = min((uint32_t)__float_as_int(flq) + C.moffc, 32u);
+    rp = __float_as_int(flp) == __float_as_int(fhp) ? (int)blp : 32;
+    rq = __float_as_int(flq) == __float_as_int(fhq) ? (int)blq : 32;
+    ip = (uint32_t)(0x10000 + (__float_as_int(y2p) >> 31) * 0xFFFF);
+    iq = (uint32_t)(0x10000 + (__float_as_int(y2q) >> 31) * 0xFFFF);
+}
+
 /* Rescan of a sweep's points, for the few sweeps whose bound over the
  * certified points does not reach best: builds the fine histogram of the
  * certified points' events (W.hist, zero on entry) and their bucket ids
@@ -1304,7 +1356,7 @@ __device__ __noinline__ int td_rescan(const float *xs, int npc, int nnz, const T
     td_f2x FA[D], FB[D];
     td_load_coef2<D>(W.fab2, FA, FB);
     const TdPairCoef<D> C = td_pair_coef<D>(FA, FB, E, blog2);
-    const int npairs = ((nnz + 127) & ~127) >> 1; /* a multiple of 64 */
+    const int npairs = ((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) >> 1; /* a multiple of 32 */
     const unsigned below = (1u << lane) - 1u;
     const float4 *x4 = reinterpret_cast<const float4 *>(xs);
     const unsigned hq = td_saddr(W.hist);
@@ -1378,15 +1430,17 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     const unsigned xq = td_saddr(xs) + 16u * (unsigned)lane; /* this lane's pair in the first block */
     const unsigned pstride = 16u * (unsigned)npc;            /* bytes between planes */
     const unsigned cq = td_saddr(W.hist) + 4u * (unsigned)lane; /* this lane's coarse column */
-    /* One round places 128 points, two staged pairs per lane: points
-     * i0 + l, i0 + 32 + l (pair i0/2 + l) and i0 + 64 + l, i0 + 96 + l (pair
-     * i0/2 + 32 + l).  Each event goes to the lane's column of the coarse
-     * histogram, row bucket / (B/32); a point whose bucket is not certified
-     * has bucket B, i.e. row 32, whose packed count is then the number of
-     * uncertain points (a padding point of the last round adds nothing).
-     * Neither the fine histogram, bucket ids nor the uncertain points are
-     * recorded here: the few sweeps that need them rescan (td_rescan). */
-    constexpr int UNR = 4;
+    /* One round places TD_ROUND points, UNR/2 staged pairs per lane: pair
+     * i0/2 + 32 h + l holds points i0 + 64 h + l and i0 + 64 h + 32 + l.
+     * Each event goes to the lane's column of the coarse histogram, row
+     * floor(key * 16) = bucket / (B/32), certified at that level; a point
+     * whose row is not certified goes to row 32, whose packed count is then
+     * the number of uncertain points (a padding point of the last round adds
+     * nothing).  Neither the fine buckets nor the uncertain points are
+     * recorded here: the few sweeps that need them rescan (td_rescan), with
+     * the fine test. */
+    constexpr int UNR = TD_ROUND / 32;
+    constexpr int NPR = UNR / 2; /* pairs per lane and round */
     /* the coarse histogram starts at zero (its storage holds the previous
      * sweep's fine histogram, bucket ids or lists when that one went past
      * the coarse bound; those stay readable until the sweep's caller is done) */
@@ -1398,26 +1452,25 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     auto round = [&](int i0, bool tail) {
         int slot[UNR];
         uint32_t inc[UNR];
-        float4 pa[NPL], pb[NPL];
+        float4 pl[NPR][NPL];
         /* all loads of the round first (the accesses keep program order) */
         const unsigned ba = xq + 8u * (unsigned)i0; /* pair i0/2 + l */
 #pragma unroll
-        for (int c = 0; c < NPL; ++c) {
-            pa[c] = td_lds128(ba + c * pstride);
-            pb[c] = td_lds128(ba + 512u + c * pstride);
-        }
-        td_pair_slots<D>(pa, C, slot[0], slot[1], inc[0], inc[1]);
-        td_pair_slots<D>(pb, C, slot[2], slot[3], inc[2], inc[3]);
+        for (int h = 0; h < NPR; ++h)
+#pragma unroll
+            for (int c = 0; c < NPL; ++c) pl[h][c] = td_lds128(ba + 512u * h + c * pstride);
+#pragma unroll
+        for (int h = 0; h < NPR; ++h) td_pair_rows<D>(pl[h], C, slot[2 * h], slot[2 * h + 1], inc[2 * h], inc[2 * h + 1]);
         if (tail) {
 #pragma unroll
             for (int u = 0; u < UNR; ++u)
-                if (i0 + 32 * u + lane >= nnz) { /* points up to a multiple of 128 are staged */
-                    slot[u] = B;
+                if (i0 + 32 * u + lane >= nnz) { /* points up to a multiple of TD_ROUND are staged */
+                    slot[u] = 32;
                     inc[u] = 0u;
                 }
         }
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) td_reds_add(cq + (((unsigned)slot[u] >> lp) << 7), inc[u]);
+        for (int u = 0; u < UNR; ++u) td_reds_add(cq + ((unsigned)slot[u] << 7), inc[u]);
     };
     const int nfull = nnz & ~(32 * UNR - 1);
     for (int i0 = 0; i0 < nfull; i0 += 32 * UNR) round(i0, false);
@@ -1846,7 +1899,7 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     const int nmaxp = max(128, td_pow2_at_least(L.nmax));
     /* staging area: ceil(pmax/2) planes of npc pairs (sizing); this
      * dimension uses the first ceil(D/2) */
-    const int npc = ((L.nmax + 127) & ~127) >> 1;
+    const int npc = ((L.nmax + TD_ROUND - 1) & ~(TD_ROUND - 1)) >> 1;
     const int nplanes_max = (L.pmax + 1) >> 1;
     const int blog2_cap = L.blog2;
     /* layout: xs (pair planes) | per warp: region { hist [Bmax + 4] u32,
@@ -2107,7 +2160,7 @@ size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
     int nmaxp = td_pow2_at_least(nmax);
     nmaxp = nmaxp < 128 ? 128 : nmaxp;
     /* ceil(pmax/2) planes of (nmax rounded up to 128)/2 pairs, 16 bytes each */
-    size_t off = (size_t)((pmax + 1) / 2) * (size_t)(((nmax + 127) & ~127) / 2) * 16;
+    size_t off = (size_t)((pmax + 1) / 2) * (size_t)(((nmax + TD_ROUND - 1) & ~(TD_ROUND - 1)) / 2) * 16;
     const size_t hbytes = (size_t)((1 << blog2) + 4) * 4;
     size_t rbytes = hbytes + (size_t)nmaxp * 4;
     if (rbytes < (size_t)TD_COARSE_WORDS * 4) rbytes = (size_t)TD_COARSE_WORDS * 4;

@@ -296,6 +296,30 @@ def run_ours(a):
     plain_rate = psw / (pm / 1e3)
     same = bool(torch.equal(outp, out[: a.plain_queries]))
 
+    # early-exit mode (reported apart from the full-sweep metric): the running
+    # minimum starts at the data-direction bound and a query stops at V = 0
+    early = tukey.Context(local, device_pointers=True, stream=stream.cuda_stream, early_exit=True)
+    oute = torch.empty_like(out)
+    early.depth(Xd, Zd, oute)
+    em, esw, esk = 0.0, 0, 0
+    e_steps = max(3, min(a.steps, 5))
+    for _ in range(e_steps):
+        flush.fill_(1)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        early.depth(Xd, Zd, oute)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        em += f0.elapsed_time(f1)
+        esw += early.last_stats.sweeps
+        esk += early.last_stats.early_skipped
+    early_line = {"queries_per_s": d.m * e_steps / (em / 1e3), "ms_per_step": em / e_steps,
+                  "sweeps_per_step": esw // e_steps, "skipped_per_step": esk // e_steps,
+                  "same_results": bool(torch.equal(oute, out)),
+                  "note": "td_options.early_exit: data-direction upper bound (Algorithm 3 Step 2) "
+                          "seeds each query's minimum; a query stops at V = 0. Not the full-sweep metric."}
+
     if rank != 0:
         if ws > 1:
             dist.barrier()
@@ -325,6 +349,7 @@ def run_ours(a):
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "plain_exact": {"value": plain_rate, "unit": UNIT, "queries": int(Zp.shape[0]),
                             "same_results": same, "speedup_filtered_over_plain": value / ws / plain_rate},
+            "early_exit": early_line,
             "stats_per_step": {k: v for k, v in ctx.last_stats.as_dict().items()},
             "clocks": clk}
     if not a.no_cpu_baseline:

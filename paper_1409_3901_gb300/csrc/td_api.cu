@@ -86,7 +86,7 @@ struct Work {
 };
 
 struct GraphKey {
-    int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw;
+    int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw, early_exit;
     size_t smem;
     const void *ptrs[13];
     int64_t shard_index, shard_count;
@@ -353,6 +353,7 @@ TdLaunch make_launch(const Work &w, const Plan &P, const int32_t *x_arena, const
     L.pmax = P.pmax;
     L.scratch = (char *)w.scratch.p;
     L.scratch_per_warp = td_scratch_per_warp(P.nmax);
+    L.early_exit = o.early_exit != 0;
     return L;
 }
 
@@ -484,6 +485,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         memcpy(key.nmaxD, P.nmaxD, sizeof(P.nmaxD));
         key.blog2 = blog2;
         key.spw = o.subsets_per_warp;
+        key.early_exit = L.early_exit;
         key.smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
         const Work &cw = ctx->w;
         const void *pp[13] = { x_arena, cw.Zq.p, cw.sets.p, cw.q.p, cw.order.p, cw.prefix.p, cw.tsize.p,
@@ -566,6 +568,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         st->exact_points = C.exact_points;
         st->tight_exceptions = C.tight;
         st->resolved_buckets = C.resolved;
+        st->early_skipped = C.early;
         st->kernel_launches = (uint64_t)launches;
         float ms = 0.f, mss = 0.f;
         if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) != cudaSuccess) ms = -1.f;

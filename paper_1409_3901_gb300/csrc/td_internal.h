@@ -35,7 +35,7 @@ struct TdSet {
 struct TdCounters {
     unsigned long long sweeps, dependent, filtered_points, exact_points, tight, resolved;
     unsigned long long errors;  /* device-side consistency failures (must stay 0) */
-    unsigned long long pad;
+    unsigned long long early;   /* subsets not swept because their query had reached 0 (early exit) */
 };
 
 /* Parameters of the work-queue launches. */
@@ -60,4 +60,6 @@ struct TdLaunch {
     int32_t pmax;            /* largest p over the datasets */
     char *scratch;           /* per-warp global scratch for the exact tight-set path */
     int64_t scratch_per_warp;
+    int32_t early_exit;      /* nonzero: seed qmin with the data-direction bound, stop a query at 0 */
+    int32_t pad2;
 };

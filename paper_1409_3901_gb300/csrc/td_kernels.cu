@@ -653,6 +653,38 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         }
         L.qmin[q] = INT_MAX;
     }
+    if (!L.early_exit) return;
+    /* Early-exit mode: an upper bound of T from the 2n data directions
+     * u = +-x_j (Algorithm 3, Step 2): T <= #{i : u'x_i <= 0} for every u,
+     * exact in int64.  qmin starts at that bound minus Z (T = Z + min V, and
+     * a sweep reports V exactly whenever it is below qmin). */
+    __syncthreads();
+    if (Q->direct >= 0) return;
+    __shared__ int s_ub;
+    if (threadIdx.x == 0) s_ub = INT_MAX;
+    __syncthreads();
+    int ub = INT_MAX;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        int64_t xj[TD_MAXD];
+        bool nz = false;
+#pragma unroll
+        for (int c = 0; c < TD_MAXD; ++c) {
+            xj[c] = c < p ? (int64_t)X[(int64_t)j * p + c] - s_z[c] : 0;
+            nz |= xj[c] != 0;
+        }
+        if (!nz) continue;
+        int le = 0, ge = 0;
+        for (int i = 0; i < n; ++i) {
+            int64_t dot = 0;
+            for (int c = 0; c < p; ++c) dot += xj[c] * ((int64_t)X[(int64_t)i * p + c] - s_z[c]);
+            le += dot <= 0;
+            ge += dot >= 0;
+        }
+        ub = min(ub, min(le, ge));
+    }
+    atomicMin(&s_ub, ub);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ub < INT_MAX) L.qmin[q] = s_ub - s_Z;
 }
 
 /* ====================================================================== */
@@ -1822,7 +1854,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
     int pi, pj, lr[K > 0 ? K : 1];
     td_lane_pair<D>(lane, pi, pj, lr);
-    const uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
+    uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
     for (uint32_t r = 0; r < nr; ++r) {
         if (r > 0) td_next_colex<K>(c);
         if (!td_basis_publish<D>(xs, npc, c, lane, pi, pj, lr, W)) {
@@ -1852,9 +1884,15 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
             V = G + td_tight_correction<D>(W.meta, xs, npc, nullptr, 0, nnz, W.bid, nullptr, scr, W.gcount, lane);
         }
         best = min(best, V);
+        if (L.early_exit && best <= 0) {
+            /* V = 0 is the least value: the rest of the range cannot lower it */
+            if (lane == 0) ws[7] += nr - 1 - r;
+            nr = r + 1;
+            break;
+        }
     }
     if (lane == 0) {
-        const uint64_t sw = (r1 - r0) - n_dep;
+        const uint64_t sw = (uint64_t)nr - n_dep;
         ws[0] += sw;
         ws[1] += n_dep;
         ws[2] += sw * (uint64_t)nnz - n_exact;
@@ -1951,7 +1989,10 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
         int blog2 = 7;
         while ((2 << blog2) < nnz && blog2 < blog2_cap) ++blog2;
         int best = L.qmin[q];
-        if (Q.d == D && blog2 <= blog2_cap && nnz <= L.nmax)
+        if (L.early_exit && best <= 0) {
+            /* the query has reached V = 0, the least value (early exit) */
+            if (lane == 0) ws[7] += r1 - r0;
+        } else if (Q.d == D && blog2 <= blog2_cap && nnz <= L.nmax)
             td_warp_filtered<D>(L, q, xs, npc, nnz, r0, r1, W, scr, blog2, lane, best, ws);
         else if (lane == 0)
             ws[6]++; /* inconsistent sizes: skip, the host reports TD_ERR_INTERNAL */
@@ -1971,6 +2012,7 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
         atomicAdd(&L.ctr->tight, ws[4]);
         atomicAdd(&L.ctr->resolved, ws[5]);
         atomicAdd(&L.ctr->errors, ws[6]);
+        if (ws[7]) atomicAdd(&L.ctr->early, ws[7]);
     }
 }
 

@@ -45,7 +45,7 @@ class TdError(RuntimeError):
 class td_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("device_pointers", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("subsets_per_warp", ctypes.c_int32),
-                ("buckets_log2", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("buckets_log2", ctypes.c_int32), ("early_exit", ctypes.c_int32),
                 ("shard_index", ctypes.c_int64), ("shard_count", ctypes.c_int64),
                 ("stream", ctypes.c_void_p)]
 
@@ -60,7 +60,7 @@ class td_stats(ctypes.Structure):
                 ("filtered_points", ctypes.c_uint64), ("exact_points", ctypes.c_uint64),
                 ("tight_exceptions", ctypes.c_uint64), ("resolved_buckets", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("ms", ctypes.c_float),
-                ("ms_sweep", ctypes.c_float)]
+                ("ms_sweep", ctypes.c_float), ("early_skipped", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -130,13 +130,14 @@ def _check(rc, ctx=None):
 
 
 def options(mode=TD_MODE_FILTERED, device_pointers=False, use_graph=True, subsets_per_warp=0,
-            buckets_log2=0, shard_index=0, shard_count=1, stream=None):
+            buckets_log2=0, shard_index=0, shard_count=1, stream=None, early_exit=False):
     o = td_options()
     o.mode = mode
     o.device_pointers = 1 if device_pointers else 0
     o.use_graph = 1 if use_graph else 0
     o.subsets_per_warp = subsets_per_warp
     o.buckets_log2 = buckets_log2
+    o.early_exit = 1 if early_exit else 0
     o.shard_index = shard_index
     o.shard_count = shard_count
     o.stream = stream

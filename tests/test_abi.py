@@ -73,10 +73,33 @@ def test_create_reports_missing_device(tukey):
     assert not ptr.value
 
 
-def test_structs_match_header_layout(tukey):
-    assert ctypes.sizeof(tukey.td_options) == 4 * 6 + 8 * 2 + 8
-    assert ctypes.sizeof(tukey.td_dataset) == 8 + 8 + 8 + 8 + 8
-    assert ctypes.sizeof(tukey.td_stats) == 7 * 8 + 4 + 4
+def test_structs_match_header_layout(tukey, tmp_path):
+    """Every field offset and struct size of the binding against the header,
+    as the C compiler lays them out."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"td_options": tukey.td_options, "td_dataset": tukey.td_dataset, "td_stats": tukey.td_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tukey_depth.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-I", inc, str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        a, b, c = line.split()
+        got[(a, b)] = int(c)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
 
 
 def test_workload_generators_are_deterministic():

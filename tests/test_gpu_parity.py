@@ -236,3 +236,37 @@ def test_device_pointers(td):
     assert np.array_equal(got, want)
     got2 = c.depth(Xd, Zd).cpu().numpy()     # graph replay
     assert np.array_equal(got2, want)
+
+
+def test_early_exit_same_depths(td, plain):
+    """Early-exit mode (running minimum seeded with the data-direction bound
+    of Algorithm 3 Step 2, a query stopped once it reaches V = 0) returns the
+    same depths, and skips subsets of queries whose depth is Z."""
+    ee = td.Context(0, early_exit=True)
+    rng = np.random.default_rng(21)
+    for p in (3, 4, 5, 6):
+        for trial in range(3):
+            n = int(rng.integers(p + 2, {3: 60, 4: 40, 5: 26, 6: 16}[p]))
+            lim = int(rng.choice([2, 5, 40]))
+            X = random_case(rng, p, n, lim)
+            # data rows, points far outside the data (depth Z = 0) and uniform points
+            Z = np.vstack([X[:2], np.full((1, p), 3 * lim, np.int32),
+                           rng.integers(-lim, lim + 1, size=(2, p))]).astype(np.int32)
+            want = oracle.depth_many(X, Z)
+            got = ee.depth(X, Z)
+            assert np.array_equal(got, want), (p, got.tolist(), want.tolist())
+    from paper_1409_3901_gb300 import workloads as W
+    for name in ("W1", "W2"):
+        g = load_golden(name)
+        d = W.WORKLOADS[name]()
+        got = ee.depth(d.X, d.Zq)
+        assert np.array_equal(got, np.array(g["T"])), name
+        st = ee.last_stats
+        assert st.early_skipped > 0, name
+    # shards with early exit still merge to the depth
+    X = random_case(rng, 4, 40, 20)
+    Z = np.vstack([X[:3], rng.integers(-20, 21, size=(3, 4)), np.full((1, 4), 90, np.int32)]).astype(np.int32)
+    want = oracle.depth_many(X, Z)
+    parts = [td.Context(0, shard_index=s, shard_count=3, early_exit=True).depth(X, Z).astype(np.int64)
+             for s in range(3)]
+    assert np.array_equal(np.min(np.stack(parts), axis=0), want)

@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--plain-queries", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["W2", "W3", "W4", "W5"], default="W2",
+    ap.add_argument("--workload", choices=["W2", "W3", "W4", "W5", "W6"], default="W2",
                     help="W2 (default) is the benchmark line; W3 (256 datasets, one batched call), "
                          "W4 (p=5 with ties) and W5 (request stream with Poisson arrivals) print "
                          "their own lines")
@@ -366,16 +366,17 @@ def run_other(a):
     from paper_1409_3901_gb300 import tukey, workloads as W
     torch.cuda.set_device(0)
     ctx = tukey.Context(0)
-    if a.workload in ("W3", "W4"):
-        sets = W.w3() if a.workload == "W3" else [W.w4()]
+    if a.workload in ("W3", "W4", "W6"):
+        sets = W.w3() if a.workload == "W3" else [W.WORKLOADS[a.workload]()]
         batch = [(d.X, d.Zq) for d in sets]
         for _ in range(max(1, a.warmup - 2)):
             ctx.depth_batched(batch)
-        ms, sw, ex, pts = [], 0, 0, 0
+        ms, msc, sw, ex, pts = [], [], 0, 0, 0
         for _ in range(a.steps):
             ctx.depth_batched(batch)
             st = ctx.last_stats
             ms.append(st.ms_sweep)
+            msc.append(st.ms)
             sw += st.sweeps
             ex += st.exact_points
             pts += st.exact_points + st.filtered_points
@@ -385,7 +386,10 @@ def run_other(a):
                 "datasets": len(sets), "queries": nq, "queries_per_s": nq * a.steps / t,
                 "sweeps_per_call": sw // a.steps, "ms_per_call": 1e3 * t / a.steps,
                 "exact_point_fraction": ex / max(pts, 1), "steps": a.steps,
-                "note": "sweep-kernel device time (td_stats.ms_sweep), one batched call per step"}
+                "ms_per_call_all_kernels": sum(msc) / a.steps,
+                "queries_per_s_all_kernels": nq * a.steps / (sum(msc) / 1e3),
+                "note": "sweep-kernel device time (td_stats.ms_sweep), one batched call per step; "
+                        "*_all_kernels: set-up to finalize (td_stats.ms)"}
         print(json.dumps(line), flush=True)
         return
     # W5: a stream of requests with Poisson arrivals, bounded sample

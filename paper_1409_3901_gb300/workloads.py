@@ -22,6 +22,9 @@ five benchmark workloads:
   W5  a stream of requests, each p in {3,4,5,6}, n uniform in [50, 1000]
       (p = 6: n <= 120), 1-64 queries (half data rows, half uniform points of
       the bounding box), uniform integer coordinates.
+  W6  the bivariate case alone (p = 2: S is empty, one sweep per query):
+      n = 2000, round(40 * N(0,1)) clipped; 16384 queries: 8192 data rows
+      drawn with replacement and 8192 uniform points of the bounding box.
 
 Random numbers come from a counter-based SplitMix64 stream (defined by its
 published constants), uniform doubles from its top 53 bits, Gaussians by the
@@ -240,4 +243,15 @@ def small_random(seed, n, p, lim=LIM, queries=8, data_queries=None):
     return Dataset(X, np.vstack([rows, unif]).astype(np.int32), "small p=%d n=%d" % (p, n))
 
 
-WORKLOADS = {"W1": w1, "W2": w2, "W4": w4}
+def w6(seed=5, m=16384):
+    st = Stream(seed)
+    n, p = 2000, 2
+    X = _round_clip(40.0 * st.normal(n * p)).reshape(n, p)
+    half = m // 2
+    rows = X[st.integers(0, n - 1, half)]
+    unif = _bbox_uniform(st, X, m - half)
+    return Dataset(X, np.vstack([rows, unif]).astype(np.int32),
+                   "W6 p=2 n=2000 gaussian x40, %d queries" % m)
+
+
+WORKLOADS = {"W1": w1, "W2": w2, "W4": w4, "W6": w6}

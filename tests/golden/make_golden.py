@@ -6,7 +6,7 @@ input checksum so that a test on another machine first checks that it
 regenerated the same inputs.  Queries are spread over worker processes
 (``spawn`` start method); the oracle code is the same in each.
 
-    python tests/golden/make_golden.py W1 W2 W4 W3S W5S [--procs 8]
+    python tests/golden/make_golden.py W1 W2 W4 W6 W3S W5S [--procs 8]
 
 W3S and W5S are bounded samples of the batched and stream workloads: every
 query of the datasets (requests) whose full oracle cost is small.
@@ -56,7 +56,7 @@ def main():
     with ctx.Pool(a.procs) as pool:
         for name in a.names:
             t0 = time.time()
-            if name in ("W1", "W2", "W4"):
+            if name in ("W1", "W2", "W4", "W6"):
                 d = W.WORKLOADS[name]()
                 out = {"workload": name, "description": d.name, "checksum": d.checksum(),
                        "n": d.n, "p": d.p, "m": d.m, "T": _run(pool, d.X, d.Zq)}

@@ -94,7 +94,7 @@ def test_golden_w1(ctx, plain):
     assert np.array_equal(plain.depth(d.X, d.Zq), want)
 
 
-@pytest.mark.parametrize("name", ["W2", "W4"])
+@pytest.mark.parametrize("name", ["W2", "W4", "W6"])
 def test_golden_full_size(ctx, name):
     """The full benchmark workloads, every query, in the launch form bench.py times."""
     from paper_1409_3901_gb300 import workloads as W

@@ -83,12 +83,12 @@ typedef struct {
                                  from a captured CUDA graph when the shapes repeat */
     int32_t subsets_per_warp; /* work-tile size (subsets per warp per tile); 0 = autotuned */
     int32_t buckets_log2;     /* angular buckets per sweep = 2^buckets_log2; 0 = autotuned */
-    int32_t early_exit;       /* nonzero: filtered mode seeds each query's running minimum with the
-                                 upper bound of the 2n data directions u = +-x_j (Algorithm 3,
-                                 Step 2; Proposition 2) and stops sweeping a query once that
-                                 minimum reaches 0, the least value of V(S) (then T = Z).  The
-                                 depths are unchanged; stats.early_skipped counts the subsets not
-                                 swept.  0 (default): every subset is swept. */
+    int32_t early_exit;       /* nonzero: filtered mode stops sweeping a query once its running
+                                 minimum of V(S) reaches 0, the least value (then T = Z).  The
+                                 running minimum always starts at the upper bound of the 2n data
+                                 directions u = +-x_j (Algorithm 3, Step 2).  The depths are
+                                 unchanged; stats.early_skipped counts the subsets not swept.
+                                 0 (default): every subset is swept. */
     int64_t shard_index;      /* multi-GPU sharding of Algorithm 1's subset loop: process only the */
     int64_t shard_count;      /* shard_index-th of shard_count contiguous ranges of subset positions
                                  of every query (0 or 1: all).  out[q] is then the minimum over that

@@ -653,11 +653,11 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         }
         L.qmin[q] = INT_MAX;
     }
-    if (!L.early_exit) return;
-    /* Early-exit mode: an upper bound of T from the 2n data directions
-     * u = +-x_j (Algorithm 3, Step 2): T <= #{i : u'x_i <= 0} for every u,
-     * exact in int64.  qmin starts at that bound minus Z (T = Z + min V, and
-     * a sweep reports V exactly whenever it is below qmin). */
+    /* An upper bound of T from the 2n data directions u = +-x_j (Algorithm 3,
+     * Step 2): T <= #{i : u'x_i <= 0} for every u, exact in int64.  qmin
+     * starts at that bound minus Z (T = Z + min V, and a sweep reports V
+     * exactly whenever it is below qmin), so the coarse bound prunes from the
+     * first sweep of every tile on.  No subset is skipped for it. */
     __syncthreads();
     if (Q->direct >= 0) return;
     __shared__ int s_ub;

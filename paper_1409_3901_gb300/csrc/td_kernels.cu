@@ -1070,9 +1070,10 @@ __device__ __forceinline__ void td_exact_h(const float *xs, int npc, int i, cons
 
 
 /* The row pair (pi, pj) of lane l < C(D,2) in lexicographic order, and the
- * other K rows lr[] (those of its minor); lanes past C(D,2) get pair (0, 1). */
+ * other K rows of its minor, as their offsets lr[] in the staged layout (the
+ * point part of td_xidx added per point); lanes past C(D,2) get pair (0, 1). */
 template <int D>
-__device__ __forceinline__ void td_lane_pair(int lane, int &pi, int &pj, int (&lr)[D > 2 ? D - 2 : 1])
+__device__ __forceinline__ void td_lane_pair(int lane, int npc, int &pi, int &pj, int (&lr)[D > 2 ? D - 2 : 1])
 {
     constexpr int NP = D * (D - 1) / 2;
     pi = 0;
@@ -1093,7 +1094,7 @@ __device__ __forceinline__ void td_lane_pair(int lane, int &pi, int &pj, int (&l
         int r = i;
         r += (r >= pi);
         r += (r >= pj);
-        lr[i] = r;
+        lr[i] = td_xidx(npc, 0, r); /* the point part of td_xidx is zero for point 0 */
     }
 }
 
@@ -1113,13 +1114,15 @@ __device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const
                                                  int lane, int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
                                                  const TdWarpSmem &W)
 {
+    /* lr[i]: this lane's i-th row of its minor, as the offset of that
+     * coordinate within a point's slots (td_xidx less the point part) */
     constexpr int K = D - 2;
     constexpr int NP = D * (D - 1) / 2;
     int64_t m[K > 0 ? K : 1][K > 0 ? K : 1];
 #pragma unroll
     for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[td_xidx(npc, c[j], lr[i])]);
+        for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[lr[i] + ((td_pair_of(c[j]) << 2) | ((c[j] >> 5) & 1))]);
     const int64_t M = td_detk<K>(m);
     int64_t P = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
     if (lane >= NP) P = 0;
@@ -1467,8 +1470,9 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
      * Each event goes to the lane's column of the coarse histogram, row
      * floor(key * 16) = bucket / (B/32), certified at that level; a point
      * whose row is not certified goes to row 32, whose packed count is then
-     * the number of uncertain points (a padding point of the last round adds
-     * nothing).  Neither the fine buckets nor the uncertain points are
+     * the number of uncertain points plus the number of padding points of
+     * the last round (zeros, which project to 0 and so have a NaN key and
+     * fail the test).  Neither the fine buckets nor the uncertain points are
      * recorded here: the few sweeps that need them rescan (td_rescan), with
      * the fine test. */
     constexpr int UNR = TD_ROUND / 32;
@@ -1493,14 +1497,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
             for (int c = 0; c < NPL; ++c) pl[h][c] = td_lds128(ba + 512u * h + c * pstride);
 #pragma unroll
         for (int h = 0; h < NPR; ++h) td_pair_rows<D>(pl[h], C, slot[2 * h], slot[2 * h + 1], inc[2 * h], inc[2 * h + 1]);
-        if (tail) {
-#pragma unroll
-            for (int u = 0; u < UNR; ++u)
-                if (i0 + 32 * u + lane >= nnz) { /* points up to a multiple of TD_ROUND are staged */
-                    slot[u] = 32;
-                    inc[u] = 0u;
-                }
-        }
+        (void)tail;
 #pragma unroll
         for (int u = 0; u < UNR; ++u) td_reds_add(cq + ((unsigned)slot[u] << 7), inc[u]);
     };
@@ -1509,7 +1506,9 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     if (nfull < nnz) round(nfull, true);
     __syncwarp();
     const uint32_t hU = W.hist[32 * 32 + lane];
-    const int nu = td_wsum((int)(hU & 0xFFFFu) + (int)(hU >> 16)); /* uncertain points */
+    /* uncertain points: the padding points of the last round are zeros,
+     * whose key is NaN, so each of them added one event to row 32 too */
+    const int nu = td_wsum((int)(hU & 0xFFFFu) + (int)(hU >> 16)) - (((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz);
     n_exact += (uint64_t)nu;
 
     /* Pass 1: per-lane totals of the +1/-1 events, i.e. a histogram of 32
@@ -1853,7 +1852,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
      * the rounding of the products below */
     const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
     int pi, pj, lr[K > 0 ? K : 1];
-    td_lane_pair<D>(lane, pi, pj, lr);
+    td_lane_pair<D>(lane, npc, pi, pj, lr);
     uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
     for (uint32_t r = 0; r < nr; ++r) {
         if (r > 0) td_next_colex<K>(c);

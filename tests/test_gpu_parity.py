@@ -270,3 +270,37 @@ def test_early_exit_same_depths(td, plain):
     parts = [td.Context(0, shard_index=s, shard_count=3, early_exit=True).depth(X, Z).astype(np.int64)
              for s in range(3)]
     assert np.array_equal(np.min(np.stack(parts), axis=0), want)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_coordinate_limits(ctx, plain, td, p):
+    """Centred coordinates up to td_coord_limit(p): corners of the allowed
+    box, duplicates and large-magnitude ties, which push the exact int64 /
+    int128 intermediates and the FP32 error bound to their extremes."""
+    L = int(td.td_coord_limit(p))
+    h = L // 2
+    rng = np.random.default_rng(400 + p)
+    n = {1: 80, 2: 80, 3: 50, 4: 30, 5: 18, 6: 12}[p]
+    for trial in range(3):
+        X = rng.integers(-h, h + 1, size=(n, p))
+        X[: n // 4] = np.where(rng.random((n // 4, p)) < 0.5, -h, h)   # corners
+        X[-3:] = X[:3]                                                 # duplicates
+        v = rng.integers(-3, 4, size=p)
+        X[n // 4: n // 4 + 3] = np.outer([1, -2, 3], v) * (h // 9)    # collinear through 0, within h
+        Z = np.vstack([X[:2], np.zeros((1, p), np.int64),
+                       rng.integers(-h, h + 1, size=(2, p))]).astype(np.int32)
+        _check_both(ctx, plain, X.astype(np.int32), Z)
+
+
+def test_maximum_n(ctx, td):
+    """n = 2048, the largest data set one call accepts, in both dimensions
+    whose subset loops stay cheap for the oracle; n = 2049 is refused."""
+    rng = np.random.default_rng(500)
+    for p in (2, 3):
+        X = rng.integers(-127, 128, size=(2048, p)).astype(np.int32)
+        X[100:140] = X[0]                                      # ties at the maximum size
+        Z = np.vstack([X[:2], rng.integers(-127, 128, size=(1, p))]).astype(np.int32)
+        assert np.array_equal(ctx.depth(X, Z), oracle.depth_many(X, Z))
+    with pytest.raises(td.TdError) as e:
+        ctx.depth(np.zeros((2049, 3), np.int32), np.zeros((1, 3), np.int32))
+    assert e.value.code == td.TD_ERR_INVALID

@@ -247,6 +247,37 @@ __device__ __forceinline__ int64_t td_detk(const int64_t (&m)[K > 0 ? K : 1][K >
     }
 }
 
+/* The same determinant in int32, exact when K! max|m|^K < 2^31 (every
+ * intermediate, the 2 x 2 minors and the products of the expansion, is
+ * bounded by that). */
+template <int K>
+__device__ __forceinline__ int32_t td_detk32(const int32_t (&m)[K > 0 ? K : 1][K > 0 ? K : 1])
+{
+    if constexpr (K == 0) {
+        return 1;
+    } else if constexpr (K == 1) {
+        return m[0][0];
+    } else if constexpr (K == 2) {
+        return m[0][0] * m[1][1] - m[0][1] * m[1][0];
+    } else if constexpr (K == 3) {
+        const int32_t m01 = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+        const int32_t m02 = m[0][0] * m[2][1] - m[0][1] * m[2][0];
+        const int32_t m12 = m[1][0] * m[2][1] - m[1][1] * m[2][0];
+        return m[0][2] * m12 - m[1][2] * m02 + m[2][2] * m01;
+    } else {
+        int32_t a[4][4], b[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = i + 1; j < 4; ++j) {
+                a[i][j] = m[i][0] * m[j][1] - m[i][1] * m[j][0];
+                b[i][j] = m[i][2] * m[j][3] - m[i][3] * m[j][2];
+            }
+        return a[0][1] * b[2][3] - a[0][2] * b[1][3] + a[0][3] * b[1][2]
+             + a[1][2] * b[0][3] - a[1][3] * b[0][2] + a[2][3] * b[0][1];
+    }
+}
+
 /* Exact integer value of an integer-valued binary32 x with |x| <= 2^22:
  * x + 1.5*2^23 lies in [2^23, 2^24), where binary32 spacing is 1, so the sum
  * is exact and its bit pattern is 0x4B400000 + x. */

@@ -1109,24 +1109,41 @@ __device__ __forceinline__ void td_lane_pair(int lane, int npc, int &pi, int &pj
  * fetching its P with one shuffle; every lane writes the same intrinsic
  * coordinates (the rows other than a and b) and subset ids.  Returns false
  * (uniformly) when every P vanishes (rank < K). */
-template <int D>
+template <int D, bool NM>
 __device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const int (&c)[D > 2 ? D - 2 : 1],
                                                  int lane, int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
                                                  const TdWarpSmem &W)
 {
     /* lr[i]: this lane's i-th row of its minor, as the offset of that
-     * coordinate within a point's slots (td_xidx less the point part) */
+     * coordinate within a point's slots (td_xidx less the point part).
+     * NM: the minors are computed in int32 (the caller has checked
+     * K! max|x|^K < 2^31), else in int64. */
     constexpr int K = D - 2;
     constexpr int NP = D * (D - 1) / 2;
-    int64_t m[K > 0 ? K : 1][K > 0 ? K : 1];
+    int64_t P;
+    uint32_t key;
+    if constexpr (NM) {
+        int32_t m[K > 0 ? K : 1][K > 0 ? K : 1];
 #pragma unroll
-    for (int i = 0; i < K; ++i)
+        for (int i = 0; i < K; ++i)
 #pragma unroll
-        for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[lr[i] + ((td_pair_of(c[j]) << 2) | ((c[j] >> 5) & 1))]);
-    const int64_t M = td_detk<K>(m);
-    int64_t P = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
-    if (lane >= NP) P = 0;
-    const uint32_t key = P != 0 ? ((__float_as_uint(fabsf(td_i64_to_f32_bf(P))) & ~31u) | (uint32_t)(31 - lane)) : 0u;
+            for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[lr[i] + ((td_pair_of(c[j]) << 2) | ((c[j] >> 5) & 1))]);
+        const int32_t M = td_detk32<K>(m);
+        int32_t P32 = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
+        if (lane >= NP) P32 = 0;
+        key = P32 != 0 ? ((__float_as_uint(__int2float_rn(P32 < 0 ? -P32 : P32)) & ~31u) | (uint32_t)(31 - lane)) : 0u;
+        P = P32;
+    } else {
+        int64_t m[K > 0 ? K : 1][K > 0 ? K : 1];
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+#pragma unroll
+            for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[lr[i] + ((td_pair_of(c[j]) << 2) | ((c[j] >> 5) & 1))]);
+        const int64_t M = td_detk<K>(m);
+        P = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
+        if (lane >= NP) P = 0;
+        key = P != 0 ? ((__float_as_uint(fabsf(td_i64_to_f32_bf(P))) & ~31u) | (uint32_t)(31 - lane)) : 0u;
+    }
     const uint32_t kmax = __reduce_max_sync(TD_FULL, key);
     if (kmax == 0u) return false;
     const int wl = 31 - (int)(kmax & 31u);
@@ -1135,11 +1152,15 @@ __device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const
     const int e = lane & 15, t = e & 7, col = (e >> 3) ? b : a;
     const int x = min(t, col), y = max(t, col);
     const int src = x * (2 * D - x - 1) / 2 + (y - x - 1);
-    const int64_t Pv = __shfl_sync(TD_FULL, P, t == col ? 0 : src);
+    int64_t Pv;
+    if constexpr (NM)
+        Pv = __shfl_sync(TD_FULL, (int32_t)P, t == col ? 0 : src);
+    else
+        Pv = __shfl_sync(TD_FULL, P, t == col ? 0 : src);
     const int64_t v = t == col ? 0 : (t < col ? Pv : -Pv);
     __syncwarp();
     if (lane < 16 && t < D) {
-        const float f = td_i64_to_f32_bf(v);
+        const float f = NM ? __int2float_rn((int32_t)v) : td_i64_to_f32_bf(v);
         W.qa[e] = v;
         W.q32[e] = (int32_t)v;
         W.fab2[e] = td_pk(f, f);
@@ -1853,10 +1874,22 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
     int pi, pj, lr[K > 0 ? K : 1];
     td_lane_pair<D>(lane, npc, pi, pj, lr);
+    /* minors in int32 when K! max|x|^K < 2^31 (max over the coordinates) */
+    bool nm;
+    {
+        double mm = 0.0;
+#pragma unroll
+        for (int r = 0; r < D; ++r) mm = fmax(mm, (double)mxf[r]);
+        double b = 1.0;
+#pragma unroll
+        for (int i = 1; i <= K; ++i) b *= (double)i * mm;
+        nm = b < 2147483647.0;
+    }
     uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
     for (uint32_t r = 0; r < nr; ++r) {
         if (r > 0) td_next_colex<K>(c);
-        if (!td_basis_publish<D>(xs, npc, c, lane, pi, pj, lr, W)) {
+        if (!(nm ? td_basis_publish<D, true>(xs, npc, c, lane, pi, pj, lr, W)
+                 : td_basis_publish<D, false>(xs, npc, c, lane, pi, pj, lr, W))) {
             ++n_dep;
             continue;
         }

@@ -52,6 +52,8 @@
 #include <stdint.h>
 #include <limits.h>
 
+#include <type_traits>
+
 #include "td_internal.h"
 #include "td_exact.cuh"
 
@@ -1109,37 +1111,72 @@ __device__ __forceinline__ void td_lane_pair(int lane, int npc, int &pi, int &pj
  * fetching its P with one shuffle; every lane writes the same intrinsic
  * coordinates (the rows other than a and b) and subset ids.  Returns false
  * (uniformly) when every P vanishes (rank < K). */
+/* Cofactors of column 0 of a K x K matrix (column 0 unused):
+ * cof[i] = (-1)^i det(m without row i and column 0), so that
+ * det(m) = sum_i m[i][0] cof[i]. */
+template <int K, typename T>
+__device__ __forceinline__ void td_cofactors0(const T (&m)[K > 0 ? K : 1][K > 0 ? K : 1], T (&cof)[K > 0 ? K : 1])
+{
+    if constexpr (K <= 1) {
+        cof[0] = 1;
+    } else {
+        constexpr int J = K - 1;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            T s[J][J];
+#pragma unroll
+            for (int a = 0; a < J; ++a)
+#pragma unroll
+                for (int b = 0; b < J; ++b) s[a][b] = m[a + (a >= i)][b + 1];
+            T d;
+            if constexpr (std::is_same<T, int32_t>::value) d = td_detk32<J>(s);
+            else d = td_detk<J>(s);
+            cof[i] = (i & 1) ? -d : d;
+        }
+    }
+}
+
 template <int D, bool NM>
 __device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const int (&c)[D > 2 ? D - 2 : 1],
                                                  int lane, int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
-                                                 const TdWarpSmem &W)
+                                                 const TdWarpSmem &W, int64_t (&cof)[D > 2 ? D - 2 : 1],
+                                                 bool refresh)
 {
     /* lr[i]: this lane's i-th row of its minor, as the offset of that
      * coordinate within a point's slots (td_xidx less the point part).
-     * NM: the minors are computed in int32 (the caller has checked
-     * K! max|x|^K < 2^31), else in int64. */
+     * The minor is expanded along column 0 (point c[0], the one the colex
+     * successor changes most often): the cofactors cof[] of the other
+     * columns are recomputed only when refresh is set (c[1..K) changed).
+     * NM: the arithmetic is int32 (the caller has checked
+     * K! max|x|^K < 2^31, which bounds every intermediate), else int64. */
     constexpr int K = D - 2;
     constexpr int NP = D * (D - 1) / 2;
+    using T = typename std::conditional<NM, int32_t, int64_t>::type;
+    if (refresh) {
+        T m[K > 0 ? K : 1][K > 0 ? K : 1];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            m[i][0] = 0;
+#pragma unroll
+            for (int j = 1; j < K; ++j) m[i][j] = td_f2i(xs[lr[i] + ((td_pair_of(c[j]) << 2) | ((c[j] >> 5) & 1))]);
+        }
+        T cf[K > 0 ? K : 1];
+        td_cofactors0<K, T>(m, cf);
+#pragma unroll
+        for (int i = 0; i < (K > 0 ? K : 1); ++i) cof[i] = cf[i];
+    }
+    T M = (K > 0) ? 0 : 1;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+        M += (T)td_f2i(xs[lr[i] + ((td_pair_of(c[0]) << 2) | ((c[0] >> 5) & 1))]) * (T)cof[i];
     int64_t P;
     uint32_t key;
     if constexpr (NM) {
-        int32_t m[K > 0 ? K : 1][K > 0 ? K : 1];
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-#pragma unroll
-            for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[lr[i] + ((td_pair_of(c[j]) << 2) | ((c[j] >> 5) & 1))]);
-        const int32_t M = td_detk32<K>(m);
         int32_t P32 = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
         if (lane >= NP) P32 = 0;
         key = P32 != 0 ? ((__float_as_uint(__int2float_rn(P32 < 0 ? -P32 : P32)) & ~31u) | (uint32_t)(31 - lane)) : 0u;
         P = P32;
     } else {
-        int64_t m[K > 0 ? K : 1][K > 0 ? K : 1];
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-#pragma unroll
-            for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[lr[i] + ((td_pair_of(c[j]) << 2) | ((c[j] >> 5) & 1))]);
-        const int64_t M = td_detk<K>(m);
         P = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
         if (lane >= NP) P = 0;
         key = P != 0 ? ((__float_as_uint(fabsf(td_i64_to_f32_bf(P))) & ~31u) | (uint32_t)(31 - lane)) : 0u;
@@ -1874,6 +1911,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
     int pi, pj, lr[K > 0 ? K : 1];
     td_lane_pair<D>(lane, npc, pi, pj, lr);
+    int64_t cof[K > 0 ? K : 1]; /* cofactors of column 0 of this lane's minor, for c[1..K) */
     /* minors in int32 when K! max|x|^K < 2^31 (max over the coordinates) */
     bool nm;
     {
@@ -1887,9 +1925,14 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     }
     uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
     for (uint32_t r = 0; r < nr; ++r) {
-        if (r > 0) td_next_colex<K>(c);
-        if (!(nm ? td_basis_publish<D, true>(xs, npc, c, lane, pi, pj, lr, W)
-                 : td_basis_publish<D, false>(xs, npc, c, lane, pi, pj, lr, W))) {
+        bool refresh = r == 0;
+        if (r > 0) {
+            /* the successor changes c[1..K) only when c[0] cannot grow */
+            if (K >= 2) refresh = !(c[0] + 1 < c[K >= 2 ? 1 : 0]);
+            td_next_colex<K>(c);
+        }
+        if (!(nm ? td_basis_publish<D, true>(xs, npc, c, lane, pi, pj, lr, W, cof, refresh)
+                 : td_basis_publish<D, false>(xs, npc, c, lane, pi, pj, lr, W, cof, refresh))) {
             ++n_dep;
             continue;
         }

@@ -655,18 +655,24 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         }
         L.qmin[q] = INT_MAX;
     }
-    /* An upper bound of T from the 2n data directions u = +-x_j (Algorithm 3,
+    /* An upper bound of T from data directions u = +-x_j (Algorithm 3,
      * Step 2): T <= #{i : u'x_i <= 0} for every u, exact in int64.  qmin
      * starts at that bound minus Z (T = Z + min V, and a sweep reports V
      * exactly whenever it is below qmin), so the coarse bound prunes from the
-     * first sweep of every tile on.  No subset is skipped for it. */
+     * first sweep of every tile on.  No subset is skipped for it.  The bound
+     * costs n point evaluations per direction; ndir = min(n, subsets / 64)
+     * evenly spaced directions keep it near 1% of the subset loop (none for
+     * a loop of fewer than 64 subsets). */
     __syncthreads();
     if (Q->direct >= 0) return;
+    const int ndir = (int)min((int64_t)n, Q->nsub / 64);
+    if (ndir <= 0) return;
     __shared__ int s_ub;
     if (threadIdx.x == 0) s_ub = INT_MAX;
     __syncthreads();
     int ub = INT_MAX;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int kd = threadIdx.x; kd < ndir; kd += blockDim.x) {
+        const int j = (int)((int64_t)kd * n / ndir);
         int64_t xj[TD_MAXD];
         bool nz = false;
 #pragma unroll

@@ -85,7 +85,7 @@ typedef struct {
     int32_t buckets_log2;     /* angular buckets per sweep = 2^buckets_log2; 0 = autotuned */
     int32_t early_exit;       /* nonzero: filtered mode stops sweeping a query once its running
                                  minimum of V(S) reaches 0, the least value (then T = Z).  The
-                                 running minimum always starts at the upper bound of the 2n data
+                                 running minimum always starts at the upper bound of data
                                  directions u = +-x_j (Algorithm 3, Step 2).  The depths are
                                  unchanged; stats.early_skipped counts the subsets not swept.
                                  0 (default): every subset is swept. */

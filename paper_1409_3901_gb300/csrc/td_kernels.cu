@@ -205,11 +205,13 @@ struct TdScratch {
     int32_t *c1;  /* level-1 coordinates [NP][4] */
     int64_t *y1;  /* level-1 projections [NP][2] */
     uint16_t *i1; /* level-1 sort list [NP] */
+    uint16_t *bid;   /* filtered sweep: bucket id per point (rare path) [NP] */
+    uint16_t *glist; /* filtered sweep: uncertain / gathered points (rare path) [NP] */
 };
 
 __host__ __device__ inline int64_t td_scratch_bytes(int np)
 {
-    return (int64_t)np * (16 + 16 + 2 + 16 + 16 + 2) + 256;
+    return (int64_t)np * (16 + 16 + 2 + 16 + 16 + 2 + 2 + 2) + 256;
 }
 
 __device__ inline TdScratch td_scratch_at(char *base, int np)
@@ -221,7 +223,9 @@ __device__ inline TdScratch td_scratch_at(char *base, int np)
     s.c1 = (int32_t *)p; p += (size_t)np * 16;
     s.y1 = (int64_t *)p; p += (size_t)np * 16;
     s.i0 = (uint16_t *)p; p += (size_t)np * 2;
-    s.i1 = (uint16_t *)p;
+    s.i1 = (uint16_t *)p; p += (size_t)np * 2;
+    s.bid = (uint16_t *)p; p += (size_t)np * 2;
+    s.glist = (uint16_t *)p;
     return s;
 }
 
@@ -976,12 +980,12 @@ __device__ __forceinline__ int td_exact_pass(const float *xs, int npc, const TdW
     const int B = 1 << blog2;
     const float Mb = __int_as_float(0x4B400000 - ((blog2 - 1) << 23)); /* spacing 2/B, see td_sweep_filtered */
     const int Mbits = __float_as_int(Mb);
-    const unsigned lq = td_saddr(W.glist), hq = td_saddr(W.hist), bq = td_saddr(W.bid);
+    const unsigned hq = td_saddr(W.hist);
     int t = 0;
     for (int l0 = 0; l0 < nu; l0 += 32) {
         const int l = l0 + lane;
         const bool act = l < nu;
-        const unsigned i = act ? td_ldsu16(lq + 2u * (unsigned)l) : 0u;
+        const unsigned i = act ? (unsigned)W.glist[l] : 0u;
         float x[D];
         td_load_point<D>(xs, npc, (int)i, x);
         bool plus, zero, ok;
@@ -1051,7 +1055,7 @@ __device__ __forceinline__ int td_exact_pass(const float *xs, int npc, const TdW
             if (need) j = td_exact_bucket(h1, h2, max(0, min(j, B - 1)), B);
         }
         if (act) {
-            td_sts16(bq + 2u * i, (unsigned short)(zero ? TD_SENT : (unsigned)j));
+            W.bid[i] = (uint16_t)(zero ? TD_SENT : (unsigned)j);
             if (!zero) td_reds_add(hq + 4u * (unsigned)j, plus ? 0x10000u : 1u);
             t += zero;
         }
@@ -2021,20 +2025,24 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     const int npc = ((L.nmax + TD_ROUND - 1) & ~(TD_ROUND - 1)) >> 1;
     const int nplanes_max = (L.pmax + 1) >> 1;
     const int blog2_cap = L.blog2;
-    /* layout: xs (pair planes) | per warp: region { hist [Bmax + 4] u32,
-     * bid [nmaxp] u16, glist [nmaxp] u16 } or the coarse histogram, whichever
-     * is larger | gcount | basis (qa, qb, meta, fab, q32) */
+    /* layout: xs (pair planes) | per warp: region { fine hist [Bmax + 4]
+     * u32 } or the coarse histogram, whichever is larger | gcount | basis
+     * (qa, qb, meta, fab, q32).  The bucket ids and lists of the rare path
+     * are in the warp's global scratch. */
     float *xs = reinterpret_cast<float *>(smem);
     const size_t off = (size_t)nplanes_max * npc * 16;
     const int Bmax = 1 << blog2_cap;
     const size_t hbytes = (size_t)(Bmax + 4) * 4;
-    const size_t rbytes = max((size_t)TD_COARSE_WORDS * 4, hbytes + (size_t)nmaxp * 4);
+    const size_t rbytes = max((size_t)TD_COARSE_WORDS * 4, hbytes);
     const size_t per_warp = (rbytes + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     unsigned char *wb = smem + off + per_warp * w;
     TdWarpSmem W;
     W.hist = reinterpret_cast<uint32_t *>(wb);
-    W.bid = reinterpret_cast<uint16_t *>(wb + hbytes);
-    W.glist = W.bid + nmaxp;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + w;
+    /* the global scratch keeps the host's sizing (td_scratch_per_warp(nmax)) */
+    const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, td_pow2_at_least(L.nmax));
+    W.bid = scr.bid;
+    W.glist = scr.glist;
     W.gcount = reinterpret_cast<int *>(wb + rbytes);
     W.qa = reinterpret_cast<int64_t *>(wb + rbytes + 16);
     W.qb = W.qa + 8;
@@ -2042,9 +2050,6 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     W.fab2 = reinterpret_cast<td_f2x *>(wb + rbytes + 16 + 192);
     W.meta = reinterpret_cast<int *>(wb + rbytes + 16 + 320);
     for (int j = lane; j < max(Bmax + 4, TD_COARSE_WORDS); j += 32) W.hist[j] = 0u;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + w;
-    /* the global scratch keeps the host's sizing (td_scratch_per_warp(nmax)) */
-    const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, td_pow2_at_least(L.nmax));
     unsigned long long *ws = s_stats[w];
     if (lane < 8) ws[lane] = 0ull;
     int staged = -1;
@@ -2285,7 +2290,7 @@ size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
     /* ceil(pmax/2) planes of (nmax rounded up to 128)/2 pairs, 16 bytes each */
     size_t off = (size_t)((pmax + 1) / 2) * (size_t)(((nmax + TD_ROUND - 1) & ~(TD_ROUND - 1)) / 2) * 16;
     const size_t hbytes = (size_t)((1 << blog2) + 4) * 4;
-    size_t rbytes = hbytes + (size_t)nmaxp * 4;
+    size_t rbytes = hbytes;
     if (rbytes < (size_t)TD_COARSE_WORDS * 4) rbytes = (size_t)TD_COARSE_WORDS * 4;
     size_t per_warp = (rbytes + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
     return off + per_warp * warps;

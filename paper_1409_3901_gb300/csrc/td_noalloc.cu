@@ -54,7 +54,7 @@ constexpr size_t kSets = kCtr + al256(sizeof(TdCounters));
 constexpr size_t kStatus = kSets + al256(sizeof(TdSet));
 constexpr size_t kScratch = kStatus + al256(4 * sizeof(unsigned long long));
 /* per-warp scratch of the exact tight-set path, sized for TD_NOALLOC_MAX_N */
-constexpr size_t kPerWarp = al256((size_t)256 * 68 * ((TD_NOALLOC_MAX_N + 255) / 256) + 256);
+constexpr size_t kPerWarp = al256((size_t)256 * 72 * ((TD_NOALLOC_MAX_N + 255) / 256) + 256);
 constexpr size_t kBytes = kScratch + (size_t)TD_NOALLOC_CTAS * kWarps * kPerWarp;
 static_assert(kBytes <= (size_t)TD_NOALLOC_BYTES, "TD_NOALLOC_BYTES too small for the layout");
 

@@ -703,10 +703,16 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
 /* tile prefix kernel                                                      */
 /* ====================================================================== */
 
-__host__ __device__ inline int td_auto_spw(int nnz)
+/* Subsets per warp and tile: about 2^16 point evaluations per warp and tile
+ * (the per-tile set-up then costs well under 1%), at most 128, and at most
+ * 1/64 of the query's range per CTA tile so that a short subset loop still
+ * spreads over many CTAs; at least 4. */
+__host__ __device__ inline int td_auto_spw(int nnz, int64_t nrange, int warps)
 {
-    int s = 16384 / (nnz > 0 ? nnz : 1);
-    return s < 4 ? 4 : (s > 64 ? 64 : s);
+    int64_t s = 65536 / (nnz > 0 ? nnz : 1);
+    const int64_t cap = nrange / (64 * (int64_t)(warps > 0 ? warps : 1));
+    s = s < cap ? s : cap;
+    return s < 4 ? 4 : (s > 128 ? 128 : (int)s);
 }
 
 /* Tiles of every query, and for each effective dimension D = 2..6 the prefix
@@ -723,7 +729,7 @@ __global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
     for (int j = beg; j < end; ++j) {
         const int q = L.order[j];
         const TdQuery &Q = L.q[q];
-        int spw = L.spw > 0 ? L.spw : td_auto_spw(Q.nnz);
+        int spw = L.spw > 0 ? L.spw : td_auto_spw(Q.nnz, Q.hi - Q.lo, L.warps);
         int64_t ts = (int64_t)spw * L.warps;
         L.tile_size[q] = (int)ts;
         int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? (Q.hi - Q.lo + ts - 1) / ts : 0;

@@ -286,86 +286,6 @@ __device__ __forceinline__ int32_t td_f2i(float x)
     return __float_as_int(x + 12582912.0f) - 0x4B400000;
 }
 
-/* floor(v) for |v| <= 2^22 as the same bit pattern trick, with the addition
- * rounded toward minus infinity; returns the biased pattern (compare two of
- * them directly, subtract 0x4B400000 for the integer). */
-__device__ __forceinline__ int32_t td_floor_bits(float v)
-{
-    return __float_as_int(__fadd_rd(v, 12582912.0f));
-}
-
-/* Cooperative subset basis: lane l < C(D,2) computes the Plucker coordinate
- * P_ab of the l-th row pair (lexicographic), the warp picks the first pair of
- * largest |P| and every lane gathers the columns a and b of Q by shuffles.
- * xs holds the points (binary32, exact integers), stride PS; c[] the subset.
- * Returns false (uniformly) when the subset has rank < K. */
-template <int D>
-__device__ __forceinline__ bool td_make_basis_coop(const float *xs, int PS, const int (&c)[D > 2 ? D - 2 : 1],
-                                                   int lane, TdBasis<D> &B)
-{
-    constexpr int K = D - 2;
-    constexpr int NP = D * (D - 1) / 2;
-    int a = 0, b = 1;
-    {
-        int l = lane < NP ? lane : 0;
-#pragma unroll
-        for (int aa = 0; aa < D - 1; ++aa) {
-            const int cnt = D - 1 - aa;
-            if (l >= 0 && l < cnt) {
-                a = aa;
-                b = aa + 1 + l;
-            }
-            l -= cnt;
-        }
-    }
-    int64_t m[K > 0 ? K : 1][K > 0 ? K : 1];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        int r = i;
-        r += (r >= a);
-        r += (r >= b);
-#pragma unroll
-        for (int j = 0; j < K; ++j) m[i][j] = td_f2i(xs[(size_t)c[j] * PS + r]);
-    }
-    const int64_t M = td_detk<K>(m);
-    int64_t P = ((a + b) & 1) ? M : -M; /* -(-1)^(a+b) M */
-    if (lane >= NP) P = 0;
-    uint64_t key = P != 0 ? ((((uint64_t)(P < 0 ? -P : P)) << 5) | (uint64_t)(31 - lane)) : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t ok = __shfl_xor_sync(TD_FULL, key, o);
-        key = ok > key ? ok : key;
-    }
-    if (key == 0ull) return false;
-    const int w = 31 - (int)(key & 31ull);
-    const int ba = __shfl_sync(TD_FULL, a, w), bb = __shfl_sync(TD_FULL, b, w);
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-        {
-            const int x = t < ba ? t : ba, y = t < ba ? ba : t;
-            const int src = (t == ba) ? 0 : x * (2 * D - x - 1) / 2 + (y - x - 1);
-            const int64_t v = __shfl_sync(TD_FULL, P, src);
-            B.qa[t] = (t == ba) ? 0 : (t < ba ? v : -v);
-        }
-        {
-            const int x = t < bb ? t : bb, y = t < bb ? bb : t;
-            const int src = (t == bb) ? 0 : x * (2 * D - x - 1) / 2 + (y - x - 1);
-            const int64_t v = __shfl_sync(TD_FULL, P, src);
-            B.qb[t] = (t == bb) ? 0 : (t < bb ? v : -v);
-        }
-    }
-    B.a = ba;
-    B.b = bb;
-#pragma unroll
-    for (int i = 0; i < (K > 0 ? K : 1); ++i) {
-        int r = i;
-        r += (r >= ba);
-        r += (r >= bb);
-        B.rows[i] = r;
-    }
-    return true;
-}
-
 /* Half-plane normalisation of a nonzero projected point: h = y or -y with
  * h2 > 0, or h2 == 0 and h1 > 0.  Returns true when h == y ("orientation +":
  * the point is on the counted side just before its line is crossed). */

@@ -89,18 +89,6 @@ __device__ __forceinline__ float4 td_lds128(unsigned a)
     return v;
 }
 
-__device__ __forceinline__ unsigned td_ldsu16(unsigned a)
-{
-    unsigned short v;
-    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
-    return v;
-}
-
-__device__ __forceinline__ void td_sts16(unsigned a, unsigned short v)
-{
-    asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
-}
-
 __device__ __forceinline__ void td_reds_add(unsigned a, unsigned v)
 {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
@@ -875,25 +863,6 @@ __device__ __forceinline__ int td_exact_bucket(int64_t h1, int64_t h2, int b, in
     return b;
 }
 
-__device__ __forceinline__ float td_key(float h1, float h2)
-{
-    float s = fabsf(h1) + h2;
-    return 1.0f - h1 * __fdividef(1.0f, s);
-}
-
-template <int D>
-__device__ __forceinline__ void td_exact_y(const TdBasis<D> &B, const float (&x)[D], int64_t &y1, int64_t &y2)
-{
-    y1 = 0;
-    y2 = 0;
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-        const int64_t xv = td_f2i(x[r]);
-        y1 += B.qa[r] * xv;
-        y2 += B.qb[r] * xv;
-    }
-}
-
 /* Histogram layout: bucket b at word b.  Lane l owns the per = B/32 buckets
  * [l*per, (l+1)*per).  The scans that run on every sweep (per-lane totals,
  * clearing) visit a lane's chunks of four in the rotated order c = (k + l)
@@ -1085,7 +1054,6 @@ __device__ __forceinline__ void td_exact_h(const float *xs, int npc, int i, cons
     }
     plus = td_normalise(Y1, Y2, h1, h2);
 }
-
 
 /* The row pair (pi, pj) of lane l < C(D,2) in lexicographic order, and the
  * other K rows of its minor, as their offsets lr[] in the staged layout (the

@@ -817,6 +817,46 @@ __device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int npc, int
     return Q.nnz;
 }
 
+/* The same staging by one warp into its own area (the D = 2 kernel, where a
+ * query has a single subset): nonzero points compacted in data order with
+ * ballots, the pivot coordinates of the query, zeros up to a multiple of
+ * TD_ROUND.  Returns the number staged. */
+__device__ int td_stage_points_warp(const TdLaunch &L, int q, float *xs, int npc, int lane)
+{
+    const TdQuery &Q = L.q[q];
+    const TdSet S = L.sets[Q.set];
+    const int n = S.n, p = S.p;
+    const int32_t *X = L.X + S.x_off;
+    const int32_t *z = L.Zq + (int64_t)q * TD_MAXD;
+    const int p0 = Q.piv[0], p1 = Q.piv[1];
+    const unsigned below = (1u << lane) - 1u;
+    int o = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        bool nz = false;
+        float v0 = 0.f, v1 = 0.f;
+        if (i < n) {
+            for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != z[c];
+            v0 = (float)((int64_t)X[(int64_t)i * p + p0] - z[p0]);
+            v1 = (float)((int64_t)X[(int64_t)i * p + p1] - z[p1]);
+        }
+        const unsigned b = __ballot_sync(TD_FULL, nz);
+        if (nz) {
+            const int pos = o + __popc(b & below);
+            xs[td_xidx(npc, pos, 0)] = v0;
+            xs[td_xidx(npc, pos, 1)] = v1;
+        }
+        o += __popc(b);
+    }
+    const int npad = (o + TD_ROUND - 1) & ~(TD_ROUND - 1);
+    for (int j = o + lane; j < npad; j += 32) {
+        xs[td_xidx(npc, j, 0)] = 0.f;
+        xs[td_xidx(npc, j, 1)] = 0.f;
+    }
+    __syncwarp();
+    return o;
+}
+
 /* ====================================================================== */
 /* filtered sweep (one warp, one subset)                                   */
 /* ====================================================================== */
@@ -2003,13 +2043,17 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
      * u32 } or the coarse histogram, whichever is larger | gcount | basis
      * (qa, qb, meta, fab, q32).  The bucket ids and lists of the rare path
      * are in the warp's global scratch. */
-    float *xs = reinterpret_cast<float *>(smem);
-    const size_t off = (size_t)nplanes_max * npc * 16;
+    /* D = 2 (one subset a query): every warp takes its own queries, with its
+     * own staging area of npc pairs in front of its region, and no block
+     * barrier */
+    const size_t xs_warp = (D == 2) ? (size_t)npc * 16 : 0;
+    const size_t off = (D == 2) ? 0 : (size_t)nplanes_max * npc * 16;
     const int Bmax = 1 << blog2_cap;
     const size_t hbytes = (size_t)(Bmax + 4) * 4;
     const size_t rbytes = max((size_t)TD_COARSE_WORDS * 4, hbytes);
     const size_t per_warp = (rbytes + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
-    unsigned char *wb = smem + off + per_warp * w;
+    unsigned char *wb = smem + off + (per_warp + xs_warp) * w + xs_warp;
+    float *xs = reinterpret_cast<float *>(D == 2 ? wb - xs_warp : smem);
     TdWarpSmem W;
     W.hist = reinterpret_cast<uint32_t *>(wb);
     const int gw = blockIdx.x * (blockDim.x >> 5) + w;
@@ -2026,6 +2070,51 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     for (int j = lane; j < max(Bmax + 4, TD_COARSE_WORDS); j += 32) W.hist[j] = 0u;
     unsigned long long *ws = s_stats[w];
     if (lane < 8) ws[lane] = 0ull;
+    if constexpr (D == 2) {
+        __syncwarp();
+        for (;;) {
+            unsigned long long tk = 0ull;
+            if (lane == 0) tk = atomicAdd(ticket, 1ull);
+            const int64_t tile = (int64_t)__shfl_sync(TD_FULL, tk, 0);
+            if (tile >= total) break;
+            const int j = td_query_of_tile(prefix, L.nq, tile);
+            const int q = L.order[j];
+            const TdQuery &Q = L.q[q];
+            const int nnz = Q.nnz;
+            const int64_t ts = L.tile_size[q];
+            const int64_t t0 = Q.lo + (tile - prefix[j]) * ts;
+            const uint64_t r0 = (uint64_t)t0, r1 = (uint64_t)min(t0 + ts, Q.hi);
+            int blog2 = 7;
+            while ((2 << blog2) < nnz && blog2 < blog2_cap) ++blog2;
+            int best = L.qmin[q];
+            if (L.early_exit && best <= 0) {
+                if (lane == 0) ws[7] += r1 - r0;
+                continue;
+            }
+            if (Q.d != 2 || blog2 > blog2_cap || nnz > L.nmax) {
+                if (lane == 0) ws[6]++; /* inconsistent sizes: the host reports TD_ERR_INTERNAL */
+                continue;
+            }
+            if (td_stage_points_warp(L, q, xs, npc, lane) != nnz) {
+                if (lane == 0) ws[6]++;
+                continue;
+            }
+            td_warp_filtered<D>(L, q, xs, npc, nnz, r0, r1, W, scr, blog2, lane, best, ws);
+            if (lane == 0 && best < INT_MAX) atomicMin(&L.qmin[q], best);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            atomicAdd(&L.ctr->sweeps, ws[0]);
+            atomicAdd(&L.ctr->dependent, ws[1]);
+            atomicAdd(&L.ctr->filtered_points, ws[2]);
+            atomicAdd(&L.ctr->exact_points, ws[3]);
+            atomicAdd(&L.ctr->tight, ws[4]);
+            atomicAdd(&L.ctr->resolved, ws[5]);
+            atomicAdd(&L.ctr->errors, ws[6]);
+            if (ws[7]) atomicAdd(&L.ctr->early, ws[7]);
+        }
+        return;
+    }
     int staged = -1;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(ticket, 1ull);
@@ -2261,13 +2350,15 @@ size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
 {
     int nmaxp = td_pow2_at_least(nmax);
     nmaxp = nmaxp < 128 ? 128 : nmaxp;
-    /* ceil(pmax/2) planes of (nmax rounded up to 128)/2 pairs, 16 bytes each */
-    size_t off = (size_t)((pmax + 1) / 2) * (size_t)(((nmax + TD_ROUND - 1) & ~(TD_ROUND - 1)) / 2) * 16;
+    /* ceil(pmax/2) planes of (nmax rounded up to 128)/2 pairs, 16 bytes each,
+     * shared by the CTA; for the D = 2 kernel (pmax = 2) one plane per warp */
+    const size_t plane = (size_t)(((nmax + TD_ROUND - 1) & ~(TD_ROUND - 1)) / 2) * 16;
     const size_t hbytes = (size_t)((1 << blog2) + 4) * 4;
     size_t rbytes = hbytes;
     if (rbytes < (size_t)TD_COARSE_WORDS * 4) rbytes = (size_t)TD_COARSE_WORDS * 4;
     size_t per_warp = (rbytes + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
-    return off + per_warp * warps;
+    if (pmax == 2) return (plane + per_warp) * warps;
+    return (size_t)((pmax + 1) / 2) * plane + per_warp * warps;
 }
 
 size_t td_plain_smem(int nmax, int pmax, int warps)

@@ -140,7 +140,6 @@ extern "C" int td_depth_noalloc(const int32_t *X, int32_t n, int32_t p, const in
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TD_ERR_CUDA;
     int blog2 = 7;
     while ((2 << blog2) < n && blog2 < 11) ++blog2;
-    const size_t smem = td_filtered_smem(n, p, blog2, kWarps);
 
     TdLaunch L;
     memset(&L, 0, sizeof(L));
@@ -180,10 +179,14 @@ extern "C" int td_depth_noalloc(const int32_t *X, int32_t n, int32_t p, const in
     if (td_launch_setup(L, s) != cudaSuccess) return TD_ERR_CUDA;
     if (td_launch_tiles(L, s) != cudaSuccess) return TD_ERR_CUDA;
     for (int D = 2; D <= std::min((int)p, 6); ++D) {
-        const int occ = td_filtered_occupancy(D, kWarps, smem);
+        /* each dimension's kernel sized for its own layout (pmax = D) */
+        TdLaunch LD = L;
+        LD.pmax = D;
+        const size_t smemD = td_filtered_smem(n, D, blog2, kWarps);
+        const int occ = td_filtered_occupancy(D, kWarps, smemD);
         if (occ < 1) return TD_ERR_INVALID;
         const int grid = std::min(sms * occ, TD_NOALLOC_CTAS);
-        if (td_launch_filtered(D, L, grid, smem, s) != cudaSuccess) return TD_ERR_CUDA;
+        if (td_launch_filtered(D, LD, grid, smemD, s) != cudaSuccess) return TD_ERR_CUDA;
     }
     if (td_launch_finalize(L, s) != cudaSuccess) return TD_ERR_CUDA;
     td_k_noalloc_status<<<1, 256, 0, s>>>(L, td_coord_limit(p), status);

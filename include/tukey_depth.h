@@ -110,8 +110,11 @@ typedef struct {
 typedef struct {
     uint64_t sweeps;            /* (query, subset of rank p-2) pairs swept (Algorithm 1 step 1) */
     uint64_t skipped_dependent; /* subsets of rank < p-2, skipped */
-    uint64_t filtered_points;   /* projected points placed by the FP32 filter alone */
-    uint64_t exact_points;      /* projected points that needed exact integer arithmetic */
+    uint64_t filtered_points;   /* projected points (over all sweeps) whose angular range the FP32
+                                   filter certified (plain mode: 0) */
+    uint64_t exact_points;      /* projected points it could not certify (the subset's own points
+                                   among them); in the sweeps that need their order they are placed
+                                   with exact integer arithmetic (plain mode: every point) */
     uint64_t tight_exceptions;  /* subsets whose span holds more data points than the subset */
     uint64_t resolved_buckets;  /* sweeps whose extremum needed an exact in-bucket order */
     uint64_t kernel_launches;   /* CUDA kernels launched by the call */

@@ -1567,7 +1567,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
         for (int j = lane; j < (TD_COARSE_WORDS >> 2); j += 32) z4[j] = make_uint4(0u, 0u, 0u, 0u);
         __syncwarp();
     }
-    auto round = [&](int i0, bool tail) {
+    auto round = [&](int i0) {
         int slot[UNR];
         uint32_t inc[UNR];
         float4 pl[NPR][NPL];
@@ -1579,13 +1579,11 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
             for (int c = 0; c < NPL; ++c) pl[h][c] = td_lds128(ba + 512u * h + c * pstride);
 #pragma unroll
         for (int h = 0; h < NPR; ++h) td_pair_rows<D>(pl[h], C, slot[2 * h], slot[2 * h + 1], inc[2 * h], inc[2 * h + 1]);
-        (void)tail;
 #pragma unroll
         for (int u = 0; u < UNR; ++u) td_reds_add(cq + ((unsigned)slot[u] << 7), inc[u]);
     };
-    const int nfull = nnz & ~(32 * UNR - 1);
-    for (int i0 = 0; i0 < nfull; i0 += 32 * UNR) round(i0, false);
-    if (nfull < nnz) round(nfull, true);
+    /* the last, partial round runs like the others over its padding zeros */
+    for (int i0 = 0; i0 < nnz; i0 += 32 * UNR) round(i0);
     __syncwarp();
     const uint32_t hU = W.hist[32 * 32 + lane];
     /* uncertain points: the padding points of the last round are zeros,

@@ -31,7 +31,12 @@ def test_noalloc_matches_td_depth_on_consecutive_calls():
     import torch
     from paper_1409_3901_gb300 import tukey as td
     ctx = td.Context(0)
-    cases = [_case(1, 300, 4, 24, 60), _case(2, 120, 5, 16, 40), _case(1, 300, 4, 24, 60)]
+    rng = np.random.default_rng(8)
+    B = rng.integers(-3, 4, size=(2, 4))
+    Xp = (rng.integers(-9, 10, size=(150, 2)) @ B).astype(np.int32)        # rank 2 inside p = 4
+    Zp = np.vstack([Xp[:10], (rng.integers(-9, 10, size=(10, 2)) @ B)]).astype(np.int32)
+    cases = [_case(1, 300, 4, 24, 60), _case(2, 120, 5, 16, 40), _case(5, 400, 2, 30, 50),
+             (Xp, Zp), _case(1, 300, 4, 24, 60)]
     free_after = []
     for X, Z in cases:
         want = ctx.depth(X, Z)                     # the existing entry point

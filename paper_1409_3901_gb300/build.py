@@ -2,7 +2,7 @@
 
     python -m paper_1409_3901_gb300.build [--force]
 
-The two translation units compile in parallel and are linked into one shared
+The translation units compile in parallel and are linked into one shared
 library next to this file.  Objects go to ``_build/`` (git-ignored).
 """
 import os
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtukeydepth.so")
-SOURCES = ["td_kernels.cu", "td_api.cu", "td_noalloc.cu"]
+SOURCES = ["td_kernels.cu", "td_api.cu", "td_noalloc.cu", "td_issue_rate.cu"]
 HEADERS = ["td_internal.h", "td_exact.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "550"]
@@ -33,7 +33,7 @@ def _stale():
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
-    deps.append(os.path.join(ROOT, "include", "tukey_depth.h"))
+    deps += [os.path.join(ROOT, "include", h) for h in ("tukey_depth.h", "td_issue_rate.h")]
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
 

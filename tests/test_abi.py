@@ -1,5 +1,5 @@
-"""The C-ABI library loads and exports every symbol include/tukey_depth.h
-declares; host-side argument checks (no GPU needed)."""
+"""The C-ABI library loads and exports every symbol the headers under
+include/ declare; host-side argument checks (no GPU needed)."""
 import ctypes
 import os
 import re
@@ -9,13 +9,16 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "tukey_depth.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 def _declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"\b(td_[a-z_]+)\s*\(", text)
-    return sorted(set(names))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(td_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -61,6 +64,10 @@ def test_null_and_bad_arguments_rejected_without_device(tukey):
     assert tukey.td_stream_create(None, 0, None) == tukey.TD_ERR_INVALID
     done = ctypes.c_int()
     assert tukey.td_stream_poll(None, 1, ctypes.byref(done)) == tukey.TD_ERR_INVALID
+    rate = ctypes.c_double()
+    assert tukey.td_issue_rate(0, 0, None, None) == tukey.TD_ERR_INVALID
+    assert tukey.td_issue_rate(0, 4, ctypes.byref(rate), None) == tukey.TD_ERR_INVALID
+    assert tukey.td_issue_rate(0, -1, ctypes.byref(rate), None) == tukey.TD_ERR_INVALID
 
 
 def test_create_reports_missing_device(tukey):
@@ -71,6 +78,8 @@ def test_create_reports_missing_device(tukey):
     rc = tukey.td_create(ctypes.byref(ptr), 0, None)
     assert rc in (tukey.TD_ERR_CUDA, tukey.TD_ERR_OOM)
     assert not ptr.value
+    rate = ctypes.c_double()
+    assert tukey.td_issue_rate(0, 0, ctypes.byref(rate), None) == tukey.TD_ERR_CUDA
 
 
 def test_structs_match_header_layout(tukey, tmp_path):

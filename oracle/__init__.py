@@ -12,5 +12,8 @@ from .oracle import (  # noqa: F401
     depth_range,
     bivariate_closed,
     rank,
+    adia,
+    critical,
+    ADIA_STATS,
     OracleError,
 )

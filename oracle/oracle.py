@@ -22,7 +22,8 @@ class OracleError(RuntimeError):
     pass
 
 
-_ERRORS = {-1: "invalid argument", -2: "coordinates exceed the exact-arithmetic bound", -3: "out of memory"}
+_ERRORS = {-1: "invalid argument", -2: "coordinates exceed the exact-arithmetic bound", -3: "out of memory",
+           -4: "internal inconsistency"}
 
 
 def build(force=False):
@@ -54,6 +55,10 @@ def _load():
             lib.oracle_bivariate_closed.restype = ctypes.c_int
             lib.oracle_rank.argtypes = [i32p, ctypes.c_int64, ctypes.c_int, i32p, i32p]
             lib.oracle_rank.restype = ctypes.c_int
+            lib.oracle_adia.argtypes = [i32p, ctypes.c_int64, ctypes.c_int, i32p, i64p, i64p]
+            lib.oracle_adia.restype = ctypes.c_int
+            lib.oracle_critical.argtypes = [i64p, ctypes.c_int64, i64p, ctypes.POINTER(ctypes.c_uint8)]
+            lib.oracle_critical.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -127,3 +132,33 @@ def rank(X, z):
     if r < 0:
         _check(r)
     return r, [int(piv[i]) for i in range(r)]
+
+
+ADIA_STATS = ("pops", "step4_subsets", "nodes", "max_stack", "union_points", "step5_subsets",
+              "d0_after_search", "algorithm1")
+
+
+def adia(X, z):
+    """Algorithm 3 (ADIA): (count, stats).  The count is never below depth(X, z)."""
+    lib = _load()
+    X, Xp = _i32(X)
+    z, zp = _i32(z)
+    n, p = X.shape
+    out = ctypes.c_int64(0)
+    st = (ctypes.c_int64 * 8)()
+    _check(lib.oracle_adia(Xp, n, p, zp, ctypes.byref(out), st))
+    return int(out.value), dict(zip(ADIA_STATS, (int(v) for v in st)))
+
+
+def critical(Y):
+    """(G, crit): Algorithm 2's minimum over generic directions for the 2-D
+    points Y and the 0/1 flags of the critical points (lines bounding a cell
+    whose count is G)."""
+    lib = _load()
+    Y = np.ascontiguousarray(Y, dtype=np.int64).reshape(-1, 2)
+    G = ctypes.c_int64(0)
+    crit = np.zeros(Y.shape[0], dtype=np.uint8)
+    _check(lib.oracle_critical(Y.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), Y.shape[0],
+                               ctypes.byref(G), crit.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+    return int(G.value), crit
+

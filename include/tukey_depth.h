@@ -70,6 +70,14 @@ extern "C" {
 typedef struct td_ctx td_ctx;
 typedef struct td_stream td_stream;
 
+/* Algorithms (td_options.algorithm). */
+#define TD_ALG_RCOM 0 /* Algorithm 1 (Section 3) over every (p-2)-subset: the exact count T */
+#define TD_ALG_ADIA 1 /* Algorithm 3 (Section 4): an adaptive search from the best data direction
+                         (Steps 2-4), then Algorithm 1 over the subsets of the points in the
+                         halfspaces of the nodes it ends with (Step 5).  Every value it takes is
+                         some V(S), so out[q] >= T; the paper reports out[q] == T in all its
+                         experiments, without proof.  Filtered mode, unsharded only. */
+
 /* Execution forms of the same computation (identical results). */
 #define TD_MODE_FILTERED 0    /* persistent launch over (dataset, query, subset-tile) work,
                                  FP32 filter with exact fallback, angular buckets */
@@ -89,6 +97,8 @@ typedef struct {
                                  directions u = +-x_j (Algorithm 3, Step 2).  The depths are
                                  unchanged; stats.early_skipped counts the subsets not swept.
                                  0 (default): every subset is swept. */
+    int32_t algorithm;        /* TD_ALG_RCOM (default) or TD_ALG_ADIA */
+    int32_t reserved;         /* must be 0 */
     int64_t shard_index;      /* multi-GPU sharding of Algorithm 1's subset loop: process only the */
     int64_t shard_count;      /* shard_index-th of shard_count contiguous ranges of subset positions
                                  of every query (0 or 1: all).  out[q] is then the minimum over that
@@ -123,6 +133,12 @@ typedef struct {
                                    launch stream around them) */
     uint64_t early_skipped;     /* subsets not swept because their query had reached 0
                                    (td_options.early_exit) */
+    uint64_t adia_pops;         /* Algorithm 3: nodes popped in Step 4 */
+    uint64_t adia_subsets;      /* Algorithm 3: subsets evaluated in Steps 2(c) and 4 (exact sort) */
+    uint64_t adia_union_points; /* Algorithm 3: points in the unions of Step 5(a), summed over queries
+                                   (Step 5(b) sweeps are counted in sweeps) */
+    uint64_t adia_fallbacks;    /* Algorithm 3: queries whose search outgrew its node table or
+                                   iteration bound and were swept in full (exact count) */
 } td_stats;
 
 /* Coordinate bound |X_ij - z_j| <= td_coord_limit(p) accepted for dimension p. */

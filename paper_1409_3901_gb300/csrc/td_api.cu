@@ -38,6 +38,12 @@ cudaError_t td_launch_plain(int D, const TdLaunch &L, int q, int grid, size_t sm
 cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s);
 int td_filtered_occupancy(int D, int warps, size_t smem);
 int td_plain_occupancy(int D, int warps, size_t smem);
+size_t td_adia_smem(int nmax, int D, int nev);
+int td_adia_nev(int nmax, int D, size_t limit);
+int td_adia_occupancy(int D, size_t smem);
+cudaError_t td_launch_adia(int D, const TdLaunch &L, int grid, int nev, size_t smem, cudaStream_t s);
+int td_adia_threads();
+int64_t td_adia_ws_entries();
 
 namespace {
 
@@ -82,13 +88,17 @@ cudaError_t grow_host(HostBuf &b, size_t bytes)
 /* Device state of one batched call (or one stream request). */
 struct Work {
     DevBuf X, Zq, sets, q, order, prefix, tsize, ticket, qmin, out, ctr, scratch;
+    DevBuf perm, akeys, adep, astk; /* Algorithm 3: staging order per query, node tables per CTA */
     int grid[TD_NDIM] = { 0, 0, 0, 0, 0 }; /* persistent grid of the sweep kernel of dimension D = 2 + i */
+    int agrid[TD_NDIM] = { 0, 0, 0, 0, 0 }; /* Algorithm 3 search kernel of dimension D = 2 + i: grid, */
+    int anev[TD_NDIM] = { 0, 0, 0, 0, 0 };  /* evaluating warps and shared memory */
+    size_t asmem[TD_NDIM] = { 0, 0, 0, 0, 0 };
 };
 
 struct GraphKey {
-    int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw, early_exit;
+    int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw, early_exit, algorithm;
     size_t smem;
-    const void *ptrs[13];
+    const void *ptrs[17];
     int64_t shard_index, shard_count;
     bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
 };
@@ -98,6 +108,7 @@ struct GraphKey {
 struct td_ctx {
     int device = 0;
     int sms = 0;
+    int smem_optin = 0; /* largest dynamic shared memory per block */
     td_options opt;
     cudaStream_t own = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
@@ -170,6 +181,15 @@ td_options default_options()
 }
 
 cudaStream_t stream_of(td_ctx *c) { return c->opt.stream ? (cudaStream_t)c->opt.stream : c->own; }
+
+int validate_options(const td_options &o)
+{
+    if (o.mode != TD_MODE_FILTERED && o.mode != TD_MODE_PLAIN_EXACT) return TD_ERR_INVALID;
+    if (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count)) return TD_ERR_INVALID;
+    if (o.algorithm != TD_ALG_RCOM && o.algorithm != TD_ALG_ADIA) return TD_ERR_INVALID;
+    if (o.algorithm == TD_ALG_ADIA && (o.mode != TD_MODE_FILTERED || o.shard_count > 1)) return TD_ERR_INVALID;
+    return TD_OK;
+}
 
 int validate_set(const td_dataset &d)
 {
@@ -354,6 +374,14 @@ TdLaunch make_launch(const Work &w, const Plan &P, const int32_t *x_arena, const
     L.scratch = (char *)w.scratch.p;
     L.scratch_per_warp = td_scratch_per_warp(P.nmax);
     L.early_exit = o.early_exit != 0;
+    L.adia = o.algorithm == TD_ALG_ADIA;
+    if (L.adia) {
+        L.perm = (uint16_t *)w.perm.p;
+        L.perm_stride = P.nmax;
+        L.adia_keys = (uint64_t *)w.akeys.p;
+        L.adia_dep = (int32_t *)w.adep.p;
+        L.adia_stack = (int32_t *)w.astk.p;
+    }
     return L;
 }
 
@@ -389,8 +417,21 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
     } else {
         size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
         TDCK(td_launch_setup(Lf, s));
+        nl = 1;
+        if (Lf.adia) {
+            /* Algorithm 3, Steps 2-5(a): the search sets each query's subset
+             * range, staging order and running minimum for the sweep */
+            for (int D = 3; D <= std::min(P.pmax, 6); ++D) {
+                TdLaunch LD = Lf;
+                LD.nmax = P.nmaxD[D - 2];
+                LD.pmax = D;
+                LD.scratch_per_warp = td_scratch_per_warp(LD.nmax);
+                TDCK(td_launch_adia(D, LD, w.agrid[D - 2], w.anev[D - 2], w.asmem[D - 2], s));
+                ++nl;
+            }
+        }
         TDCK(td_launch_tiles(Lf, s));
-        nl = 2;
+        ++nl;
         /* inside a stream capture only an "external" record becomes an event
          * node of the graph; outside a capture the flag changes nothing */
         if (ev_a) TDCK(cudaEventRecordWithFlags(ev_a, s, cudaEventRecordExternal));
@@ -433,6 +474,38 @@ size_t filtered_grids(td_ctx *ctx, const Plan &P, const td_options &o, int *grid
     return scratch;
 }
 
+/* Algorithm 3: grid, evaluating warps and shared memory of the search kernel
+ * of every dimension D = 3 .. min(pmax, 6), and its buffers (staging order
+ * per query, node tables per CTA).  Returns the scratch bytes it needs, or 0
+ * if a kernel cannot be resident. */
+size_t adia_prepare(td_ctx *ctx, Work &w, const Plan &P, cudaError_t *err)
+{
+    *err = cudaSuccess;
+    size_t scratch = 256;
+    int gmax = 0;
+    for (int D = 3; D <= std::min(P.pmax, 6); ++D) {
+        const int nmaxD = P.nmaxD[D - 2];
+        const int nev = td_adia_nev(nmaxD, D, (size_t)ctx->smem_optin);
+        if (nev < 1) return 0;
+        const size_t smem = td_adia_smem(nmaxD, D, nev);
+        const int occ = td_adia_occupancy(D, smem);
+        if (occ < 1) return 0;
+        const int grid = std::max(1, std::min(P.nq, ctx->sms * occ));
+        w.agrid[D - 2] = grid;
+        w.anev[D - 2] = nev;
+        w.asmem[D - 2] = smem;
+        gmax = std::max(gmax, grid);
+        scratch = std::max(scratch, (size_t)grid * nev * (size_t)td_scratch_per_warp(nmaxD));
+    }
+    const size_t ent = (size_t)std::max(gmax, 1) * (size_t)td_adia_ws_entries();
+    cudaError_t e = grow(w.perm, (size_t)std::max(P.nq, 1) * P.nmax * 2);
+    if (e == cudaSuccess) e = grow(w.akeys, ent * 8);
+    if (e == cudaSuccess) e = grow(w.adep, ent * 4);
+    if (e == cudaSuccess) e = grow(w.astk, ent * 4);
+    *err = e;
+    return scratch;
+}
+
 /* One synchronous batched call. */
 int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
 {
@@ -461,9 +534,16 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         warps_total = grid * kWarpsPlain;
         TDCK(alloc_work(ctx->w, P, warps_total, true));
     } else {
-        const size_t scratch = filtered_grids(ctx, P, o, grids);
+        size_t scratch = filtered_grids(ctx, P, o, grids);
         if (scratch < 1) return TD_ERR_INVALID;
         TDCK(alloc_work(ctx->w, P, 0, true));
+        if (o.algorithm == TD_ALG_ADIA) {
+            cudaError_t ae;
+            const size_t as = adia_prepare(ctx, ctx->w, P, &ae);
+            TDCK(ae);
+            if (as < 1) return TD_ERR_INVALID;
+            scratch = std::max(scratch, as);
+        }
         TDCK(grow(ctx->w.scratch, scratch));
     }
     memcpy(ctx->w.grid, grids, sizeof(grids));
@@ -486,10 +566,12 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         key.blog2 = blog2;
         key.spw = o.subsets_per_warp;
         key.early_exit = L.early_exit;
+        key.algorithm = o.algorithm;
         key.smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
         const Work &cw = ctx->w;
-        const void *pp[13] = { x_arena, cw.Zq.p, cw.sets.p, cw.q.p, cw.order.p, cw.prefix.p, cw.tsize.p,
-                               cw.ticket.p, cw.qmin.p, cw.out.p, cw.ctr.p, cw.scratch.p, cw.X.p };
+        const void *pp[17] = { x_arena,     cw.Zq.p,   cw.sets.p,  cw.q.p,     cw.order.p, cw.prefix.p,
+                               cw.tsize.p,  cw.ticket.p, cw.qmin.p, cw.out.p,   cw.ctr.p,   cw.scratch.p,
+                               cw.X.p,      cw.perm.p, cw.akeys.p, cw.adep.p,  cw.astk.p };
         memcpy(key.ptrs, pp, sizeof(pp));
         key.shard_index = L.shard_index;
         key.shard_count = L.shard_count;
@@ -522,6 +604,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         }
         TDCK(cudaGraphLaunch(ctx->gexec, s));
         launches = 3 + std::min(P.pmax, 6) - 1; /* set-up, tiles, sweeps for D = 2..min(p,6), finalize */
+        if (L.adia) launches += std::max(0, std::min(P.pmax, 6) - 2); /* search kernels, D = 3..min(p,6) */
     } else {
         rc = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, s, &launches, ctx->evs0, ctx->evs1);
         if (rc != TD_OK) return rc;
@@ -569,6 +652,10 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         st->tight_exceptions = C.tight;
         st->resolved_buckets = C.resolved;
         st->early_skipped = C.early;
+        st->adia_pops = C.adia_pops;
+        st->adia_subsets = C.adia_subsets;
+        st->adia_union_points = C.adia_union;
+        st->adia_fallbacks = C.adia_fallback;
         st->kernel_launches = (uint64_t)launches;
         float ms = 0.f, mss = 0.f;
         if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) != cudaSuccess) ms = -1.f;
@@ -625,8 +712,14 @@ extern "C" int td_create(td_ctx **out, int device, const td_options *opt)
     ctx->device = device;
     ctx->opt = opt ? *opt : default_options();
     if (ctx->opt.shard_count < 1) ctx->opt.shard_count = 1;
+    if (validate_options(ctx->opt) != TD_OK) {
+        delete ctx;
+        return TD_ERR_INVALID;
+    }
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
@@ -644,8 +737,9 @@ extern "C" int td_create(td_ctx **out, int device, const td_options *opt)
 extern "C" int td_set_options(td_ctx *ctx, const td_options *opt)
 {
     if (!ctx || !opt) return TD_ERR_INVALID;
-    if (opt->mode != TD_MODE_FILTERED && opt->mode != TD_MODE_PLAIN_EXACT) return TD_ERR_INVALID;
-    if (opt->shard_count > 1 && (opt->shard_index < 0 || opt->shard_index >= opt->shard_count)) return TD_ERR_INVALID;
+    td_options o = *opt;
+    if (o.shard_count < 1) o.shard_count = 1;
+    if (validate_options(o) != TD_OK) return TD_ERR_INVALID;
     ctx->opt = *opt;
     if (ctx->opt.shard_count < 1) ctx->opt.shard_count = 1;
     ctx->gvalid = false;
@@ -659,7 +753,8 @@ extern "C" int td_destroy(td_ctx *ctx)
     if (ctx->own) cudaStreamSynchronize(ctx->own);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     Work &w = ctx->w;
-    DevBuf *bufs[] = { &w.X, &w.Zq, &w.sets, &w.q, &w.order, &w.prefix, &w.tsize, &w.ticket, &w.qmin, &w.out, &w.ctr, &w.scratch };
+    DevBuf *bufs[] = { &w.X,      &w.Zq,  &w.sets, &w.q,     &w.order, &w.prefix, &w.tsize, &w.ticket,
+                       &w.qmin,   &w.out, &w.ctr,  &w.scratch, &w.perm, &w.akeys, &w.adep,  &w.astk };
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->hstage.p) cudaFreeHost(ctx->hstage.p);
@@ -767,9 +862,14 @@ int pump(td_stream *s)
     const int blog2 = blog2_for(P.nmax, o);
     (void)cudaGetLastError();
     int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
-    const size_t scratch = filtered_grids(ctx, P, o, grids);
+    size_t scratch = filtered_grids(ctx, P, o, grids);
     if (scratch < 1) return TD_ERR_INVALID;
     cudaError_t e = alloc_work(sl.w, P, 0, true);
+    if (e == cudaSuccess && o.algorithm == TD_ALG_ADIA) {
+        const size_t as = adia_prepare(ctx, sl.w, P, &e);
+        if (e == cudaSuccess && as < 1) return TD_ERR_INVALID;
+        scratch = std::max(scratch, as);
+    }
     if (e == cudaSuccess) e = grow(s->scratch, scratch);
     if (e == cudaSuccess && !sl.done) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     const size_t outb = (size_t)((P.nq + 3) & ~3) * 4 + sizeof(TdCounters);
@@ -907,7 +1007,8 @@ extern "C" int td_stream_destroy(td_stream *s)
     for (int k = 0; k < 2; ++k) {
         td_stream_slot &sl = s->slot[k];
         Work &w = sl.w;
-        DevBuf *bufs[] = { &w.X, &w.Zq, &w.sets, &w.q, &w.order, &w.prefix, &w.tsize, &w.ticket, &w.qmin, &w.out, &w.ctr, &w.scratch };
+        DevBuf *bufs[] = { &w.X,    &w.Zq,  &w.sets, &w.q,       &w.order, &w.prefix, &w.tsize, &w.ticket,
+                           &w.qmin, &w.out, &w.ctr,  &w.scratch, &w.perm,  &w.akeys,  &w.adep,  &w.astk };
         for (DevBuf *b : bufs)
             if (b->p) cudaFree(b->p);
         if (sl.hstage.p) cudaFreeHost(sl.hstage.p);

@@ -36,6 +36,7 @@ struct TdCounters {
     unsigned long long sweeps, dependent, filtered_points, exact_points, tight, resolved;
     unsigned long long errors;  /* device-side consistency failures (must stay 0) */
     unsigned long long early;   /* subsets not swept because their query had reached 0 (early exit) */
+    unsigned long long adia_pops, adia_subsets, adia_union, adia_fallback; /* Algorithm 3 search */
 };
 
 /* Parameters of the work-queue launches. */
@@ -61,5 +62,10 @@ struct TdLaunch {
     char *scratch;           /* per-warp global scratch for the exact tight-set path */
     int64_t scratch_per_warp;
     int32_t early_exit;      /* nonzero: seed qmin with the data-direction bound, stop a query at 0 */
-    int32_t pad2;
+    int32_t adia;            /* nonzero: Algorithm 3 (search kernel before the sweep) */
+    uint16_t *perm;          /* Algorithm 3: staging position of every nonzero point, per query, or null */
+    int64_t perm_stride;     /* entries per query in perm */
+    uint64_t *adia_keys;     /* Algorithm 3 node tables, per CTA of the search kernel */
+    int32_t *adia_dep;
+    int32_t *adia_stack;
 };

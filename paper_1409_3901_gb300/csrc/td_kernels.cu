@@ -759,9 +759,10 @@ __global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
 /* ====================================================================== */
 
 /* Stage the nonzero projected centred points of query q, in the order of the
- * data, into xs in the pair layout (td_xidx, nplanes planes npc pairs apart)
- * -- exact, the coordinates are integers below 2^24.  Returns the number
- * staged (== Q.nnz). */
+ * data (or, under Algorithm 3, in the order L.perm gives), into xs in the
+ * pair layout (td_xidx, nplanes planes npc pairs apart) -- exact, the
+ * coordinates are integers below 2^24.  Returns the number staged
+ * (== Q.nnz). */
 __device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int npc, int nplanes, int *s_tmp)
 {
     const TdQuery &Q = L.q[q];
@@ -802,10 +803,11 @@ __device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int npc, int
         bool nz = false;
         for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != zc[c];
         if (!nz) continue;
+        const int pos = L.perm ? (int)L.perm[(size_t)q * L.perm_stride + o] : o;
         for (int c = 0; c < 2 * nplanes; ++c) {
             float v = 0.f;
             if (c < d) v = (float)((int64_t)X[(int64_t)i * p + pv[c]] - zc[pv[c]]);
-            xs[td_xidx(npc, o, c)] = v;
+            xs[td_xidx(npc, pos, c)] = v;
         }
         ++o;
     }
@@ -2164,6 +2166,12 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
 }
 
 /* ====================================================================== */
+/* Algorithm 3 (ADIA): search kernel                                        */
+/* ====================================================================== */
+
+#include "td_adia.cuh"
+
+/* ====================================================================== */
 /* plain exact kernel (one query per launch)                               */
 /* ====================================================================== */
 
@@ -2430,6 +2438,58 @@ cudaError_t td_launch_plain(int D, const TdLaunch &L, int q, int grid, size_t sm
     td_plain_fn(D)<<<grid, L.warps * 32, smem, s>>>(L, q);
     return cudaGetLastError();
 }
+
+/* Algorithm 3 search kernel: shared memory for nev evaluating warps, and the
+ * largest nev (<= D-1) that fits in limit bytes (0 if none). */
+size_t td_adia_smem(int nmax, int D, int nev)
+{
+    const int nmaxp = td_pow2_at_least(nmax);
+    const int nwords = nmaxp >> 5;
+    const int PSI = D <= 4 ? 4 : 8;
+    size_t off = ((size_t)nmax * PSI * 4 + 15) & ~(size_t)15;
+    off += ((size_t)nmaxp * 2 + 15) & ~(size_t)15;
+    off += ((size_t)nwords * 4 + 15) & ~(size_t)15;
+    off += ((size_t)(nwords + 1) * 4 + 15) & ~(size_t)15;
+    return off + td_adia_warp_bytes(nmaxp) * (size_t)nev;
+}
+
+int td_adia_nev(int nmax, int D, size_t limit)
+{
+    for (int nev = D - 1; nev >= 1; --nev)
+        if (td_adia_smem(nmax, D, nev) <= limit) return nev;
+    return 0;
+}
+
+typedef void (*td_kfn_adia)(TdLaunch, int);
+
+static td_kfn_adia td_adia_fn(int D)
+{
+    switch (D) {
+    case 3: return td_k_adia<3>;
+    case 4: return td_k_adia<4>;
+    case 5: return td_k_adia<5>;
+    default: return td_k_adia<6>;
+    }
+}
+
+int td_adia_occupancy(int D, size_t smem)
+{
+    int blocks = 0;
+    if (cudaFuncSetAttribute(td_adia_fn(D), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_adia_fn(D), TD_ADIA_THREADS, smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+cudaError_t td_launch_adia(int D, const TdLaunch &L, int grid, int nev, size_t smem, cudaStream_t s)
+{
+    td_adia_fn(D)<<<grid, TD_ADIA_THREADS, smem, s>>>(L, nev);
+    return cudaGetLastError();
+}
+
+int td_adia_threads() { return TD_ADIA_THREADS; }
+int64_t td_adia_ws_entries() { return TD_ADIA_CAP; }
 
 cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s)
 {

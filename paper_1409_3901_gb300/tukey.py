@@ -27,6 +27,7 @@ TD_ERR_CUDA = -6
 TD_ERR_NOTFOUND = -7
 TD_ERR_INTERNAL = -8
 TD_MAX_P = 6
+TD_ALG_RCOM, TD_ALG_ADIA = 0, 1
 TD_ISSUE_FFMA, TD_ISSUE_FFMA2, TD_ISSUE_INT, TD_ISSUE_MIXED = 0, 1, 2, 3
 ISSUE_KINDS = {"ffma": TD_ISSUE_FFMA, "ffma2": TD_ISSUE_FFMA2, "int": TD_ISSUE_INT, "mixed": TD_ISSUE_MIXED}
 TD_MAX_N = 2048
@@ -48,6 +49,7 @@ class td_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("device_pointers", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("subsets_per_warp", ctypes.c_int32),
                 ("buckets_log2", ctypes.c_int32), ("early_exit", ctypes.c_int32),
+                ("algorithm", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("shard_index", ctypes.c_int64), ("shard_count", ctypes.c_int64),
                 ("stream", ctypes.c_void_p)]
 
@@ -62,7 +64,9 @@ class td_stats(ctypes.Structure):
                 ("filtered_points", ctypes.c_uint64), ("exact_points", ctypes.c_uint64),
                 ("tight_exceptions", ctypes.c_uint64), ("resolved_buckets", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("ms", ctypes.c_float),
-                ("ms_sweep", ctypes.c_float), ("early_skipped", ctypes.c_uint64)]
+                ("ms_sweep", ctypes.c_float), ("early_skipped", ctypes.c_uint64),
+                ("adia_pops", ctypes.c_uint64), ("adia_subsets", ctypes.c_uint64),
+                ("adia_union_points", ctypes.c_uint64), ("adia_fallbacks", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -134,7 +138,8 @@ def _check(rc, ctx=None):
 
 
 def options(mode=TD_MODE_FILTERED, device_pointers=False, use_graph=True, subsets_per_warp=0,
-            buckets_log2=0, shard_index=0, shard_count=1, stream=None, early_exit=False):
+            buckets_log2=0, shard_index=0, shard_count=1, stream=None, early_exit=False,
+            algorithm=TD_ALG_RCOM):
     o = td_options()
     o.mode = mode
     o.device_pointers = 1 if device_pointers else 0
@@ -142,6 +147,7 @@ def options(mode=TD_MODE_FILTERED, device_pointers=False, use_graph=True, subset
     o.subsets_per_warp = subsets_per_warp
     o.buckets_log2 = buckets_log2
     o.early_exit = 1 if early_exit else 0
+    o.algorithm = algorithm
     o.shard_index = shard_index
     o.shard_count = shard_count
     o.stream = stream

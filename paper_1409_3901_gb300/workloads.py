@@ -25,6 +25,10 @@ five benchmark workloads:
   W6  the bivariate case alone (p = 2: S is empty, one sweep per query):
       n = 2000, round(40 * N(0,1)) clipped; 16384 queries: 8192 data rows
       drawn with replacement and 8192 uniform points of the bounding box.
+  W7  the shapes of the paper's simulation (Section 5.2, Tables 2 and 3):
+      round(40 * N(0, I_p)) clipped, for (p, n) = (3, 1280), (4, 640),
+      (5, 160), (6, 80); 10 datasets each, with the four queries
+      z = alpha * 40 * 1_p, alpha in {0, 0.4, 0.8, 1.2} (160 queries).
 
 Random numbers come from a counter-based SplitMix64 stream (defined by its
 published constants), uniform doubles from its top 53 bits, Gaussians by the
@@ -252,6 +256,21 @@ def w6(seed=5, m=16384):
     unif = _bbox_uniform(st, X, m - half)
     return Dataset(X, np.vstack([rows, unif]).astype(np.int32),
                    "W6 p=2 n=2000 gaussian x40, %d queries" % m)
+
+
+W7_SHAPES = ((3, 1280), (4, 640), (5, 160), (6, 80))
+W7_ALPHAS = (0.0, 0.4, 0.8, 1.2)
+
+
+def w7(seed=6, reps=10):
+    out = []
+    for si, (p, n) in enumerate(W7_SHAPES):
+        for r in range(reps):
+            st = Stream(seed, sub=100 * (si + 1) + r)
+            X = _round_clip(40.0 * st.normal(n * p)).reshape(n, p)
+            Zq = np.array([[int(round(40 * a))] * p for a in W7_ALPHAS], dtype=np.int32)
+            out.append(Dataset(X, Zq, "W7[p=%d n=%d rep=%d]" % (p, n, r), {"p": p, "n": n, "rep": r}))
+    return out
 
 
 WORKLOADS = {"W1": w1, "W2": w2, "W4": w4, "W6": w6}

@@ -6,10 +6,12 @@ input checksum so that a test on another machine first checks that it
 regenerated the same inputs.  Queries are spread over worker processes
 (``spawn`` start method); the oracle code is the same in each.
 
-    python tests/golden/make_golden.py W1 W2 W4 W6 W3S W5S [--procs 8]
+    python tests/golden/make_golden.py W1 W2 W4 W6 W3S W5S W1A W2A W7A [--procs 8]
 
 W3S and W5S are bounded samples of the batched and stream workloads: every
-query of the datasets (requests) whose full oracle cost is small.
+query of the datasets (requests) whose full oracle cost is small.  W1A, W2A
+and W7A hold the counts of Algorithm 3 (ADIA, the oracle's oracle.adia) on
+W1, W2 and W7.
 """
 import argparse
 import json
@@ -37,8 +39,14 @@ def _one(args):
     return oracle.depth(X, z)
 
 
-def _run(pool, X, Zq):
-    return [int(v) for v in pool.map(_one, [(X, z) for z in Zq], chunksize=1)]
+def _one_adia(args):
+    import oracle
+    X, z = args
+    return oracle.adia(X, z)[0]
+
+
+def _run(pool, X, Zq, fn=_one):
+    return [int(v) for v in pool.map(fn, [(X, z) for z in Zq], chunksize=1)]
 
 
 def _cost(d):
@@ -60,6 +68,17 @@ def main():
                 d = W.WORKLOADS[name]()
                 out = {"workload": name, "description": d.name, "checksum": d.checksum(),
                        "n": d.n, "p": d.p, "m": d.m, "T": _run(pool, d.X, d.Zq)}
+            elif name in ("W1A", "W2A"):
+                d = W.WORKLOADS[name[:2]]()
+                out = {"workload": name[:2], "algorithm": "Algorithm 3 (ADIA)", "description": d.name,
+                       "checksum": d.checksum(), "n": d.n, "p": d.p, "m": d.m,
+                       "T": _run(pool, d.X, d.Zq, _one_adia)}
+            elif name == "W7A":
+                items = []
+                for i, d in enumerate(W.w7()):
+                    items.append({"index": i, "checksum": d.checksum(), "n": d.n, "p": d.p, "m": d.m,
+                                  "T": _run(pool, d.X, d.Zq, _one_adia)})
+                out = {"workload": "W7", "algorithm": "Algorithm 3 (ADIA)", "items": items}
             elif name in ("W3S", "W5S"):
                 sets = W.w3() if name == "W3S" else W.w5()
                 items = []

@@ -125,3 +125,16 @@ def test_workload_generators_are_deterministic():
     a_, c_ = d4.meta["hyperplane_a"], d4.meta["hyperplane_c"]
     on = (d4.X @ np.array(a_) == c_).sum()
     assert on >= 10
+
+
+def test_algorithm_option_validation(tukey):
+    """Algorithm 3 runs in the filtered form on unsharded calls only; unknown
+    algorithms are rejected before any device work."""
+    bad = [tukey.options(algorithm=2),
+           tukey.options(algorithm=tukey.TD_ALG_ADIA, mode=tukey.TD_MODE_PLAIN_EXACT),
+           tukey.options(algorithm=tukey.TD_ALG_ADIA, shard_index=0, shard_count=2)]
+    for o in bad:
+        ptr = ctypes.c_void_p()
+        assert tukey.td_create(ctypes.byref(ptr), 0, ctypes.byref(o)) == tukey.TD_ERR_INVALID
+        assert not ptr.value
+    assert tukey.td_set_options(None, ctypes.byref(bad[0])) == tukey.TD_ERR_INVALID

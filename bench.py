@@ -46,9 +46,10 @@ def _args():
     ap.add_argument("--plain-queries", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["W2", "W3", "W4", "W5", "W6"], default="W2",
+    ap.add_argument("--workload", choices=["W2", "W3", "W4", "W5", "W6", "W7"], default="W2",
                     help="W2 (default) is the benchmark line; W3 (256 datasets, one batched call), "
-                         "W4 (p=5 with ties) and W5 (request stream with Poisson arrivals) print "
+                         "W4 (p=5 with ties), W5 (request stream with Poisson arrivals), W6 (p=2) "
+                         "and W7 (the Section 5.2 shapes, Algorithm 1 against Algorithm 3) print "
                          "their own lines")
     ap.add_argument("--stream-seconds", type=float, default=20.0)
     return ap.parse_args()
@@ -314,6 +315,33 @@ def run_ours(a):
         em += f0.elapsed_time(f1)
         esw += early.last_stats.sweeps
         esk += early.last_stats.early_skipped
+    # Algorithm 3 (ADIA) on the same queries, reported apart: its count is an
+    # upper bound of T that the paper reports equal to T
+    actx = tukey.Context(local, device_pointers=True, stream=stream.cuda_stream,
+                         algorithm=tukey.TD_ALG_ADIA)
+    outa = torch.empty_like(out)
+    actx.depth(Xd, Zd, outa)
+    am, asw, apops, aun, afb = 0.0, 0, 0, 0, 0
+    for _ in range(e_steps):
+        flush.fill_(1)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        actx.depth(Xd, Zd, outa)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        am += f0.elapsed_time(f1)
+        sa = actx.last_stats
+        asw += sa.sweeps
+        apops += sa.adia_pops
+        aun += sa.adia_union_points
+        afb += sa.adia_fallbacks
+    adia_line = {"queries_per_s": d.m * e_steps / (am / 1e3), "ms_per_step": am / e_steps,
+                 "step5_sweeps_per_step": asw // e_steps, "pops_per_step": apops // e_steps,
+                 "mean_union_points": aun / e_steps / d.m, "fallbacks": afb,
+                 "equal_to_exact": int((outa == out).sum().item()), "queries": d.m,
+                 "note": "td_options.algorithm = TD_ALG_ADIA (Algorithm 3): search kernel, then the "
+                         "filtered sweep over the subsets of the Step 5 union. Not the full-sweep metric."}
     early_line = {"queries_per_s": d.m * e_steps / (em / 1e3), "ms_per_step": em / e_steps,
                   "sweeps_per_step": esw // e_steps, "skipped_per_step": esk // e_steps,
                   "same_results": bool(torch.equal(oute, out)),
@@ -356,6 +384,7 @@ def run_ours(a):
             "plain_exact": {"value": plain_rate, "unit": UNIT, "queries": int(Zp.shape[0]),
                             "same_results": same, "speedup_filtered_over_plain": value / ws / plain_rate},
             "early_exit": early_line,
+            "adia": adia_line,
             "stats_per_step": {k: v for k, v in ctx.last_stats.as_dict().items()},
             "clocks": clk}
     if not a.no_cpu_baseline:
@@ -397,6 +426,9 @@ def run_other(a):
                 "note": "sweep-kernel device time (td_stats.ms_sweep), one batched call per step; "
                         "*_all_kernels: set-up to finalize (td_stats.ms)"}
         print(json.dumps(line), flush=True)
+        return
+    if a.workload == "W7":
+        run_w7(a, tukey, W)
         return
     # W5: a stream of requests with Poisson arrivals, bounded sample
     import random
@@ -441,6 +473,55 @@ def run_other(a):
             "requests": len(lat), "arrival_rate_per_s": lam, "calibrated_rate_per_s": rate,
             "throughput_requests_per_s": len(lat) / el, "throughput_sweeps_per_s": done_sweeps / el,
             "sample": "requests with C(n,p-2)*n <= 3e8 among the first 400 of the stream, cycled"}
+    print(json.dumps(line), flush=True)
+
+
+def run_w7(a, tukey, W):
+    """The shapes of the paper's simulation (Section 5.2): Algorithm 1 (every
+    subset, the exact count) against Algorithm 3 (ADIA), per (p, n) and per
+    alpha, each cell one batched call over its 10 datasets; device time from
+    the first to the last kernel of the call (td_stats.ms)."""
+    sets = W.w7()
+    rcom = tukey.Context(0)
+    adia = tukey.Context(0, algorithm=tukey.TD_ALG_ADIA)
+
+    def timed(ctx, batch):
+        for _ in range(max(1, a.warmup - 2)):
+            outs = ctx.depth_batched(batch)
+        ms = 0.0
+        for _ in range(a.steps):
+            outs = ctx.depth_batched(batch)
+            ms += ctx.last_stats.ms
+        return ms / a.steps, outs, ctx.last_stats
+
+    cells = []
+    tot = {"rcom_ms": 0.0, "adia_ms": 0.0, "queries": 0, "equal": 0}
+    for p, n in W.W7_SHAPES:
+        group = [d for d in sets if d.meta["p"] == p and d.meta["n"] == n]
+        r_ms, r_out, r_st = timed(rcom, [(d.X, d.Zq) for d in group])
+        nq = sum(d.m for d in group)
+        tot["rcom_ms"] += r_ms
+        tot["queries"] += nq
+        for ai, alpha in enumerate(W.W7_ALPHAS):
+            batch = [(d.X, d.Zq[ai:ai + 1]) for d in group]
+            a_ms, a_out, a_st = timed(adia, batch)
+            exact = np.array([o[ai] for o in r_out])
+            got = np.array([o[0] for o in a_out])
+            eq = int((got == exact).sum())
+            tot["adia_ms"] += a_ms
+            tot["equal"] += eq
+            cells.append({"p": p, "n": n, "alpha": alpha, "datasets": len(group),
+                          "rcom_ms_per_query": r_ms / nq, "adia_ms_per_query": a_ms / len(group),
+                          "adia_equal_to_exact": eq, "mean_exact_depth": float(exact.mean()),
+                          "adia_pops": int(a_st.adia_pops), "adia_union_points": int(a_st.adia_union_points),
+                          "adia_step5_sweeps": int(a_st.sweeps), "adia_fallbacks": int(a_st.adia_fallbacks)})
+    line = {"metric": "query depths/s", "workload": "W7", "unit": "queries/s",
+            "rcom_queries_per_s": tot["queries"] / (tot["rcom_ms"] / 1e3),
+            "adia_queries_per_s": tot["queries"] / (tot["adia_ms"] / 1e3),
+            "queries": tot["queries"], "adia_equal_to_exact": tot["equal"], "steps": a.steps,
+            "cells": cells,
+            "note": "Algorithm 1 timed per (p, n) over its 40 queries, Algorithm 3 per (p, n, alpha) "
+                    "over 10 queries; td_stats.ms of one batched call, averaged over the steps"}
     print(json.dumps(line), flush=True)
 
 

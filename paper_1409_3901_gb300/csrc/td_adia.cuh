@@ -117,38 +117,17 @@ __device__ int td_adia_rank(const int64_t (*rows)[TD_MAXD], int cnt, int d)
     return rank;
 }
 
-/* Determinant of a k x k matrix (k <= 5) by fraction-free elimination. */
-__device__ td_i128 td_adia_det(td_i128 (*m)[TD_MAXD], int k)
+/* Per-warp shared buffers of one subset evaluation (nmaxp points): H (exact
+ * projections, int64 pairs) | Hf (their binary32 copies) | idx (sort list) |
+ * gcount | basis and meta rows | crit (critical-point bits) | cell flags. */
+__host__ __device__ inline size_t td_adia_crit_off(int nmaxp)
 {
-    td_i128 prev = 1;
-    int sign = 1;
-    for (int c = 0; c < k - 1; ++c) {
-        if (m[c][c] == 0) {
-            int sw = -1;
-            for (int r = c + 1; r < k; ++r)
-                if (m[r][c] != 0) { sw = r; break; }
-            if (sw < 0) return 0;
-            for (int cc = 0; cc < k; ++cc) {
-                td_i128 t = m[c][cc];
-                m[c][cc] = m[sw][cc];
-                m[sw][cc] = t;
-            }
-            sign = -sign;
-        }
-        for (int r = c + 1; r < k; ++r) {
-            for (int cc = c + 1; cc < k; ++cc) m[r][cc] = (m[r][cc] * m[c][c] - m[r][c] * m[c][cc]) / prev;
-            m[r][c] = 0;
-        }
-        prev = m[c][c];
-    }
-    return sign > 0 ? m[k - 1][k - 1] : -m[k - 1][k - 1];
+    return (size_t)nmaxp * 26 + 16 + TD_WARP_META_BYTES;
 }
 
-/* Per-warp shared buffers of one subset evaluation (nmaxp points). */
 __host__ __device__ inline size_t td_adia_warp_bytes(int nmaxp)
 {
-    return ((size_t)nmaxp * 16 + (size_t)nmaxp * 2 + 16 + TD_WARP_META_BYTES + (size_t)(nmaxp >> 3) + (size_t)nmaxp +
-            16 + 15) & ~(size_t)15;
+    return (td_adia_crit_off(nmaxp) + (size_t)(nmaxp >> 3) + (size_t)nmaxp + 16 + 15) & ~(size_t)15;
 }
 
 /* Exact V(S) of one subset c (compact point indices) by one warp, and, when
@@ -163,12 +142,13 @@ __device__ int td_adia_eval(const int32_t *xi, int PSI, int nnz, const int (&c)[
 {
     constexpr int K = D - 2;
     int64_t *H = reinterpret_cast<int64_t *>(wb);
-    uint16_t *idx = reinterpret_cast<uint16_t *>(wb + (size_t)nmaxp * 16);
-    int *gcount = reinterpret_cast<int *>(idx + nmaxp);
-    int64_t *wqa = reinterpret_cast<int64_t *>(wb + (size_t)nmaxp * 16 + (size_t)nmaxp * 2 + 16);
+    float2 *Hf = reinterpret_cast<float2 *>(wb + (size_t)nmaxp * 16);
+    uint16_t *idx = reinterpret_cast<uint16_t *>(wb + (size_t)nmaxp * 24);
+    int *gcount = reinterpret_cast<int *>(wb + (size_t)nmaxp * 26);
+    int64_t *wqa = reinterpret_cast<int64_t *>(wb + (size_t)nmaxp * 26 + 16);
     int64_t *wqb = wqa + TD_MAXD;
     int *wmeta = reinterpret_cast<int *>(wqb + TD_MAXD);
-    uint32_t *crit = reinterpret_cast<uint32_t *>(wb + (size_t)nmaxp * 16 + (size_t)nmaxp * 2 + 16 + TD_WARP_META_BYTES);
+    uint32_t *crit = reinterpret_cast<uint32_t *>(wb + td_adia_crit_off(nmaxp));
     unsigned char *cell = reinterpret_cast<unsigned char *>(crit + (nmaxp >> 5));
     for (int i = lane; i < (nmaxp >> 5); i += 32) crit[i] = 0u;
     int64_t s[K][D];
@@ -201,6 +181,7 @@ __device__ int td_adia_eval(const int32_t *xi, int PSI, int nnz, const int (&c)[
         if (valid) {
             H[2 * i] = h1;
             H[2 * i + 1] = h2;
+            Hf[i] = make_float2(__ll2float_rn(h1), __ll2float_rn(h2));
         }
         const unsigned bn = __ballot_sync(TD_FULL, nonz);
         if (nonz) idx[m + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)(i | (plus ? 0x8000 : 0));
@@ -213,10 +194,10 @@ __device__ int td_adia_eval(const int32_t *xi, int PSI, int nnz, const int (&c)[
         const int npad = td_pow2_at_least(m);
         for (int l = m + lane; l < npad; l += 32) idx[l] = TD_SENT;
         __syncwarp();
-        td_sort_exact(idx, npad, H, lane);
+        td_sort_exact(idx, npad, H, lane, Hf);
         auto same_line = [&](int l0, int l1) -> bool {
             const int a = idx[l0] & 0x7FFF, b = idx[l1] & 0x7FFF;
-            return td_cross_sign(H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) == 0;
+            return td_cross_sign_f(Hf[a], Hf[b], H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) == 0;
         };
         int A = 0;
         for (int l = lane; l < m; l += 32) A += (idx[l] >> 15) & 1;
@@ -323,7 +304,7 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
     __shared__ unsigned s_dkey;
     __shared__ unsigned long long s_okey, s_prev;
     __shared__ int s_le, s_ge, s_low, s_side;
-    __shared__ td_i128 s_cof[TD_MAXD];
+    __shared__ int64_t s_qa[TD_MAXD], s_qb[TD_MAXD], s_yt[2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int T = blockDim.x;
     const int nmaxp = td_pow2_at_least(L.nmax);
@@ -381,14 +362,27 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
          * key = count * 2^13 + 2 j + (1 for -x_j) orders count, j, sign */
         unsigned best = 0xFFFFFFFFu;
         for (int a = threadIdx.x; a < nnz; a += T) {
-            int64_t u[TD_MAXD];
-            for (int c = 0; c < p; ++c) u[c] = xorig(a, c);
             int le = Z, ge = Z;
-            for (int i = 0; i < nnz; ++i) {
-                int64_t dot = 0;
-                for (int c = 0; c < p; ++c) dot += u[c] * xorig(i, c);
-                le += dot <= 0;
-                ge += dot >= 0;
+            if (same_coords) { /* p == D: registers, unrolled */
+                int64_t u[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) u[c] = xi[(size_t)a * PSI + c];
+                for (int i = 0; i < nnz; ++i) {
+                    int64_t dot = 0;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) dot += u[c] * xi[(size_t)i * PSI + c];
+                    le += dot <= 0;
+                    ge += dot >= 0;
+                }
+            } else {
+                int64_t u[TD_MAXD];
+                for (int c = 0; c < p; ++c) u[c] = xorig(a, c);
+                for (int i = 0; i < nnz; ++i) {
+                    int64_t dot = 0;
+                    for (int c = 0; c < p; ++c) dot += u[c] * xorig(i, c);
+                    le += dot <= 0;
+                    ge += dot >= 0;
+                }
             }
             const unsigned j = orig[a];
             best = min(best, min(((unsigned)le << 13) | (j << 1), ((unsigned)ge << 13) | (j << 1) | 1u));
@@ -417,7 +411,12 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
          * (projection + 2^48) * 2^12 + index. */
         auto okey = [&](int i) -> unsigned long long {
             int64_t dot = 0;
-            for (int c = 0; c < p; ++c) dot += umin[c] * xorig(i, c);
+            if (same_coords) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) dot += umin[c] * xi[(size_t)i * PSI + c];
+            } else {
+                for (int c = 0; c < p; ++c) dot += umin[c] * xorig(i, c);
+            }
             return ((unsigned long long)(dot + ((int64_t)1 << 48)) << 12) | (unsigned long long)i;
         };
         const unsigned long long zero_key = (unsigned long long)((int64_t)1 << 48) << 12;
@@ -477,8 +476,7 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
             const int V0 = td_adia_eval<D>(xi, PSI, nnz, c, wb, nmaxp, scr, INT_MAX, lane);
             if (lane == 0) {
                 ++st_sub;
-                const uint32_t *crit = reinterpret_cast<const uint32_t *>(
-                    wb + (size_t)nmaxp * 16 + (size_t)nmaxp * 2 + 16 + TD_WARP_META_BYTES);
+                const uint32_t *crit = reinterpret_cast<const uint32_t *>(wb + td_adia_crit_off(nmaxp));
                 int h0 = -1;
                 for (int wd = 0; wd < nwords && h0 < 0; ++wd)
                     if (crit[wd]) h0 = wd * 32 + __ffs(crit[wd]) - 1;
@@ -539,8 +537,7 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
                         const int V = s_V[sidx2];
                         if (V > s_d0) continue;
                         const uint32_t *crit = reinterpret_cast<const uint32_t *>(
-                            smem + off + td_adia_warp_bytes(nmaxp) * (size_t)(sidx2 - base) + (size_t)nmaxp * 16 +
-                            (size_t)nmaxp * 2 + 16 + TD_WARP_META_BYTES);
+                            smem + off + td_adia_warp_bytes(nmaxp) * (size_t)(sidx2 - base) + td_adia_crit_off(nmaxp));
                         int Ss[TD_MAXD];
                         int o = 0;
                         for (int b = 0; b < K1; ++b)
@@ -602,58 +599,85 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
             __syncthreads();
             continue;
         }
-        /* Step 5(a): the closed side with fewer points of every node left */
-        for (int sl = 0; sl < TD_ADIA_CAP; ++sl) {
-            const uint64_t key = keys[sl];
-            if (key == 0ull || dep[sl] < 0) continue;
+        /* Step 5(a): the closed side with fewer points of every node left.
+         * For F = S + {t} (t its largest index) the functional
+         * x -> y_t x y_x of the projections by the basis of S vanishes on
+         * span(S) and on x_t, so it is det[x_F | x] up to a sign that is the
+         * same for every x; the choice of side below does not depend on that
+         * sign (fewer points, or on a tie the side of the least index off
+         * the hyperplane).  The nodes left are listed in stk first (the
+         * stack is empty now). */
+        if (threadIdx.x == 0) s_ns = 0;
+        __syncthreads();
+        for (int s2 = threadIdx.x; s2 < TD_ADIA_CAP; s2 += T)
+            if (keys[s2] != 0ull && dep[s2] >= 0) stk[atomicAdd(&s_ns, 1)] = s2;
+        __syncthreads();
+        const int nlive = s_ns;
+        for (int f = 0; f < nlive; ++f) {
             if (threadIdx.x == 0) {
                 int F[TD_MAXD];
-                td_adia_unpack(key, F, K1);
-                /* normal: cof[j] = (-1)^(j + D - 1) * det of the points' coordinates without row j */
-                for (int j = 0; j < D; ++j) {
-                    td_i128 mtx[TD_MAXD][TD_MAXD];
-                    for (int r = 0, rr = 0; r < D; ++r) {
-                        if (r == j) continue;
-                        for (int cc = 0; cc < K1; ++cc) mtx[rr][cc] = xi[(size_t)F[cc] * PSI + r];
-                        ++rr;
-                    }
-                    const td_i128 mnr = td_adia_det(mtx, K1);
-                    s_cof[j] = ((j + D - 1) & 1) ? -mnr : mnr;
+                td_adia_unpack(keys[stk[f]], F, K1);
+                int64_t sm[K][D];
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+#pragma unroll
+                    for (int cc = 0; cc < D; ++cc) sm[j][cc] = xi[(size_t)F[j] * PSI + cc];
+                TdBasis<D> Bs;
+                if (!td_make_basis<D>(sm, Bs)) ++st_err; /* F is independent: cannot happen */
+                int64_t y1 = 0, y2 = 0;
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc) {
+                    s_qa[cc] = Bs.qa[cc];
+                    s_qb[cc] = Bs.qb[cc];
+                    y1 += Bs.qa[cc] * (int64_t)xi[(size_t)F[K] * PSI + cc];
+                    y2 += Bs.qb[cc] * (int64_t)xi[(size_t)F[K] * PSI + cc];
                 }
+                s_yt[0] = y1;
+                s_yt[1] = y2;
                 s_le = Z;
                 s_ge = Z;
                 s_low = INT_MAX;
             }
             __syncthreads();
+            int64_t qa[D], qb[D];
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) {
+                qa[cc] = s_qa[cc];
+                qb[cc] = s_qb[cc];
+            }
+            const int64_t t1 = s_yt[0], t2 = s_yt[1];
+            auto side_of = [&](int i) -> int {
+                int64_t y1 = 0, y2 = 0;
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc) {
+                    const int64_t xv = xi[(size_t)i * PSI + cc];
+                    y1 += qa[cc] * xv;
+                    y2 += qb[cc] * xv;
+                }
+                return td_cross_sign(t1, t2, y1, y2);
+            };
             int le = 0, ge = 0, low = INT_MAX;
             for (int i = threadIdx.x; i < nnz; i += T) {
-                td_i128 dt = 0;
-                for (int j = 0; j < D; ++j) dt += s_cof[j] * (td_i128)xi[(size_t)i * PSI + j];
-                le += dt <= 0;
-                ge += dt >= 0;
-                if (dt != 0) low = min(low, i);
+                const int sg = side_of(i);
+                le += sg <= 0;
+                ge += sg >= 0;
+                if (sg != 0) low = min(low, i);
             }
             atomicAdd(&s_le, le);
             atomicAdd(&s_ge, ge);
             atomicMin(&s_low, low);
             __syncthreads();
             if (threadIdx.x == 0) {
-                int side = 0; /* -1: det <= 0, +1: det >= 0, 0: every point */
+                int side = 0; /* -1: <= 0, +1: >= 0, 0: every point */
                 if (s_le < s_ge) side = -1;
                 else if (s_ge < s_le) side = 1;
-                else if (s_low != INT_MAX) {
-                    td_i128 dt = 0;
-                    for (int j = 0; j < D; ++j) dt += s_cof[j] * (td_i128)xi[(size_t)s_low * PSI + j];
-                    side = dt > 0 ? 1 : -1;
-                }
+                else if (s_low != INT_MAX) side = side_of(s_low);
                 s_side = side;
             }
             __syncthreads();
             const int side = s_side;
             for (int i = threadIdx.x; i < nnz; i += T) {
-                td_i128 dt = 0;
-                for (int j = 0; j < D; ++j) dt += s_cof[j] * (td_i128)xi[(size_t)i * PSI + j];
-                const int sg = (dt > 0) - (dt < 0);
+                const int sg = side_of(i);
                 if (side == 0 || sg == 0 || sg == side) atomicOr(&inK[i >> 5], 1u << (i & 31));
             }
             __syncthreads();

@@ -237,18 +237,107 @@ __device__ __forceinline__ bool td_item_less(uint16_t u, uint16_t v, const int64
     return td_cross_sign(H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) > 0;
 }
 
-/* Bitonic sort of idx[0..npad) (npad a power of two >= 32; entries beyond the
- * valid ones are TD_SENT) by increasing line direction, one warp. */
-__device__ void td_sort_exact(uint16_t *idx, int npad, const int64_t *H, int lane)
+/* Sign of u x v for the exact integer pairs H (u = (u1, u2), ...) with
+ * binary32 copies Hf: the FP32 cross product decides when it exceeds its
+ * forward error bound, else the exact __int128 one.  Each float is the int64
+ * rounded to nearest (relative error <= u = 2^-24, products < 2^125, no
+ * overflow); the fma-based cross product then differs from the exact one by
+ * less than 6u(|u1 v2| + |u2 v1|), and |u1 v2| <= |p1|(1 + 4u) for the
+ * rounded product p1, so |c| > 8u(|p1| + |p2|) fixes the sign. */
+__device__ __forceinline__ int td_cross_sign_f(float2 uf, float2 vf, int64_t u1, int64_t u2, int64_t v1, int64_t v2)
 {
+    const float p2 = uf.y * vf.x;
+    const float p1 = uf.x * vf.y;
+    const float c = fmaf(uf.x, vf.y, -p2);
+    const float b = (8.0f * TD_U) * (fabsf(p1) + fabsf(p2));
+    if (c > b) return 1;
+    if (c < -b) return -1;
+    return td_cross_sign(u1, u2, v1, v2);
+}
+
+/* td_item_less with the FP32 filter of td_cross_sign_f (Hf may be null). */
+__device__ __forceinline__ bool td_item_less_f(uint16_t u, uint16_t v, const int64_t *H, const float2 *Hf)
+{
+    if (u == TD_SENT) return false;
+    if (v == TD_SENT) return true;
+    const int a = u & 0x7FFF, b = v & 0x7FFF;
+    if (!Hf) return td_cross_sign(H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) > 0;
+    return td_cross_sign_f(Hf[a], Hf[b], H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) > 0;
+}
+
+/* Bitonic sort of idx[0..npad) (npad a power of two >= 32; entries beyond the
+ * valid ones are TD_SENT) by increasing line direction, one warp.  The pairs
+ * of one step are disjoint, so each lane takes four of them at a time: all
+ * loads first, then the four comparisons, then the stores (the steps are
+ * latency-bound otherwise).  With Hf (binary32 copies of H, may be null) the
+ * comparisons are FP32-filtered; they are exact either way. */
+__device__ void td_sort_exact(uint16_t *idx, int npad, const int64_t *H, int lane, const float2 *Hf = nullptr)
+{
+    const int half = npad >> 1;
     for (int size = 2; size <= npad; size <<= 1)
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = lane; t < (npad >> 1); t += 32) {
+            int t = lane;
+            for (; t + 96 < half; t += 128) {
+                int ii[4], ia[4], ib[4], cr[4];
+                uint16_t u[4], v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int tt = t + 32 * k;
+                    ii[k] = ((tt & ~(stride - 1)) << 1) | (tt & (stride - 1));
+                    u[k] = idx[ii[k]];
+                    v[k] = idx[ii[k] + stride];
+                    ia[k] = u[k] == TD_SENT ? 0 : (u[k] & 0x7FFF);
+                    ib[k] = v[k] == TD_SENT ? 0 : (v[k] & 0x7FFF);
+                }
+                if (Hf) {
+                    float2 fa[4], fb[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        fa[k] = Hf[ia[k]];
+                        fb[k] = Hf[ib[k]];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float p2 = fa[k].y * fb[k].x;
+                        const float p1 = fa[k].x * fb[k].y;
+                        const float c = fmaf(fa[k].x, fb[k].y, -p2);
+                        const float bnd = (8.0f * TD_U) * (fabsf(p1) + fabsf(p2));
+                        cr[k] = c > bnd ? 1 : (c < -bnd ? -1 : 2);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (cr[k] == 2)
+                            cr[k] = td_cross_sign(H[2 * ia[k]], H[2 * ia[k] + 1], H[2 * ib[k]], H[2 * ib[k] + 1]);
+                } else {
+                    int64_t a1[4], a2[4], b1[4], b2[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        a1[k] = H[2 * ia[k]];
+                        a2[k] = H[2 * ia[k] + 1];
+                        b1[k] = H[2 * ib[k]];
+                        b2[k] = H[2 * ib[k] + 1];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cr[k] = td_cross_sign(a1[k], a2[k], b1[k], b2[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    /* u before v iff u is valid and (v is padding or u x v > 0) */
+                    const bool uv = u[k] != TD_SENT && (v[k] == TD_SENT || cr[k] > 0);
+                    const bool vu = v[k] != TD_SENT && (u[k] == TD_SENT || cr[k] < 0);
+                    const bool up = (ii[k] & size) == 0;
+                    if (up ? vu : uv) {
+                        idx[ii[k]] = v[k];
+                        idx[ii[k] + stride] = u[k];
+                    }
+                }
+            }
+            for (; t < half; t += 32) {
                 int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
                 int j = i + stride;
                 bool up = (i & size) == 0;
                 uint16_t u = idx[i], v = idx[j];
-                bool swap = up ? td_item_less(v, u, H) : td_item_less(u, v, H);
+                bool swap = up ? td_item_less_f(v, u, H, Hf) : td_item_less_f(u, v, H, Hf);
                 if (swap) {
                     idx[i] = v;
                     idx[j] = u;

@@ -45,7 +45,7 @@
 #define TD_ADIA_CAP_LOG2 11
 #define TD_ADIA_CAP (1 << TD_ADIA_CAP_LOG2)
 #define TD_ADIA_MAX_POPS 20000
-#define TD_ADIA_THREADS 160
+#define TD_ADIA_THREADS 256
 
 /* Node key: the sorted point indices (< 4096), 12 bits each, shifted left
  * by one with the low bit set (0 marks an empty slot). */
@@ -117,7 +117,7 @@ __device__ int td_adia_rank(const int64_t (*rows)[TD_MAXD], int cnt, int d)
     return rank;
 }
 
-/* Per-warp shared buffers of one subset evaluation (nmaxp points): H (exact
+/* Shared buffers of one subset evaluation (nmaxp points): H (exact
  * projections, int64 pairs) | Hf (their binary32 copies) | idx (sort list) |
  * gcount | basis and meta rows | crit (critical-point bits) | cell flags. */
 __host__ __device__ inline size_t td_adia_crit_off(int nmaxp)
@@ -125,9 +125,92 @@ __host__ __device__ inline size_t td_adia_crit_off(int nmaxp)
     return (size_t)nmaxp * 26 + 16 + TD_WARP_META_BYTES;
 }
 
-__host__ __device__ inline size_t td_adia_warp_bytes(int nmaxp)
+__host__ __device__ inline size_t td_adia_eval_bytes(int nmaxp)
 {
     return (td_adia_crit_off(nmaxp) + (size_t)(nmaxp >> 3) + (size_t)nmaxp + 16 + 15) & ~(size_t)15;
+}
+
+/* Block-wide exclusive prefix sum of v and the total (s_w: 32 ints). */
+__device__ __forceinline__ int td_block_excl(int v, int *s_w, int &tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int inc = td_wscan_incl(v, lane);
+    __syncthreads();
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    int base = 0, t = 0;
+    for (int k = 0; k < nw; ++k) {
+        const int x = s_w[k];
+        base += k < w ? x : 0;
+        t += x;
+    }
+    tot = t;
+    return base + inc - v;
+}
+
+/* Block-wide minimum (op 0) or maximum (op 1) of v (s_w: 32 ints). */
+__device__ __forceinline__ int td_block_minmax(int v, int *s_w, int op)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int r = op ? td_wmax(v) : td_wmin(v);
+    __syncthreads();
+    if (lane == 0) s_w[w] = r;
+    __syncthreads();
+    int t = s_w[0];
+    for (int k = 1; k < nw; ++k) t = op ? max(t, s_w[k]) : min(t, s_w[k]);
+    return t;
+}
+
+/* Bitonic sort of idx[0..npad) by increasing line direction with the whole
+ * block, FP32-filtered exact comparisons (td_cross_sign_f).  For strides up
+ * to 32 the pairs of a warp stay inside the warp's own 64-entry windows in
+ * every step, so those steps are separated by warp barriers only. */
+__device__ void td_sort_block(uint16_t *idx, int npad, const int64_t *H, const float2 *Hf)
+{
+    const int half = npad >> 1, T = blockDim.x;
+    for (int size = 2; size <= npad; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t0 = threadIdx.x; t0 < half; t0 += 2 * T) {
+                int ii[2], cr[2];
+                uint16_t u[2], v[2];
+                float2 fa[2], fb[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int tt = min(t0 + k * T, half - 1);
+                    ii[k] = ((tt & ~(stride - 1)) << 1) | (tt & (stride - 1));
+                    u[k] = idx[ii[k]];
+                    v[k] = idx[ii[k] + stride];
+                    fa[k] = Hf[u[k] == TD_SENT ? 0 : (u[k] & 0x7FFF)];
+                    fb[k] = Hf[v[k] == TD_SENT ? 0 : (v[k] & 0x7FFF)];
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float p2 = fa[k].y * fb[k].x;
+                    const float p1 = fa[k].x * fb[k].y;
+                    const float c = fmaf(fa[k].x, fb[k].y, -p2);
+                    const float bnd = (8.0f * TD_U) * (fabsf(p1) + fabsf(p2));
+                    cr[k] = c > bnd ? 1 : (c < -bnd ? -1 : 2);
+                    if (cr[k] == 2 && u[k] != TD_SENT && v[k] != TD_SENT) {
+                        const int ia = u[k] & 0x7FFF, ib = v[k] & 0x7FFF;
+                        cr[k] = td_cross_sign(H[2 * ia], H[2 * ia + 1], H[2 * ib], H[2 * ib + 1]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (t0 + k * T >= half) continue;
+                    /* u before v iff u is valid and (v is padding or u x v > 0) */
+                    const bool uv = u[k] != TD_SENT && (v[k] == TD_SENT || cr[k] == 1);
+                    const bool vu = v[k] != TD_SENT && (u[k] == TD_SENT || cr[k] == -1);
+                    const bool up = (ii[k] & size) == 0;
+                    if (up ? vu : uv) {
+                        idx[ii[k]] = v[k];
+                        idx[ii[k] + stride] = u[k];
+                    }
+                }
+            }
+            if (stride > 32 || stride == 1) __syncthreads();
+            else __syncwarp();
+        }
 }
 
 /* Exact V(S) of one subset c (compact point indices) by one warp, and, when
@@ -252,6 +335,152 @@ __device__ int td_adia_eval(const int32_t *xi, int PSI, int nnz, const int (&c)[
     return V;
 }
 
+/* Exact V(S) of one subset c (compact point indices, the same in every
+ * thread) by the whole block, and, when G(S) <= d0, the critical points of S
+ * as bits of crit (cleared first).  The projections are exact int64, the
+ * lines are ordered by a comparison sort with the exact (FP32-filtered)
+ * comparator, and the walk reads the count of every cell of the line
+ * arrangement.  Returns, in every thread, INT_MAX for a dependent subset;
+ * V(S) when G(S) <= d0, else G(S) (> d0). */
+template <int D>
+__device__ int td_adia_eval_block(const int32_t *xi, int PSI, int nnz, const int (&c)[D - 2], unsigned char *eb,
+                                  int nmaxp, const TdScratch &scr, int d0, int *s_w, int *s_res)
+{
+    constexpr int K = D - 2;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, w = tid >> 5;
+    int64_t *H = reinterpret_cast<int64_t *>(eb);
+    float2 *Hf = reinterpret_cast<float2 *>(eb + (size_t)nmaxp * 16);
+    uint16_t *idx = reinterpret_cast<uint16_t *>(eb + (size_t)nmaxp * 24);
+    int *gcount = reinterpret_cast<int *>(eb + (size_t)nmaxp * 26);
+    int64_t *wqa = reinterpret_cast<int64_t *>(eb + (size_t)nmaxp * 26 + 16);
+    int64_t *wqb = wqa + TD_MAXD;
+    int *wmeta = reinterpret_cast<int *>(wqb + TD_MAXD);
+    uint32_t *crit = reinterpret_cast<uint32_t *>(eb + td_adia_crit_off(nmaxp));
+    unsigned char *cell = reinterpret_cast<unsigned char *>(crit + (nmaxp >> 5));
+    for (int i = tid; i < (nmaxp >> 5); i += T) crit[i] = 0u;
+    /* the subset's basis, by warp 0, read by every thread from wqa / wqb */
+    if (w == 0) {
+        int64_t s[K][D];
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+#pragma unroll
+            for (int t = 0; t < D; ++t) s[j][t] = xi[(size_t)c[j] * PSI + t];
+        TdBasis<D> Bs;
+        const bool ok = td_make_basis<D>(s, Bs);
+        if (ok) td_publish_basis<D>(Bs, c, wqa, wqb, wmeta, lane);
+        if (lane == 0) s_res[1] = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_res[1]) return INT_MAX; /* the same in every thread */
+    int64_t qa[D], qb[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        qa[k] = wqa[k];
+        qb[k] = wqb[k];
+    }
+    /* exact projections; compacted list of the nonzero ones (orientation in bit 15) */
+    int m = 0, tcount = 0;
+    for (int i0 = 0; i0 < nnz; i0 += T) {
+        const int i = i0 + tid;
+        int64_t y1 = 0, y2 = 0;
+        const bool valid = i < nnz;
+        if (valid) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const int64_t xv = xi[(size_t)i * PSI + k];
+                y1 += qa[k] * xv;
+                y2 += qb[k] * xv;
+            }
+        }
+        const bool tight = valid && y1 == 0 && y2 == 0;
+        const bool nonz = valid && !tight;
+        int64_t h1 = 0, h2 = 0;
+        bool plus = false;
+        if (nonz) plus = td_normalise(y1, y2, h1, h2);
+        if (valid) {
+            H[2 * i] = h1;
+            H[2 * i + 1] = h2;
+            Hf[i] = make_float2(__ll2float_rn(h1), __ll2float_rn(h2));
+        }
+        int tot = 0, ttot = 0;
+        const int pos = td_block_excl(nonz ? 1 : 0, s_w, tot);
+        if (nonz) idx[m + pos] = (uint16_t)(i | (plus ? 0x8000 : 0));
+        td_block_excl(tight ? 1 : 0, s_w, ttot);
+        m += tot;
+        tcount += ttot;
+    }
+    int G = 0;
+    if (m > 0) {
+        const int npad = td_pow2_at_least(m);
+        for (int l = m + tid; l < npad; l += T) idx[l] = TD_SENT;
+        __syncthreads();
+        td_sort_block(idx, npad, H, Hf);
+        auto same_line = [&](int l0, int l1) -> bool {
+            const int a = idx[l0] & 0x7FFF, b = idx[l1] & 0x7FFF;
+            return td_cross_sign_f(Hf[a], Hf[b], H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) == 0;
+        };
+        const int C = (m + T - 1) / T;
+        const int beg = min(tid * C, m), end = min(beg + C, m);
+        int pl = 0, sev = 0, nst = 0;
+        for (int l = beg; l < end; ++l) {
+            pl += (idx[l] >> 15) & 1;
+            sev += (idx[l] & 0x8000) ? -1 : 1;
+            nst += (l == 0 || !same_line(l - 1, l)) ? 1 : 0;
+        }
+        int A = 0, tmp = 0;
+        td_block_excl(pl, s_w, A);
+        const int vexcl = A + td_block_excl(sev, s_w, tmp);
+        const int gexcl = td_block_excl(nst, s_w, tmp);
+        /* walk value after each group = count of the cell that follows it;
+         * A is the count of the cell before the first line (the same cell as
+         * the one after the last line, turned by pi) */
+        int v = vexcl, mn = A, mx = A;
+        for (int l = beg; l < end; ++l) {
+            v += (idx[l] & 0x8000) ? -1 : 1;
+            if (l + 1 == m || !same_line(l, l + 1)) {
+                mn = min(mn, v);
+                mx = max(mx, v);
+            }
+        }
+        mn = td_block_minmax(mn, s_w, 0);
+        mx = td_block_minmax(mx, s_w, 1);
+        G = min(mn, m - mx);
+        if (G <= d0) {
+            /* cell[g] = 1 when the cell before line group g has count G;
+             * cell[L] (after the last group) equals cell[0] */
+            if (tid == 0) cell[0] = (unsigned char)(min(A, m - A) == G);
+            v = vexcl;
+            int g = gexcl - 1;
+            for (int l = beg; l < end; ++l) {
+                v += (idx[l] & 0x8000) ? -1 : 1;
+                if (l == 0 || !same_line(l - 1, l)) ++g;
+                if (l + 1 == m || !same_line(l, l + 1)) cell[g + 1] = (unsigned char)(min(v, m - v) == G);
+            }
+            __syncthreads();
+            g = gexcl - 1;
+            for (int l = beg; l < end; ++l) {
+                if (l == 0 || !same_line(l - 1, l)) ++g;
+                if (cell[g] | cell[g + 1]) {
+                    const int i = idx[l] & 0x7FFF;
+                    atomicOr(&crit[i >> 5], 1u << (i & 31));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    int V = G;
+    if (tcount > K && G <= d0) {
+        if (w == 0) {
+            const int mS = td_tight_correction<D>(wmeta, nullptr, 0, xi, PSI, nnz, nullptr, H, scr, gcount, lane);
+            if (lane == 0) s_res[0] = mS;
+        }
+        __syncthreads();
+        V = G + s_res[0];
+        __syncthreads();
+    }
+    return V;
+}
+
 /* Exact staging of query q's nonzero centred points (pivot coordinates,
  * int32, row stride PSI) in data order, and their data indices. */
 __device__ int td_adia_stage(const TdLaunch &L, int q, int32_t *xi, int PSI, uint16_t *orig, int *s_tmp)
@@ -293,20 +522,19 @@ __device__ int td_adia_stage(const TdLaunch &L, int q, int32_t *xi, int PSI, uin
     return Q.nnz;
 }
 
-template <int D>
-__global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int nev)
+template <int D, bool WARP>
+__global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L)
 {
     constexpr int K = D - 2, K1 = D - 1;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_tmp[32];
+    __shared__ int s_tmp[32], s_w[32], s_res[4];
     __shared__ int s_node[TD_MAXD], s_S[TD_MAXD], s_V[TD_MAXD];
     __shared__ int s_d0, s_ns, s_done, s_fail, s_improved, s_pick, s_nk;
     __shared__ unsigned s_dkey;
     __shared__ unsigned long long s_okey, s_prev;
     __shared__ int s_le, s_ge, s_low, s_side;
     __shared__ int64_t s_qa[TD_MAXD], s_qb[TD_MAXD], s_yt[2];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int T = blockDim.x;
+    const int T = blockDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nmaxp = td_pow2_at_least(L.nmax);
     const int nwords = nmaxp >> 5;
     const int PSI = D <= 4 ? 4 : 8;
@@ -318,9 +546,16 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
     off += ((size_t)nwords * 4 + 15) & ~(size_t)15;
     int *wpre = reinterpret_cast<int *>(smem + off);
     off += ((size_t)(nwords + 1) * 4 + 15) & ~(size_t)15;
-    unsigned char *wb = smem + off + td_adia_warp_bytes(nmaxp) * (size_t)(w < nev ? w : 0);
-    const TdScratch scr =
-        td_scratch_at(L.scratch + (size_t)(blockIdx.x * nev + (w < nev ? w : 0)) * L.scratch_per_warp, nmaxp);
+    /* evaluation buffers: one for the block, or (WARP) one per warp w < D-1 */
+    const size_t ebytes = td_adia_eval_bytes(nmaxp);
+    const int wslot = (WARP && w < K1) ? w : 0;
+    unsigned char *eb = smem + off + ebytes * (size_t)wslot;
+    auto crit_of = [&](int slot) -> const uint32_t * {
+        return reinterpret_cast<const uint32_t *>(smem + off + ebytes * (size_t)slot + td_adia_crit_off(nmaxp));
+    };
+    const uint32_t *crit = crit_of(0);
+    const TdScratch scr = td_scratch_at(
+        L.scratch + ((size_t)blockIdx.x * (WARP ? TD_ADIA_THREADS / 32 : 1) + wslot) * L.scratch_per_warp, nmaxp);
     uint64_t *keys = L.adia_keys + (size_t)blockIdx.x * TD_ADIA_CAP;
     int32_t *dep = L.adia_dep + (size_t)blockIdx.x * TD_ADIA_CAP;
     int32_t *stk = L.adia_stack + (size_t)blockIdx.x * TD_ADIA_CAP;
@@ -469,14 +704,23 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
                 }
         __syncthreads();
         /* Step 2(c): V of the start subset and its critical point of least index */
-        if (w == 0) {
+        {
             int c[K];
 #pragma unroll
             for (int b = 0; b < K; ++b) c[b] = s_S[b];
-            const int V0 = td_adia_eval<D>(xi, PSI, nnz, c, wb, nmaxp, scr, INT_MAX, lane);
-            if (lane == 0) {
+            int V0 = 0;
+            if constexpr (WARP) {
+                if (w == 0) {
+                    const int v = td_adia_eval<D>(xi, PSI, nnz, c, eb, nmaxp, scr, INT_MAX, lane);
+                    if (lane == 0) s_res[2] = v;
+                }
+                __syncthreads();
+                V0 = s_res[2];
+            } else {
+                V0 = td_adia_eval_block<D>(xi, PSI, nnz, c, eb, nmaxp, scr, INT_MAX, s_w, s_res);
+            }
+            if (threadIdx.x == 0) {
                 ++st_sub;
-                const uint32_t *crit = reinterpret_cast<const uint32_t *>(wb + td_adia_crit_off(nmaxp));
                 int h0 = -1;
                 for (int wd = 0; wd < nwords && h0 < 0; ++wd)
                     if (crit[wd]) h0 = wd * 32 + __ffs(crit[wd]) - 1;
@@ -501,7 +745,10 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
             }
         }
         __syncthreads();
-        /* Step 4 */
+        /* Step 4: pop a node; its subsets in lexicographic order (subset j
+         * omits member K1-1-j), each evaluated by the whole block; thread 0
+         * pushes the new nodes of a subset with V <= d0 and stops at the
+         * first subset that lowers d0 */
         for (int pops = 0; !s_fail; ++pops) {
             if (threadIdx.x == 0) {
                 if (s_ns == 0) {
@@ -518,61 +765,66 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
             __syncthreads();
             if (s_done || s_fail) break;
             const int d0 = s_d0;
-            for (int base = 0; base < K1 && !s_improved; base += nev) {
-                const int sidx = base + w;
-                if (w < nev && sidx < K1) {
-                    /* subset sidx in lexicographic order omits member K1-1-sidx */
+            /* thread 0: apply (iii) and (iv) for subset sidx with value V and
+             * critical bits cb */
+            auto apply = [&](int sidx, int V, const uint32_t *cb) {
+                ++st_sub;
+                if (V > s_d0) return;
+                int c[K];
+#pragma unroll
+                for (int b = 0; b < K; ++b) c[b] = s_node[b < K1 - 1 - sidx ? b : b + 1];
+                for (int wd = 0; wd < nwords && !s_fail; ++wd) {
+                    uint32_t bits = cb[wd];
+                    for (int b = 0; b < K1; ++b)
+                        if ((s_node[b] >> 5) == wd) bits &= ~(1u << (s_node[b] & 31));
+                    while (bits) {
+                        const int tpt = wd * 32 + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        int Nn[TD_MAXD];
+                        for (int b = 0; b < K; ++b) Nn[b] = c[b];
+                        Nn[K] = tpt;
+                        for (int a = 1; a < K1; ++a)
+                            for (int b = a; b > 0 && Nn[b - 1] > Nn[b]; --b) {
+                                const int tt = Nn[b];
+                                Nn[b] = Nn[b - 1];
+                                Nn[b - 1] = tt;
+                            }
+                        const int sl = td_adia_insert(keys, dep, td_adia_pack(Nn, K1), V);
+                        if (sl == -2 || s_ns >= TD_ADIA_CAP) {
+                            s_fail = 1;
+                            break;
+                        }
+                        if (sl >= 0) stk[s_ns++] = sl;
+                    }
+                }
+                if (V < s_d0) { /* (iv) */
+                    s_d0 = V;
+                    s_improved = 1;
+                }
+            };
+            if constexpr (WARP) {
+                /* the D-1 subsets in parallel, one warp each */
+                if (w < K1) {
+                    int c[K];
+#pragma unroll
+                    for (int b = 0; b < K; ++b) c[b] = s_node[b < K1 - 1 - w ? b : b + 1];
+                    const int V = td_adia_eval<D>(xi, PSI, nnz, c, eb, nmaxp, scr, d0, lane);
+                    if (lane == 0) s_V[w] = V;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0)
+                    for (int sidx = 0; sidx < K1 && !s_improved && !s_fail; ++sidx) apply(sidx, s_V[sidx], crit_of(sidx));
+                __syncthreads();
+            } else {
+                for (int sidx = 0; sidx < K1; ++sidx) {
                     int c[K];
 #pragma unroll
                     for (int b = 0; b < K; ++b) c[b] = s_node[b < K1 - 1 - sidx ? b : b + 1];
-                    const int V = td_adia_eval<D>(xi, PSI, nnz, c, wb, nmaxp, scr, d0, lane);
-                    if (lane == 0) {
-                        s_V[sidx] = V;
-                        ++st_sub;
-                    }
+                    const int V = td_adia_eval_block<D>(xi, PSI, nnz, c, eb, nmaxp, scr, d0, s_w, s_res);
+                    if (threadIdx.x == 0) apply(sidx, V, crit);
+                    __syncthreads();
+                    if (s_improved || s_fail) break;
                 }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    for (int sidx2 = base; sidx2 < min(base + nev, K1) && !s_improved && !s_fail; ++sidx2) {
-                        const int V = s_V[sidx2];
-                        if (V > s_d0) continue;
-                        const uint32_t *crit = reinterpret_cast<const uint32_t *>(
-                            smem + off + td_adia_warp_bytes(nmaxp) * (size_t)(sidx2 - base) + td_adia_crit_off(nmaxp));
-                        int Ss[TD_MAXD];
-                        int o = 0;
-                        for (int b = 0; b < K1; ++b)
-                            if (b != K1 - 1 - sidx2) Ss[o++] = s_node[b];
-                        for (int wd = 0; wd < nwords && !s_fail; ++wd) {
-                            uint32_t bits = crit[wd];
-                            for (int b = 0; b < K1; ++b)
-                                if ((s_node[b] >> 5) == wd) bits &= ~(1u << (s_node[b] & 31));
-                            while (bits) {
-                                const int tpt = wd * 32 + __ffs(bits) - 1;
-                                bits &= bits - 1;
-                                int Nn[TD_MAXD];
-                                for (int b = 0; b < K; ++b) Nn[b] = Ss[b];
-                                Nn[K] = tpt;
-                                for (int a = 1; a < K1; ++a)
-                                    for (int b = a; b > 0 && Nn[b - 1] > Nn[b]; --b) {
-                                        const int tt = Nn[b];
-                                        Nn[b] = Nn[b - 1];
-                                        Nn[b - 1] = tt;
-                                    }
-                                const int sl = td_adia_insert(keys, dep, td_adia_pack(Nn, K1), V);
-                                if (sl == -2 || s_ns >= TD_ADIA_CAP) {
-                                    s_fail = 1;
-                                    break;
-                                }
-                                if (sl >= 0) stk[s_ns++] = sl;
-                            }
-                        }
-                        if (V < s_d0) { /* (iv) */
-                            s_d0 = V;
-                            s_improved = 1;
-                        }
-                    }
-                }
-                __syncthreads();
             }
             if (s_improved && !s_fail) {
                 /* Step 4(b): delete the nodes deeper than d0 */
@@ -714,5 +966,5 @@ __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L, int 
         atomicAdd(&L.ctr->adia_union, st_union);
         atomicAdd(&L.ctr->errors, st_err);
     }
-    if (lane == 0 && w < nev) atomicAdd(&L.ctr->adia_subsets, st_sub);
+    if (threadIdx.x == 0) atomicAdd(&L.ctr->adia_subsets, st_sub);
 }

@@ -38,11 +38,10 @@ cudaError_t td_launch_plain(int D, const TdLaunch &L, int q, int grid, size_t sm
 cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s);
 int td_filtered_occupancy(int D, int warps, size_t smem);
 int td_plain_occupancy(int D, int warps, size_t smem);
-size_t td_adia_smem(int nmax, int D, int nev);
-int td_adia_nev(int nmax, int D, size_t limit);
-int td_adia_occupancy(int D, size_t smem);
-cudaError_t td_launch_adia(int D, const TdLaunch &L, int grid, int nev, size_t smem, cudaStream_t s);
-int td_adia_threads();
+size_t td_adia_smem(int nmax, int D);
+int td_adia_occupancy(int D, int nmax, size_t smem);
+int td_adia_scratch_slots(int nmax);
+cudaError_t td_launch_adia(int D, const TdLaunch &L, int grid, size_t smem, cudaStream_t s);
 int64_t td_adia_ws_entries();
 
 namespace {
@@ -90,9 +89,8 @@ struct Work {
     DevBuf X, Zq, sets, q, order, prefix, tsize, ticket, qmin, out, ctr, scratch;
     DevBuf perm, akeys, adep, astk; /* Algorithm 3: staging order per query, node tables per CTA */
     int grid[TD_NDIM] = { 0, 0, 0, 0, 0 }; /* persistent grid of the sweep kernel of dimension D = 2 + i */
-    int agrid[TD_NDIM] = { 0, 0, 0, 0, 0 }; /* Algorithm 3 search kernel of dimension D = 2 + i: grid, */
-    int anev[TD_NDIM] = { 0, 0, 0, 0, 0 };  /* evaluating warps and shared memory */
-    size_t asmem[TD_NDIM] = { 0, 0, 0, 0, 0 };
+    int agrid[TD_NDIM] = { 0, 0, 0, 0, 0 }; /* Algorithm 3 search kernel of dimension D = 2 + i: */
+    size_t asmem[TD_NDIM] = { 0, 0, 0, 0, 0 }; /* grid and shared memory */
 };
 
 struct GraphKey {
@@ -426,7 +424,7 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
                 LD.nmax = P.nmaxD[D - 2];
                 LD.pmax = D;
                 LD.scratch_per_warp = td_scratch_per_warp(LD.nmax);
-                TDCK(td_launch_adia(D, LD, w.agrid[D - 2], w.anev[D - 2], w.asmem[D - 2], s));
+                TDCK(td_launch_adia(D, LD, w.agrid[D - 2], w.asmem[D - 2], s));
                 ++nl;
             }
         }
@@ -474,10 +472,10 @@ size_t filtered_grids(td_ctx *ctx, const Plan &P, const td_options &o, int *grid
     return scratch;
 }
 
-/* Algorithm 3: grid, evaluating warps and shared memory of the search kernel
- * of every dimension D = 3 .. min(pmax, 6), and its buffers (staging order
- * per query, node tables per CTA).  Returns the scratch bytes it needs, or 0
- * if a kernel cannot be resident. */
+/* Algorithm 3: grid and shared memory of the search kernel of every
+ * dimension D = 3 .. min(pmax, 6), and its buffers (staging order per query,
+ * node tables per CTA).  Returns the scratch bytes it needs, or 0 if a kernel
+ * cannot be resident. */
 size_t adia_prepare(td_ctx *ctx, Work &w, const Plan &P, cudaError_t *err)
 {
     *err = cudaSuccess;
@@ -485,17 +483,15 @@ size_t adia_prepare(td_ctx *ctx, Work &w, const Plan &P, cudaError_t *err)
     int gmax = 0;
     for (int D = 3; D <= std::min(P.pmax, 6); ++D) {
         const int nmaxD = P.nmaxD[D - 2];
-        const int nev = td_adia_nev(nmaxD, D, (size_t)ctx->smem_optin);
-        if (nev < 1) return 0;
-        const size_t smem = td_adia_smem(nmaxD, D, nev);
-        const int occ = td_adia_occupancy(D, smem);
+        const size_t smem = td_adia_smem(nmaxD, D);
+        if (smem > (size_t)ctx->smem_optin) return 0;
+        const int occ = td_adia_occupancy(D, nmaxD, smem);
         if (occ < 1) return 0;
         const int grid = std::max(1, std::min(P.nq, ctx->sms * occ));
         w.agrid[D - 2] = grid;
-        w.anev[D - 2] = nev;
         w.asmem[D - 2] = smem;
         gmax = std::max(gmax, grid);
-        scratch = std::max(scratch, (size_t)grid * nev * (size_t)td_scratch_per_warp(nmaxD));
+        scratch = std::max(scratch, (size_t)grid * td_adia_scratch_slots(nmaxD) * (size_t)td_scratch_per_warp(nmaxD));
     }
     const size_t ent = (size_t)std::max(gmax, 1) * (size_t)td_adia_ws_entries();
     cudaError_t e = grow(w.perm, (size_t)std::max(P.nq, 1) * P.nmax * 2);

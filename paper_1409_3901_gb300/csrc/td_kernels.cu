@@ -2528,9 +2528,12 @@ cudaError_t td_launch_plain(int D, const TdLaunch &L, int q, int grid, size_t sm
     return cudaGetLastError();
 }
 
-/* Algorithm 3 search kernel: shared memory for nev evaluating warps, and the
- * largest nev (<= D-1) that fits in limit bytes (0 if none). */
-size_t td_adia_smem(int nmax, int D, int nev)
+/* Algorithm 3 search kernel: the warp form (the D-1 subsets of a node in
+ * parallel warps) serves rows of at most 256 points, the block form (each
+ * subset by the whole block) longer ones; dynamic shared memory of each. */
+bool td_adia_warp_form(int nmax) { return td_pow2_at_least(nmax) <= 256; }
+
+size_t td_adia_smem(int nmax, int D)
 {
     const int nmaxp = td_pow2_at_least(nmax);
     const int nwords = nmaxp >> 5;
@@ -2539,45 +2542,39 @@ size_t td_adia_smem(int nmax, int D, int nev)
     off += ((size_t)nmaxp * 2 + 15) & ~(size_t)15;
     off += ((size_t)nwords * 4 + 15) & ~(size_t)15;
     off += ((size_t)(nwords + 1) * 4 + 15) & ~(size_t)15;
-    return off + td_adia_warp_bytes(nmaxp) * (size_t)nev;
+    return off + td_adia_eval_bytes(nmaxp) * (size_t)(td_adia_warp_form(nmax) ? D - 1 : 1);
 }
 
-int td_adia_nev(int nmax, int D, size_t limit)
-{
-    for (int nev = D - 1; nev >= 1; --nev)
-        if (td_adia_smem(nmax, D, nev) <= limit) return nev;
-    return 0;
-}
+/* global scratch slots (warps) per CTA of the search kernel */
+int td_adia_scratch_slots(int nmax) { return td_adia_warp_form(nmax) ? TD_ADIA_THREADS / 32 : 1; }
 
-typedef void (*td_kfn_adia)(TdLaunch, int);
+typedef void (*td_kfn_adia)(TdLaunch);
 
-static td_kfn_adia td_adia_fn(int D)
+static td_kfn_adia td_adia_fn(int D, bool warp)
 {
     switch (D) {
-    case 3: return td_k_adia<3>;
-    case 4: return td_k_adia<4>;
-    case 5: return td_k_adia<5>;
-    default: return td_k_adia<6>;
+    case 3: return warp ? td_k_adia<3, true> : td_k_adia<3, false>;
+    case 4: return warp ? td_k_adia<4, true> : td_k_adia<4, false>;
+    case 5: return warp ? td_k_adia<5, true> : td_k_adia<5, false>;
+    default: return warp ? td_k_adia<6, true> : td_k_adia<6, false>;
     }
 }
 
-int td_adia_occupancy(int D, size_t smem)
+int td_adia_occupancy(int D, int nmax, size_t smem)
 {
     int blocks = 0;
-    if (cudaFuncSetAttribute(td_adia_fn(D), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_adia_fn(D), TD_ADIA_THREADS, smem) != cudaSuccess)
-        return 0;
+    const td_kfn_adia fn = td_adia_fn(D, td_adia_warp_form(nmax));
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, TD_ADIA_THREADS, smem) != cudaSuccess) return 0;
     return blocks;
 }
 
-cudaError_t td_launch_adia(int D, const TdLaunch &L, int grid, int nev, size_t smem, cudaStream_t s)
+cudaError_t td_launch_adia(int D, const TdLaunch &L, int grid, size_t smem, cudaStream_t s)
 {
-    td_adia_fn(D)<<<grid, TD_ADIA_THREADS, smem, s>>>(L, nev);
+    td_adia_fn(D, td_adia_warp_form(L.nmax))<<<grid, TD_ADIA_THREADS, smem, s>>>(L);
     return cudaGetLastError();
 }
 
-int td_adia_threads() { return TD_ADIA_THREADS; }
 int64_t td_adia_ws_entries() { return TD_ADIA_CAP; }
 
 cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s)

@@ -77,6 +77,15 @@ typedef struct td_stream td_stream;
                          halfspaces of the nodes it ends with (Step 5).  Every value it takes is
                          some V(S), so out[q] >= T; the paper reports out[q] == T in all its
                          experiments, without proof.  Filtered mode, unsharded only. */
+#define TD_ALG_CRITICAL 2 /* Proposition 1 (Section 2) with r = p-1: the minimum over the
+                             hyperplanes spanned by p-1 centred points of the points strictly on
+                             the smaller side, plus the open depth of the points on the hyperplane
+                             inside it: the exact count T by a second route, O(n^(p-1)) normals
+                             of O(n) work each, one launch per query (a cross-check of
+                             Algorithm 1).  Data sets with p <= 5 and p! M^p < 2^62 for the
+                             largest centred coordinate M (TD_ERR_INVALID / TD_ERR_RANGE
+                             otherwise); td_options.mode is ignored; not served by the stream
+                             API (td_stream_create returns TD_ERR_INVALID). */
 
 /* Execution forms of the same computation (identical results). */
 #define TD_MODE_FILTERED 0    /* persistent launch over (dataset, query, subset-tile) work,
@@ -97,7 +106,7 @@ typedef struct {
                                  directions u = +-x_j (Algorithm 3, Step 2).  The depths are
                                  unchanged; stats.early_skipped counts the subsets not swept.
                                  0 (default): every subset is swept. */
-    int32_t algorithm;        /* TD_ALG_RCOM (default) or TD_ALG_ADIA */
+    int32_t algorithm;        /* TD_ALG_RCOM (default), TD_ALG_ADIA or TD_ALG_CRITICAL */
     int32_t reserved;         /* must be 0 */
     int64_t shard_index;      /* multi-GPU sharding of Algorithm 1's subset loop: process only the */
     int64_t shard_count;      /* shard_index-th of shard_count contiguous ranges of subset positions

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtukeydepth.so")
 SOURCES = ["td_kernels.cu", "td_api.cu", "td_noalloc.cu", "td_issue_rate.cu"]
-HEADERS = ["td_internal.h", "td_exact.cuh", "td_adia.cuh"]
+HEADERS = ["td_internal.h", "td_exact.cuh", "td_adia.cuh", "td_critical.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "550"]
 

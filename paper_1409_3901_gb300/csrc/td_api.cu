@@ -43,6 +43,10 @@ int td_adia_occupancy(int D, int nmax, size_t smem);
 int td_adia_scratch_slots(int nmax);
 cudaError_t td_launch_adia(int D, const TdLaunch &L, int grid, size_t smem, cudaStream_t s);
 int64_t td_adia_ws_entries();
+size_t td_critical_smem(int nmax, int pmax);
+int td_critical_occupancy(int D, size_t smem);
+cudaError_t td_launch_critical(int D, const TdLaunch &L, int q, int grid, size_t smem, cudaStream_t s);
+int td_critical_threads();
 
 namespace {
 
@@ -184,7 +188,8 @@ int validate_options(const td_options &o)
 {
     if (o.mode != TD_MODE_FILTERED && o.mode != TD_MODE_PLAIN_EXACT) return TD_ERR_INVALID;
     if (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count)) return TD_ERR_INVALID;
-    if (o.algorithm != TD_ALG_RCOM && o.algorithm != TD_ALG_ADIA) return TD_ERR_INVALID;
+    if (o.algorithm != TD_ALG_RCOM && o.algorithm != TD_ALG_ADIA && o.algorithm != TD_ALG_CRITICAL)
+        return TD_ERR_INVALID;
     if (o.algorithm == TD_ALG_ADIA && (o.mode != TD_MODE_FILTERED || o.shard_count > 1)) return TD_ERR_INVALID;
     return TD_OK;
 }
@@ -217,6 +222,30 @@ bool range_ok(const td_dataset &d)
             if (hi[c] - z > lim || z - lo[c] > lim) return false;
         }
     return true;
+}
+
+/* Proposition 1 with r = p-1 (TD_ALG_CRITICAL): p <= 5 and p! M^p < 2^62 for
+ * the largest centred coordinate M, so that every normal and every n.x is
+ * exact in int64. */
+bool critical_range_ok(int p, int64_t M)
+{
+    if (p > 5) return false;
+    long double v = 1.0L;
+    for (int i = 2; i <= p; ++i) v *= i;
+    for (int i = 0; i < p; ++i) v *= (long double)M;
+    return v < 4611686018427387904.0L; /* 2^62 */
+}
+
+int64_t max_centred(const td_dataset &d)
+{
+    int64_t M = 0;
+    for (int64_t q = 0; q < (int64_t)d.m; ++q)
+        for (int64_t i = 0; i < (int64_t)d.n; ++i)
+            for (int c = 0; c < d.p; ++c) {
+                const int64_t v = (int64_t)d.X[i * d.p + c] - d.Z[q * d.p + c];
+                M = std::max(M, v < 0 ? -v : v);
+            }
+    return M;
 }
 
 struct Plan {
@@ -373,6 +402,7 @@ TdLaunch make_launch(const Work &w, const Plan &P, const int32_t *x_arena, const
     L.scratch_per_warp = td_scratch_per_warp(P.nmax);
     L.early_exit = o.early_exit != 0;
     L.adia = o.algorithm == TD_ALG_ADIA;
+    L.critical = o.algorithm == TD_ALG_CRITICAL;
     if (L.adia) {
         L.perm = (uint16_t *)w.perm.p;
         L.perm_stride = P.nmax;
@@ -391,7 +421,30 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
                     cudaStream_t s, int *launches, cudaEvent_t ev_a = nullptr, cudaEvent_t ev_b = nullptr)
 {
     int nl = 0;
-    if (o.mode == TD_MODE_PLAIN_EXACT) {
+    if (o.algorithm == TD_ALG_CRITICAL) {
+        /* Proposition 1 with r = p-1: one launch per query, after reading
+         * back each query's effective dimension */
+        TdLaunch L = Lf;
+        L.warps = td_critical_threads() / 32;
+        const size_t smem = td_critical_smem(P.nmax, P.pmax);
+        TDCK(td_launch_setup(L, s));
+        ++nl;
+        std::vector<TdQuery> hq(P.nq);
+        TDCK(cudaMemcpyAsync(hq.data(), w.q.p, P.nq * sizeof(TdQuery), cudaMemcpyDeviceToHost, s));
+        TDCK(cudaStreamSynchronize(s));
+        if (ev_a) TDCK(cudaEventRecord(ev_a, s));
+        for (int q = 0; q < P.nq; ++q) {
+            const int D = hq[q].d;
+            if (hq[q].k < 0 || hq[q].hi <= hq[q].lo || D < 2 || D > 5) continue;
+            const int occ = td_critical_occupancy(D, smem);
+            if (occ < 1) return TD_ERR_INVALID;
+            TDCK(td_launch_critical(D, L, q, ctx->sms * occ, smem, s));
+            ++nl;
+        }
+        if (ev_b) TDCK(cudaEventRecord(ev_b, s));
+        TDCK(td_launch_finalize(L, s));
+        ++nl;
+    } else if (o.mode == TD_MODE_PLAIN_EXACT) {
         TdLaunch L = Lf;
         L.warps = kWarpsPlain;
         size_t smem = td_plain_smem(P.nmax, P.pmax, kWarpsPlain);
@@ -512,6 +565,11 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         if (v != TD_OK) return v;
         if (!devptr && !range_ok(sets[s2])) return TD_ERR_RANGE;
     }
+    if (ctx->opt.algorithm == TD_ALG_CRITICAL)
+        for (int s2 = 0; s2 < k; ++s2) {
+            if (sets[s2].p > 5) return TD_ERR_INVALID;
+            if (!devptr && !critical_range_ok(sets[s2].p, max_centred(sets[s2]))) return TD_ERR_RANGE;
+        }
     if (st) memset(st, 0, sizeof(*st));
     Plan P = make_plan(sets, k);
     if (P.nq == 0) return TD_OK;
@@ -521,7 +579,15 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     int grid = 0, warps_total = 0;
     (void)cudaGetLastError(); /* clear any stale error of an earlier call */
     int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
-    if (o.mode == TD_MODE_PLAIN_EXACT) {
+    if (o.algorithm == TD_ALG_CRITICAL) {
+        const size_t smem = td_critical_smem(P.nmax, P.pmax);
+        int occ = 0;
+        for (int D = 2; D <= 5; ++D) occ = std::max(occ, td_critical_occupancy(D, smem));
+        if (occ < 1) return TD_ERR_INVALID;
+        grid = ctx->sms * occ;
+        warps_total = grid * (td_critical_threads() / 32);
+        TDCK(alloc_work(ctx->w, P, warps_total, true));
+    } else if (o.mode == TD_MODE_PLAIN_EXACT) {
         size_t smem = td_plain_smem(P.nmax, P.pmax, kWarpsPlain);
         int occ = 0;
         for (int D = 2; D <= 6; ++D) occ = std::max(occ, td_plain_occupancy(D, kWarpsPlain, smem));
@@ -550,7 +616,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     TdLaunch L = make_launch(ctx->w, P, x_arena, o, kWarpsFiltered, blog2);
     TDCK(cudaEventRecord(ctx->ev0, s));
     int launches = 0;
-    if (o.mode == TD_MODE_FILTERED && o.use_graph) {
+    if (o.mode == TD_MODE_FILTERED && o.use_graph && o.algorithm != TD_ALG_CRITICAL) {
         GraphKey key;
         memset(&key, 0, sizeof(key));
         key.nq = P.nq;
@@ -617,8 +683,12 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         TDCK(cudaMemcpy(hq.data(), ctx->w.q.p, P.nq * sizeof(TdQuery), cudaMemcpyDeviceToHost));
         for (int qi = 0; qi < P.nq; ++qi) {
             int64_t lim = td_coord_limit(P.sets[hq[qi].set].p);
-            for (int c = 0; c < TD_MAXD; ++c)
+            int64_t M = 0;
+            for (int c = 0; c < TD_MAXD; ++c) {
                 if (hq[qi].mx[c] > lim) return TD_ERR_RANGE;
+                M = std::max<int64_t>(M, hq[qi].mx[c]);
+            }
+            if (o.algorithm == TD_ALG_CRITICAL && !critical_range_ok(hq[qi].d, M)) return TD_ERR_RANGE;
         }
     }
     if (devptr) {
@@ -905,6 +975,7 @@ extern "C" int td_stream_create(td_ctx *ctx, size_t mem_budget_bytes, td_stream 
 {
     if (!ctx || !out) return TD_ERR_INVALID;
     *out = nullptr;
+    if (ctx->opt.algorithm == TD_ALG_CRITICAL) return TD_ERR_INVALID; /* a synchronous cross-check form */
     td_stream *s = new (std::nothrow) td_stream();
     if (!s) return TD_ERR_OOM;
     s->ctx = ctx;

@@ -63,6 +63,8 @@ struct TdLaunch {
     int64_t scratch_per_warp;
     int32_t early_exit;      /* nonzero: seed qmin with the data-direction bound, stop a query at 0 */
     int32_t adia;            /* nonzero: Algorithm 3 (search kernel before the sweep) */
+    int32_t critical;        /* nonzero: Proposition 1 with r = p-1 (subsets of d-1 points) */
+    int32_t pad3;
     uint16_t *perm;          /* Algorithm 3: staging position of every nonzero point, per query, or null */
     int64_t perm_stride;     /* entries per query in perm */
     uint64_t *adia_keys;     /* Algorithm 3 node tables, per CTA of the search kernel */

@@ -726,8 +726,8 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
             Q->lo = Q->hi = 0;
         } else {
             Q->direct = -1;
-            Q->k = d - 2;
-            int64_t ns = (int64_t)td_binom(n - Z, d - 2);
+            Q->k = L.critical ? d - 1 : d - 2;
+            int64_t ns = (int64_t)td_binom(n - Z, Q->k);
             Q->nsub = ns;
             int64_t sc = L.shard_count > 1 ? L.shard_count : 1;
             int64_t si = L.shard_count > 1 ? L.shard_index : 0;
@@ -2261,6 +2261,12 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
 #include "td_adia.cuh"
 
 /* ====================================================================== */
+/* Proposition 1 with r = p-1: critical-direction kernel                    */
+/* ====================================================================== */
+
+#include "td_critical.cuh"
+
+/* ====================================================================== */
 /* plain exact kernel (one query per launch)                               */
 /* ====================================================================== */
 
@@ -2576,6 +2582,41 @@ cudaError_t td_launch_adia(int D, const TdLaunch &L, int grid, size_t smem, cuda
 }
 
 int64_t td_adia_ws_entries() { return TD_ADIA_CAP; }
+
+/* critical-direction kernel (d = 2..5): shared memory, occupancy, launch */
+size_t td_critical_smem(int nmax, int pmax)
+{
+    const int PSI = pmax <= 4 ? 4 : 8;
+    return (((size_t)nmax * PSI * 4 + 15) & ~(size_t)15) + (size_t)td_pow2_at_least(nmax) * 2;
+}
+
+static td_kfn_plain td_critical_fn(int D)
+{
+    switch (D) {
+    case 2: return td_k_critical<2>;
+    case 3: return td_k_critical<3>;
+    case 4: return td_k_critical<4>;
+    default: return td_k_critical<5>;
+    }
+}
+
+int td_critical_occupancy(int D, size_t smem)
+{
+    int blocks = 0;
+    if (cudaFuncSetAttribute(td_critical_fn(D), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_critical_fn(D), TD_CRIT_THREADS, smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+cudaError_t td_launch_critical(int D, const TdLaunch &L, int q, int grid, size_t smem, cudaStream_t s)
+{
+    td_critical_fn(D)<<<grid, TD_CRIT_THREADS, smem, s>>>(L, q);
+    return cudaGetLastError();
+}
+
+int td_critical_threads() { return TD_CRIT_THREADS; }
 
 cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s)
 {

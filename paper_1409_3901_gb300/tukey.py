@@ -27,7 +27,7 @@ TD_ERR_CUDA = -6
 TD_ERR_NOTFOUND = -7
 TD_ERR_INTERNAL = -8
 TD_MAX_P = 6
-TD_ALG_RCOM, TD_ALG_ADIA = 0, 1
+TD_ALG_RCOM, TD_ALG_ADIA, TD_ALG_CRITICAL = 0, 1, 2
 TD_ISSUE_FFMA, TD_ISSUE_FFMA2, TD_ISSUE_INT, TD_ISSUE_MIXED = 0, 1, 2, 3
 ISSUE_KINDS = {"ffma": TD_ISSUE_FFMA, "ffma2": TD_ISSUE_FFMA2, "int": TD_ISSUE_INT, "mixed": TD_ISSUE_MIXED}
 TD_MAX_N = 2048

@@ -130,7 +130,7 @@ def test_workload_generators_are_deterministic():
 def test_algorithm_option_validation(tukey):
     """Algorithm 3 runs in the filtered form on unsharded calls only; unknown
     algorithms are rejected before any device work."""
-    bad = [tukey.options(algorithm=2),
+    bad = [tukey.options(algorithm=3),
            tukey.options(algorithm=tukey.TD_ALG_ADIA, mode=tukey.TD_MODE_PLAIN_EXACT),
            tukey.options(algorithm=tukey.TD_ALG_ADIA, shard_index=0, shard_count=2)]
     for o in bad:
@@ -138,3 +138,14 @@ def test_algorithm_option_validation(tukey):
         assert tukey.td_create(ctypes.byref(ptr), 0, ctypes.byref(o)) == tukey.TD_ERR_INVALID
         assert not ptr.value
     assert tukey.td_set_options(None, ctypes.byref(bad[0])) == tukey.TD_ERR_INVALID
+
+
+def test_critical_form_not_served_by_streams(tukey):
+    """TD_ALG_CRITICAL is accepted by td_create's validation; the stream API
+    refuses it (checked without a device: td_create fails first on CPU)."""
+    o = tukey.options(algorithm=tukey.TD_ALG_CRITICAL)
+    ptr = ctypes.c_void_p()
+    rc = tukey.td_create(ctypes.byref(ptr), 0, ctypes.byref(o))
+    assert rc != tukey.TD_ERR_INVALID
+    if ptr.value:
+        tukey.td_destroy(ptr)

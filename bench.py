@@ -425,6 +425,8 @@ def run_other(a):
                 "queries_per_s_all_kernels": nq * a.steps / (sum(msc) / 1e3),
                 "note": "sweep-kernel device time (td_stats.ms_sweep), one batched call per step; "
                         "*_all_kernels: set-up to finalize (td_stats.ms)"}
+        if a.workload == "W4":
+            line["critical_cross_check"] = _critical_cross_check(tukey, sets[0], ctx, a.steps)
         print(json.dumps(line), flush=True)
         return
     if a.workload == "W7":
@@ -474,6 +476,25 @@ def run_other(a):
             "throughput_requests_per_s": len(lat) / el, "throughput_sweeps_per_s": done_sweeps / el,
             "sample": "requests with C(n,p-2)*n <= 3e8 among the first 400 of the stream, cycled"}
     print(json.dumps(line), flush=True)
+
+
+def _critical_cross_check(tukey, d, rcom, steps, count=64):
+    """Proposition 1 with r = p-1 (TD_ALG_CRITICAL) on the first `count`
+    queries: hyperplanes (p-1 subsets) per second, device time of the call,
+    and agreement with Algorithm 1."""
+    crit = tukey.Context(0, algorithm=tukey.TD_ALG_CRITICAL)
+    Z = d.Zq[:count]
+    want = rcom.depth(d.X, Z)
+    crit.depth(d.X, Z)
+    ms, hyp = 0.0, 0
+    for _ in range(max(1, min(steps, 2))):
+        got = crit.depth(d.X, Z)
+        ms += crit.last_stats.ms
+        hyp += crit.last_stats.sweeps
+    reps = max(1, min(steps, 2))
+    return {"queries": int(Z.shape[0]), "hyperplanes_per_s": hyp / (ms / 1e3), "ms_per_call": ms / reps,
+            "hyperplanes_per_call": hyp // reps, "equal_to_algorithm_1": int((got == want).sum()),
+            "note": "td_options.algorithm = TD_ALG_CRITICAL, one launch per query, exact int64"}
 
 
 def run_w7(a, tukey, W):

@@ -277,7 +277,7 @@ __device__ int td_adia_eval(const int32_t *xi, int PSI, int nnz, const int (&c)[
         const int npad = td_pow2_at_least(m);
         for (int l = m + lane; l < npad; l += 32) idx[l] = TD_SENT;
         __syncwarp();
-        td_sort_exact(idx, npad, H, lane, Hf);
+        td_sort_exact_fast(idx, npad, H, lane, Hf);
         auto same_line = [&](int l0, int l1) -> bool {
             const int a = idx[l0] & 0x7FFF, b = idx[l1] & 0x7FFF;
             return td_cross_sign_f(Hf[a], Hf[b], H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) == 0;

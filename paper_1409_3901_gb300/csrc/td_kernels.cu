@@ -266,12 +266,34 @@ __device__ __forceinline__ bool td_item_less_f(uint16_t u, uint16_t v, const int
 }
 
 /* Bitonic sort of idx[0..npad) (npad a power of two >= 32; entries beyond the
- * valid ones are TD_SENT) by increasing line direction, one warp.  The pairs
- * of one step are disjoint, so each lane takes four of them at a time: all
- * loads first, then the four comparisons, then the stores (the steps are
- * latency-bound otherwise).  With Hf (binary32 copies of H, may be null) the
- * comparisons are FP32-filtered; they are exact either way. */
-__device__ void td_sort_exact(uint16_t *idx, int npad, const int64_t *H, int lane, const float2 *Hf = nullptr)
+ * valid ones are TD_SENT) by increasing line direction, one warp. */
+__device__ void td_sort_exact(uint16_t *idx, int npad, const int64_t *H, int lane)
+{
+    for (int size = 2; size <= npad; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < (npad >> 1); t += 32) {
+                int i = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
+                int j = i + stride;
+                bool up = (i & size) == 0;
+                uint16_t u = idx[i], v = idx[j];
+                bool swap = up ? td_item_less(v, u, H) : td_item_less(u, v, H);
+                if (swap) {
+                    idx[i] = v;
+                    idx[j] = u;
+                }
+            }
+            __syncwarp();
+        }
+}
+
+/* The same sort for the plain form and the Algorithm 3 search, where
+ * registers are not scarce: the pairs of one step are disjoint, so each lane
+ * takes four of them at a time (all loads first, then the four comparisons,
+ * then the stores; the steps are latency-bound otherwise), and with Hf
+ * (binary32 copies of H, may be null) the comparisons are FP32-filtered;
+ * they are exact either way.  (The sweep kernel keeps td_sort_exact: this
+ * one, inlined there, costs it registers.) */
+__device__ void td_sort_exact_fast(uint16_t *idx, int npad, const int64_t *H, int lane, const float2 *Hf)
 {
     const int half = npad >> 1;
     for (int size = 2; size <= npad; size <<= 1)
@@ -2324,7 +2346,14 @@ __device__ void td_warp_plain(const TdLaunch &L, int q, const int32_t *xi, int P
             t += __popc(__ballot_sync(TD_FULL, tight));
         }
         __syncwarp();
-        int G = td_sweep_list(idx, base, H, lane);
+        int G = 0;
+        {
+            const int npad = td_pow2_at_least(base);
+            for (int l = base + lane; l < npad; l += 32) idx[l] = TD_SENT;
+            __syncwarp();
+            td_sort_exact_fast(idx, npad, H, lane, nullptr);
+            G = td_walk_sorted(idx, base, H, lane);
+        }
         st.exact += (lane == 0) ? nnz : 0;
         int V = G;
         if (t > K && G < best) {

@@ -516,13 +516,15 @@ def run_w7(a, tukey, W):
         return ms / a.steps, outs, ctx.last_stats
 
     cells = []
-    tot = {"rcom_ms": 0.0, "adia_ms": 0.0, "queries": 0, "equal": 0}
+    tot = {"rcom_ms": 0.0, "adia_ms": 0.0, "adia_shape_ms": 0.0, "queries": 0, "equal": 0}
     for p, n in W.W7_SHAPES:
         group = [d for d in sets if d.meta["p"] == p and d.meta["n"] == n]
         r_ms, r_out, r_st = timed(rcom, [(d.X, d.Zq) for d in group])
         nq = sum(d.m for d in group)
         tot["rcom_ms"] += r_ms
         tot["queries"] += nq
+        s_ms, _, _ = timed(adia, [(d.X, d.Zq) for d in group])
+        tot["adia_shape_ms"] += s_ms
         for ai, alpha in enumerate(W.W7_ALPHAS):
             batch = [(d.X, d.Zq[ai:ai + 1]) for d in group]
             a_ms, a_out, a_st = timed(adia, batch)
@@ -539,10 +541,12 @@ def run_w7(a, tukey, W):
     line = {"metric": "query depths/s", "workload": "W7", "unit": "queries/s",
             "rcom_queries_per_s": tot["queries"] / (tot["rcom_ms"] / 1e3),
             "adia_queries_per_s": tot["queries"] / (tot["adia_ms"] / 1e3),
+            "adia_queries_per_s_shape_batches": tot["queries"] / (tot["adia_shape_ms"] / 1e3),
             "queries": tot["queries"], "adia_equal_to_exact": tot["equal"], "steps": a.steps,
             "cells": cells,
             "note": "Algorithm 1 timed per (p, n) over its 40 queries, Algorithm 3 per (p, n, alpha) "
-                    "over 10 queries; td_stats.ms of one batched call, averaged over the steps"}
+                    "over 10 queries (and per (p, n) over 40: *_shape_batches); td_stats.ms of one "
+                    "batched call, averaged over the steps"}
     print(json.dumps(line), flush=True)
 
 

@@ -154,3 +154,21 @@ def test_golden_w7_batched(adia):
     assert adia.last_stats.adia_fallbacks == 0
     for it, o in zip(g["items"], outs):
         assert np.array_equal(o, np.array(it["T"])), (it["index"], o.tolist(), it["T"])
+
+
+def test_golden_w3_sample_batched(adia):
+    """40 datasets of the batched workload W3 (p in {3, 4, 5}, n from 100 to
+    2000) in one call: the search kernel of each dimension runs in the block
+    form for every query of the batch."""
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W3SA")
+    sets = W.w3()
+    batch = []
+    for it in g["items"]:
+        d = sets[it["index"]]
+        assert d.checksum() == it["checksum"]
+        batch.append((d.X, d.Zq))
+    outs = adia.depth_batched(batch)
+    assert adia.last_stats.adia_fallbacks == 0
+    for it, o in zip(g["items"], outs):
+        assert np.array_equal(o, np.array(it["T"])), (it["index"], o.tolist(), it["T"])

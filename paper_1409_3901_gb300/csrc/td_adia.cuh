@@ -2,9 +2,10 @@
  * td_adia.cuh -- Algorithm 3 (ADIA, Section 4) on the device; included by
  * td_kernels.cu after the exact sweep helpers it uses.
  *
- * td_k_adia<D> runs Steps 2-4 and Step 5(a) for the queries of effective
- * dimension D (persistent CTAs, one query at a time per CTA, in work order),
- * and hands Step 5(b) to the filtered sweep: it writes the staging order of
+ * td_k_adia<D, WARP> runs Steps 2-4 and Step 5(a) for the queries of
+ * effective dimension D (persistent CTAs of 256 threads, one query at a time
+ * per CTA, in work order), and hands Step 5(b) to the filtered sweep: it
+ * writes the staging order of
  * the query's nonzero points with the union of Step 5(a) first, the subset
  * range [0, C(|union|, D-2)) and the running minimum d0, so that the sweep
  * visits exactly the subsets of the union and returns min(d0, their V(S)).
@@ -33,13 +34,17 @@
  * iterations keeps the full subset range too (the exact count) and is
  * counted in the fallback statistic.
  *
- * Inside one node the semantics of Step 4(a) are kept while its subsets are
- * evaluated in parallel: a subset with V(S) > d0 changes nothing (its nodes
- * would be deleted by Step 4(b) before any later step reads them, and two
- * subsets of one node cannot produce the same node), so the warps compute
- * the critical set and the exact tight correction only when G(S) <= d0, and
- * thread 0 applies (iii) and (iv) in order, stopping at the first subset
- * that lowers d0.
+ * A subset is evaluated exactly (projections, comparison sort with the
+ * FP32-filtered exact comparator, the count of every cell of the line
+ * arrangement) either by one warp (WARP: rows of at most 256 points, the D-1
+ * subsets of a node in parallel) or by the whole block (longer rows, the
+ * subsets one after another).  A subset with V(S) > d0 changes nothing (its
+ * nodes would be deleted by Step 4(b) before any later step reads them, and
+ * two subsets of one node cannot produce the same node), so the critical set
+ * and the exact tight correction are computed only when G(S) <= d0, and
+ * thread 0 applies (iii) and (iv) in lexicographic order, stopping at the
+ * first subset that lowers d0 (the block form then evaluates no further
+ * subset of the node).
  */
 
 #define TD_ADIA_CAP_LOG2 11

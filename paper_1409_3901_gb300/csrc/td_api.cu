@@ -1003,7 +1003,8 @@ extern "C" int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *tic
     cudaSetDevice(ctx->device);
     int rc = pump(s); /* reaps finished batches first (frees budget) */
     if (rc != TD_OK) return rc;
-    const size_t bytes = request_bytes(d->n, d->p, d->m);
+    size_t bytes = request_bytes(d->n, d->p, d->m);
+    if (ctx->opt.algorithm == TD_ALG_ADIA) bytes += (size_t)d->m * d->n * 2; /* staging order per query */
     if (s->inflight + bytes > s->budget) return TD_ERR_BUSY;
     td_stream_req *r = new (std::nothrow) td_stream_req();
     if (!r) return TD_ERR_OOM;

@@ -38,25 +38,24 @@ __device__ void td_warp_critical(const int32_t *xi, int PSI, int nnz, uint64_t r
     td_unrank_colex<K1>(r0, nnz, c);
     for (uint64_t r = r0; r < r1; ++r) {
         if (r > r0) td_next_colex<K1>(c);
-        /* the normal: n_j = (-1)^(j + D - 1) det(F's coordinates without row j) */
+        /* the normal: n_j = (-1)^(j + D - 1) det(F's coordinates without row
+         * j), cofactor j by lane j, shared by shuffles */
+        int64_t mine = 0;
+        if (lane < D) {
+            int64_t M[4][4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o)
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    M[o][a] = (o < K1 && a < K1) ? xi[(size_t)c[a] * PSI + (o < lane ? o : o + 1)] : 0;
+            const int64_t m = td_detn<K1>(M);
+            mine = ((lane + D - 1) & 1) ? -m : m;
+        }
         int64_t n[D];
         bool nz = false;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            int64_t M[4][4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) M[a][b] = 0;
-#pragma unroll
-            for (int a = 0; a < K1; ++a) {
-                int o = 0;
-#pragma unroll
-                for (int rr = 0; rr < D; ++rr)
-                    if (rr != j) M[o++][a] = xi[(size_t)c[a] * PSI + rr];
-            }
-            const int64_t m = td_detn<K1>(M);
-            n[j] = ((j + D - 1) & 1) ? -m : m;
+            n[j] = td_shfl64(mine, j);
             nz |= n[j] != 0;
         }
         if (!nz) { /* dependent subset */

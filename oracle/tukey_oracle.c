@@ -544,7 +544,14 @@ static int64_t *centre(const int32_t *X, int64_t n, int p, const int32_t *z)
  *
  * The result is d0 as a count, Z included.  Every value d0 takes is V(S) of
  * some subset, so the result is never below the exact count T; the paper
- * reports it equal to T in all its experiments, without proof. */
+ * reports it equal to T in all its experiments, without proof.
+ *
+ * Pins: the critical points (A2) against a brute force and the paper's own
+ * condition; the count against the exact count (never below it, equal in
+ * general position).  The order of the traversal (A3-A6: exclusions, the
+ * break, deletions, the side of Step 5(a), the start point) has no value
+ * printed in the paper to pin it and leaves the count unchanged on every
+ * input tried: parity unpinned for the traversal itself. */
 
 /* Critical points (reading A2) of the projected points y (pairs, cnt of them,
  * zero pairs allowed).  crit[i] is set to 1 for the critical ones and 0

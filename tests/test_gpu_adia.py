@@ -172,3 +172,12 @@ def test_golden_w3_sample_batched(adia):
     assert adia.last_stats.adia_fallbacks == 0
     for it, o in zip(g["items"], outs):
         assert np.array_equal(o, np.array(it["T"])), (it["index"], o.tolist(), it["T"])
+
+
+def test_early_exit_leaves_the_counts(td, adia):
+    """Algorithm 3 with td_options.early_exit: the sweep of Step 5(b) stops a
+    query whose minimum reached 0, which cannot change its count."""
+    from paper_1409_3901_gb300 import workloads as W
+    d = W.w1()
+    ee = td.Context(0, algorithm=td.TD_ALG_ADIA, early_exit=True)
+    assert np.array_equal(ee.depth(d.X, d.Zq), adia.depth(d.X, d.Zq))

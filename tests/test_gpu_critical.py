@@ -84,3 +84,17 @@ def test_golden_w2_sample(crit):
     idx = np.array([0, 17, 32, 33, 50, 63])
     got = crit.depth(d.X, d.Zq[idx])
     assert np.array_equal(got, np.array(g["T"])[idx])
+
+
+def test_shards_merge_to_the_depth(td):
+    """shard_index / shard_count split the hyperplane positions of every query;
+    the minimum over the shards is the depth."""
+    rng = np.random.default_rng(47)
+    X = random_case(rng, 4, 60, 20, tie_rate=0.4)
+    Z = np.vstack([X[:3], rng.integers(-20, 21, size=(3, 4))]).astype(np.int32)
+    want = oracle.depth_many(X, Z)
+    parts = []
+    for k in range(3):
+        c = td.Context(0, algorithm=td.TD_ALG_CRITICAL, shard_index=k, shard_count=3)
+        parts.append(c.depth(X, Z).astype(np.int64))
+    assert np.array_equal(np.minimum.reduce(parts), want)

@@ -75,8 +75,10 @@ typedef struct td_stream td_stream;
 #define TD_ALG_ADIA 1 /* Algorithm 3 (Section 4): an adaptive search from the best data direction
                          (Steps 2-4), then Algorithm 1 over the subsets of the points in the
                          halfspaces of the nodes it ends with (Step 5).  Every value it takes is
-                         some V(S), so out[q] >= T; the paper reports out[q] == T in all its
-                         experiments, without proof.  Filtered mode, unsharded only. */
+                         some V(S), so out[q] >= T.  The paper reports out[q] == T in all its
+                         experiments, without proof; it is not so for every input (a query with
+                         T = 32 and out[q] = 33 is among the tests).  Filtered mode, unsharded
+                         only. */
 #define TD_ALG_CRITICAL 2 /* Proposition 1 (Section 2) with r = p-1: the minimum over the
                              hyperplanes spanned by p-1 centred points of the points strictly on
                              the smaller side, plus the open depth of the points on the hyperplane

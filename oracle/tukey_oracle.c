@@ -544,7 +544,10 @@ static int64_t *centre(const int32_t *X, int64_t n, int p, const int32_t *z)
  *
  * The result is d0 as a count, Z included.  Every value d0 takes is V(S) of
  * some subset, so the result is never below the exact count T; the paper
- * reports it equal to T in all its experiments, without proof.
+ * reports it equal to T in all its experiments, without proof.  It is not
+ * equal on every input: on request 20 of the seeded request stream (p = 4,
+ * n = 343), query 27 gives 33 where T = 32, with optimal subsets free of
+ * ties.
  *
  * Pins: the critical points (A2) against a brute force and the paper's own
  * condition; the count against the exact count (never below it, equal in

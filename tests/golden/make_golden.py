@@ -6,12 +6,13 @@ input checksum so that a test on another machine first checks that it
 regenerated the same inputs.  Queries are spread over worker processes
 (``spawn`` start method); the oracle code is the same in each.
 
-    python tests/golden/make_golden.py W1 W2 W4 W6 W3S W5S W1A W2A W7A W3SA [--procs 8]
+    python tests/golden/make_golden.py W1 W2 W4 W6 W3S W5S W1A W2A W7A W3SA W5SA [--procs 8]
 
 W3S and W5S are bounded samples of the batched and stream workloads: every
 query of the datasets (requests) whose full oracle cost is small.  W1A, W2A,
-W7A and W3SA hold the counts of Algorithm 3 (ADIA, the oracle's oracle.adia)
-on W1, W2, W7 and the first 40 datasets of W3S.
+W7A, W3SA and W5SA hold the counts of Algorithm 3 (ADIA, the oracle's
+oracle.adia) on W1, W2, W7, the first 40 datasets of W3S and the first 30
+requests of W5S.
 """
 import argparse
 import json
@@ -83,6 +84,15 @@ def main():
                                   "m": d.m, "T": _run(pool, d.X, d.Zq, _one_adia)})
                 out = {"workload": "W3", "algorithm": "Algorithm 3 (ADIA)",
                        "sample": "the first 40 datasets of W3S", "items": items}
+            elif name == "W5SA":
+                base = json.load(open(os.path.join(HERE, "W5S.json")))
+                items = []
+                for it in base["items"][:30]:
+                    d = W.w5_request(4, it["index"])
+                    items.append({"index": it["index"], "checksum": d.checksum(), "n": d.n, "p": d.p,
+                                  "m": d.m, "T": _run(pool, d.X, d.Zq, _one_adia)})
+                out = {"workload": "W5", "algorithm": "Algorithm 3 (ADIA)",
+                       "sample": "the first 30 requests of W5S", "items": items}
             elif name == "W7A":
                 items = []
                 for i, d in enumerate(W.w7()):

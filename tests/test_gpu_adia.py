@@ -181,3 +181,24 @@ def test_early_exit_leaves_the_counts(td, adia):
     d = W.w1()
     ee = td.Context(0, algorithm=td.TD_ALG_ADIA, early_exit=True)
     assert np.array_equal(ee.depth(d.X, d.Zq), adia.depth(d.X, d.Zq))
+
+
+def test_golden_w5_sample_stream(td):
+    """30 requests of the stream workload W5 (p from 3 to 6, uniform integer
+    data) through td_stream_*, against the stored oracle counts.  One of these
+    queries (request 20, query 27) is a case where Algorithm 3 returns 33 and
+    the exact count is 32."""
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W5SA")
+    c = td.Context(0, algorithm=td.TD_ALG_ADIA)
+    s = c.stream(1 << 30)
+    pend = []
+    for it in g["items"]:
+        d = W.w5_request(4, it["index"])
+        assert d.checksum() == it["checksum"]
+        t = s.submit(d.X, d.Zq)
+        assert t is not None
+        pend.append((it, t))
+    for it, t in pend:
+        assert np.array_equal(s.wait(t), np.array(it["T"])), it["index"]
+    s.close()

@@ -180,3 +180,18 @@ def test_adia_search_counters():
     assert 4 - 2 <= st["union_points"] <= 120
     assert st["step5_subsets"] == st["union_points"] * (st["union_points"] - 1) // 2
     assert A == oracle.depth(X, z)
+
+
+def test_adia_is_an_upper_bound_not_the_depth():
+    """A query of the seeded request stream where Algorithm 3 stops above the
+    exact count (33 against 32) although its optimal subsets are free of
+    ties: the paper's observation that Algorithm 3 finds the depth does not
+    hold for every input."""
+    from paper_1409_3901_gb300 import workloads as W
+    d = W.w5_request(4, 20)
+    z = d.Zq[27]
+    assert d.n == 343 and d.p == 4
+    A, st = oracle.adia(d.X, z)
+    assert st["algorithm1"] == 0
+    assert oracle.depth(d.X, z) == 32
+    assert A == 33

@@ -84,10 +84,10 @@ typedef struct td_stream td_stream;
                              the smaller side, plus the open depth of the points on the hyperplane
                              inside it: the exact count T by a second route, O(n^(p-1)) normals
                              of O(n) work each, one launch per query (a cross-check of
-                             Algorithm 1).  Data sets with p <= 5 and p! M^p < 2^62 for the
-                             largest centred coordinate M (TD_ERR_INVALID / TD_ERR_RANGE
-                             otherwise); td_options.mode is ignored; not served by the stream
-                             API (td_stream_create returns TD_ERR_INVALID). */
+                             Algorithm 1).  p! M^p < 2^62 for the largest centred coordinate
+                             M, and n <= 8000 at p = 6 (TD_ERR_RANGE otherwise); td_options.mode is ignored; not
+                             served by the stream API (td_stream_create returns
+                             TD_ERR_INVALID). */
 
 /* Execution forms of the same computation (identical results). */
 #define TD_MODE_FILTERED 0    /* persistent launch over (dataset, query, subset-tile) work,

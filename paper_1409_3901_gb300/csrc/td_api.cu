@@ -31,6 +31,7 @@
 size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps);
 size_t td_plain_smem(int nmax, int pmax, int warps);
 int64_t td_scratch_per_warp(int nmax);
+int64_t td_scratch_per_warp_critical(int nmax);
 cudaError_t td_launch_setup(const TdLaunch &L, cudaStream_t s);
 cudaError_t td_launch_tiles(const TdLaunch &L, cudaStream_t s);
 cudaError_t td_launch_filtered(int D, const TdLaunch &L, int grid, size_t smem, cudaStream_t s);
@@ -224,17 +225,22 @@ bool range_ok(const td_dataset &d)
     return true;
 }
 
-/* Proposition 1 with r = p-1 (TD_ALG_CRITICAL): p <= 5 and p! M^p < 2^62 for
+/* Proposition 1 with r = p-1 (TD_ALG_CRITICAL): p! M^p < 2^62 for
  * the largest centred coordinate M, so that every normal and every n.x is
  * exact in int64. */
 bool critical_range_ok(int p, int64_t M)
 {
-    if (p > 5) return false;
+    if (p > 6) return false;
     long double v = 1.0L;
     for (int i = 2; i <= p; ++i) v *= i;
     for (int i = 0; i < p; ++i) v *= (long double)M;
     return v < 4611686018427387904.0L; /* 2^62 */
 }
+
+/* The count of (p-1)-subsets, C(n, p-1), is formed on the device in 64 bits
+ * with a product of p - 1 factors before the last division; at p = 6 that
+ * product stays below 2^64 for n <= 8000. */
+bool critical_count_ok(int p, int64_t n) { return p < 6 || n <= 8000; }
 
 int64_t max_centred(const td_dataset &d)
 {
@@ -426,6 +432,7 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
          * back each query's effective dimension */
         TdLaunch L = Lf;
         L.warps = td_critical_threads() / 32;
+        L.scratch_per_warp = td_scratch_per_warp_critical(P.nmax);
         const size_t smem = td_critical_smem(P.nmax, P.pmax);
         TDCK(td_launch_setup(L, s));
         ++nl;
@@ -435,7 +442,7 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
         if (ev_a) TDCK(cudaEventRecord(ev_a, s));
         for (int q = 0; q < P.nq; ++q) {
             const int D = hq[q].d;
-            if (hq[q].k < 0 || hq[q].hi <= hq[q].lo || D < 2 || D > 5) continue;
+            if (hq[q].k < 0 || hq[q].hi <= hq[q].lo || D < 2 || D > 6) continue;
             const int occ = td_critical_occupancy(D, smem);
             if (occ < 1) return TD_ERR_INVALID;
             TDCK(td_launch_critical(D, L, q, ctx->sms * occ, smem, s));
@@ -567,7 +574,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     }
     if (ctx->opt.algorithm == TD_ALG_CRITICAL)
         for (int s2 = 0; s2 < k; ++s2) {
-            if (sets[s2].p > 5) return TD_ERR_INVALID;
+            if (!critical_count_ok(sets[s2].p, sets[s2].n)) return TD_ERR_RANGE;
             if (!devptr && !critical_range_ok(sets[s2].p, max_centred(sets[s2]))) return TD_ERR_RANGE;
         }
     if (st) memset(st, 0, sizeof(*st));
@@ -582,11 +589,13 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     if (o.algorithm == TD_ALG_CRITICAL) {
         const size_t smem = td_critical_smem(P.nmax, P.pmax);
         int occ = 0;
-        for (int D = 2; D <= 5; ++D) occ = std::max(occ, td_critical_occupancy(D, smem));
+        for (int D = 2; D <= 6; ++D) occ = std::max(occ, td_critical_occupancy(D, smem));
         if (occ < 1) return TD_ERR_INVALID;
         grid = ctx->sms * occ;
         warps_total = grid * (td_critical_threads() / 32);
         TDCK(alloc_work(ctx->w, P, warps_total, true));
+        /* the critical kernel lays its per-warp scratch out for 2 nmax points */
+        TDCK(grow(ctx->w.scratch, (size_t)warps_total * (size_t)td_scratch_per_warp_critical(P.nmax)));
     } else if (o.mode == TD_MODE_PLAIN_EXACT) {
         size_t smem = td_plain_smem(P.nmax, P.pmax, kWarpsPlain);
         int occ = 0;

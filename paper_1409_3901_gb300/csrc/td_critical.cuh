@@ -20,9 +20,9 @@
  *
  * Exact int64 arithmetic: the caller guarantees d! max|x|^d < 2^62, so the
  * cofactors ((d-1)! max|x|^(d-1)) and every n_F . x fit.  m_F is computed by
- * the tight-set recursion (td_open_depth<d-1>, d - 1 <= 4) on the points of H
- * in the d - 1 coordinates other than one where n_F is nonzero (injective on
- * H).  d <= 5.
+ * the tight-set recursion (td_open_depth<d-1>, or td_open_depth_s<5> at
+ * d = 6) on the points of H in the d - 1 coordinates other than one where
+ * n_F is nonzero (injective on H).
  */
 
 #define TD_CRIT_THREADS 256
@@ -42,11 +42,12 @@ __device__ void td_warp_critical(const int32_t *xi, int PSI, int nnz, uint64_t r
          * j), cofactor j by lane j, shared by shuffles */
         int64_t mine = 0;
         if (lane < D) {
-            int64_t M[4][4];
+            constexpr int MS = K1 > 4 ? K1 : 4;
+            int64_t M[MS][MS];
 #pragma unroll
-            for (int o = 0; o < 4; ++o)
+            for (int o = 0; o < MS; ++o)
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < MS; ++a)
                     M[o][a] = (o < K1 && a < K1) ? xi[(size_t)c[a] * PSI + (o < lane ? o : o + 1)] : 0;
             const int64_t m = td_detn<K1>(M);
             mine = ((lane + D - 1) & 1) ? -m : m;
@@ -96,16 +97,18 @@ __device__ void td_warp_critical(const int32_t *xi, int PSI, int nnz, uint64_t r
                 const unsigned bg = __ballot_sync(TD_FULL, g);
                 if (g) {
                     const int slot = t + __popc(bg & below);
+                    constexpr int CS = K1 > 4 ? 8 : 4; /* see td_k_critical's scratch */
                     int o = 0;
 #pragma unroll
                     for (int k = 0; k < D; ++k)
-                        if (k != jd) scr.c0[4 * slot + o++] = xi[(size_t)i * PSI + k];
+                        if (k != jd) scr.c0[CS * slot + o++] = xi[(size_t)i * PSI + k];
                 }
                 t += __popc(bg);
             }
             __syncwarp();
             if (lane == 0) st.tight++;
-            V += td_open_depth<K1>(scr.c0, t, scr, lane, 0);
+            if constexpr (K1 == 5) V += td_open_depth_s<5, 8>(scr.c0, t, scr, lane);
+            else V += td_open_depth<K1>(scr.c0, t, scr, lane, 0);
         }
         best = min(best, V);
     }
@@ -128,7 +131,9 @@ __global__ void __launch_bounds__(TD_CRIT_THREADS, 1) td_k_critical(TdLaunch L, 
     uint16_t *orig = reinterpret_cast<uint16_t *>(smem + (((size_t)L.nmax * PSI * 4 + 15) & ~(size_t)15));
     td_adia_stage(L, q, xi, PSI, orig, s_tmp);
     const int gw = blockIdx.x * nw + w;
-    const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, nmaxp);
+    /* scratch laid out for 2 nmaxp points: c0 then holds 8 coordinates for
+     * each of nmaxp points (the 5-D hyperplane sets at d = 6) */
+    const TdScratch scr = td_scratch_at(L.scratch + (size_t)gw * L.scratch_per_warp, 2 * nmaxp);
     TdWarpStats st = { 0, 0, 0, 0, 0, 0, 0 };
     const int64_t ts = (int64_t)(L.spw > 0 ? L.spw : 16) * nw;
     const int64_t ntiles = (Q.hi - Q.lo + ts - 1) / ts;

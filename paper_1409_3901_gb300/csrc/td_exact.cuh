@@ -71,6 +71,7 @@ __host__ __device__ __forceinline__ uint64_t td_binom(int64_t n, int k)
     case 2: return u * (u - 1) / 2;
     case 3: return u * (u - 1) / 2 * (u - 2) / 3;
     case 4: return u * (u - 1) / 2 * (u - 2) / 3 * (u - 3) / 4;
+    case 5: return u * (u - 1) / 2 * (u - 2) / 3 * (u - 3) / 4 * (u - 4) / 5;
     default: return 0;
     }
 }

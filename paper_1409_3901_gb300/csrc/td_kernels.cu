@@ -416,9 +416,10 @@ __device__ int td_sweep_list(uint16_t *idx, int cnt, const int64_t *H, int lane)
 /* open depth of a small full-rank point set (the tight-set path)         */
 /* ====================================================================== */
 
-/* K x K determinant by cofactor expansion (K <= 4, small entries). */
-template <int N>
-__device__ int64_t td_detn(const int64_t (&m)[4][4])
+/* N x N determinant (top-left block of an S x S array) by cofactor expansion
+ * (N <= 5, small entries). */
+template <int N, int S>
+__device__ int64_t td_detn(const int64_t (&m)[S][S])
 {
     if constexpr (N == 1) {
         return m[0][0];
@@ -426,7 +427,7 @@ __device__ int64_t td_detn(const int64_t (&m)[4][4])
         int64_t acc = 0;
 #pragma unroll
         for (int c = 0; c < N; ++c) {
-            int64_t sub[4][4];
+            int64_t sub[S][S];
 #pragma unroll
             for (int r = 1; r < N; ++r) {
                 int o = 0;
@@ -443,6 +444,8 @@ __device__ int64_t td_detn(const int64_t (&m)[4][4])
 
 template <int KK>
 __device__ int td_open_depth(const int32_t *c, int t, const TdScratch &scr, int lane, int level);
+template <int KK, int CS>
+__device__ int td_open_depth_s(const int32_t *c, int t, const TdScratch &scr, int lane);
 
 /* 2-D open depth of t nonzero integer points (coordinates 0,1 of c). */
 __device__ int td_open_depth2(const int32_t *c, int t, int64_t *Y, uint16_t *I, int lane)
@@ -462,7 +465,7 @@ __device__ int td_open_depth2(const int32_t *c, int t, int64_t *Y, uint16_t *I, 
  * subset s (DD-2 points of c); writes nonzero normalised ones to Y/I, and the
  * tight ones' intrinsic coordinates to ct (if DD-2 >= 2) or their sign counts.
  * Returns false if the subset is dependent. */
-template <int DD>
+template <int DD, int CS = 4>
 __device__ bool td_project_small(const int32_t *c, int t, const int *sub, int64_t *Y, uint16_t *I,
                                  int32_t *ct, int &nz, int &nt, int &pos, int &neg, int lane)
 {
@@ -471,7 +474,7 @@ __device__ bool td_project_small(const int32_t *c, int t, const int *sub, int64_
 #pragma unroll
     for (int j = 0; j < K; ++j)
 #pragma unroll
-        for (int r = 0; r < DD; ++r) s[j][r] = c[4 * sub[j] + r];
+        for (int r = 0; r < DD; ++r) s[j][r] = c[CS * sub[j] + r];
     TdBasis<DD> B;
     if (!td_make_basis<DD>(s, B)) return false;
     int *cnt = (int *)nullptr;
@@ -487,7 +490,7 @@ __device__ bool td_project_small(const int32_t *c, int t, const int *sub, int64_
         if (valid) {
 #pragma unroll
             for (int r = 0; r < DD; ++r) {
-                int64_t x = c[4 * i + r];
+                int64_t x = c[CS * i + r];
                 y1 += B.qa[r] * x;
                 y2 += B.qb[r] * x;
             }
@@ -506,13 +509,13 @@ __device__ bool td_project_small(const int32_t *c, int t, const int *sub, int64_
         }
         if (tight) {
             if (K == 1) {
-                int32_t v = c[4 * i + B.rows[0]];
+                int32_t v = c[CS * i + B.rows[0]];
                 pos += v > 0;
                 neg += v < 0;
             } else {
                 int slot = base_t + __popc(bt & below);
 #pragma unroll
-                for (int r = 0; r < K; ++r) ct[4 * slot + r] = c[4 * i + B.rows[r]];
+                for (int r = 0; r < K; ++r) ct[4 * slot + r] = c[CS * i + B.rows[r]];
             }
         }
         base_nz += __popc(bn);
@@ -566,6 +569,29 @@ __device__ int td_open_depth(const int32_t *c, int t, const TdScratch &scr, int 
             }
         return best;
     }
+}
+
+/* Open depth of t nonzero points in 5 dimensions with coordinates at stride
+ * CS in c (the hyperplanes of the critical-direction form at d = 6): the same
+ * subset method with subsets of three points, whose inner tight sets are
+ * 3-D (td_open_depth<3>). */
+template <int KK, int CS>
+__device__ int td_open_depth_s(const int32_t *c, int t, const TdScratch &scr, int lane)
+{
+    static_assert(KK == 5, "five dimensions only");
+    int best = INT_MAX;
+    for (int s2 = 2; s2 < t; ++s2)
+        for (int s1 = 1; s1 < s2; ++s1)
+            for (int s0 = 0; s0 < s1; ++s0) {
+                int sub[3] = { s0, s1, s2 };
+                int nz, nt, pos, neg;
+                if (!td_project_small<5, CS>(c, t, sub, scr.y0, scr.i0, scr.c1, nz, nt, pos, neg, lane)) continue;
+                const int G = td_sweep_list(scr.i0, nz, scr.y0, lane);
+                if (G >= best) continue;
+                const int m = nt > 3 ? td_open_depth<3>(scr.c1, nt, scr, lane, 1) : 0;
+                best = min(best, G + m);
+            }
+    return best;
 }
 
 /* m_S for a subset whose span holds t > K data points: the tight points'
@@ -2502,6 +2528,9 @@ size_t td_plain_smem(int nmax, int pmax, int warps)
 
 int64_t td_scratch_per_warp(int nmax) { return (td_scratch_bytes(td_pow2_at_least(nmax)) + 255) & ~(int64_t)255; }
 
+/* the critical-direction kernel lays its scratch out for 2 td_pow2_at_least(nmax) points */
+int64_t td_scratch_per_warp_critical(int nmax) { return td_scratch_per_warp(2 * td_pow2_at_least(nmax)); }
+
 cudaError_t td_launch_setup(const TdLaunch &L, cudaStream_t s)
 {
     td_k_setup<<<L.nq, 256, 0, s>>>(L);
@@ -2612,7 +2641,7 @@ cudaError_t td_launch_adia(int D, const TdLaunch &L, int grid, size_t smem, cuda
 
 int64_t td_adia_ws_entries() { return TD_ADIA_CAP; }
 
-/* critical-direction kernel (d = 2..5): shared memory, occupancy, launch */
+/* critical-direction kernel (d = 2..6): shared memory, occupancy, launch */
 size_t td_critical_smem(int nmax, int pmax)
 {
     const int PSI = pmax <= 4 ? 4 : 8;
@@ -2625,7 +2654,8 @@ static td_kfn_plain td_critical_fn(int D)
     case 2: return td_k_critical<2>;
     case 3: return td_k_critical<3>;
     case 4: return td_k_critical<4>;
-    default: return td_k_critical<5>;
+    case 5: return td_k_critical<5>;
+    default: return td_k_critical<6>;
     }
 }
 

@@ -1,7 +1,8 @@
 """GPU parity of the critical-direction form (Proposition 1 with r = p-1,
-td_options.algorithm = TD_ALG_CRITICAL) against the oracle, and against
-Algorithm 1 on the GPU at full benchmark sizes: two routes to the exact count
-that share no arithmetic beyond the tight-set recursion.  Bit-exact."""
+td_options.algorithm = TD_ALG_CRITICAL, p <= 6) against the oracle, and
+against Algorithm 1 on the GPU at full benchmark sizes: two routes to the
+exact count that share no arithmetic beyond the tight-set recursion.
+Bit-exact."""
 import numpy as np
 import pytest
 
@@ -22,11 +23,11 @@ def crit(td):
     return td.Context(0, algorithm=td.TD_ALG_CRITICAL)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
 def test_small_tie_heavy(crit, p):
     rng = np.random.default_rng(700 + p)
     for trial in range(6):
-        n = int(rng.integers(p + 1, {1: 60, 2: 70, 3: 60, 4: 40, 5: 25}[p]))
+        n = int(rng.integers(p + 1, {1: 60, 2: 70, 3: 60, 4: 40, 5: 25, 6: 16}[p]))
         lim = int(rng.choice([2, 3, 10, 127]))
         X = random_case(rng, p, n, lim, tie_rate=0.5)
         Z = np.vstack([X[rng.integers(0, n, size=3)], rng.integers(-lim, lim + 1, size=(3, p))]).astype(np.int32)
@@ -38,8 +39,8 @@ def test_hyperplanes_with_many_points(crit):
     """Small grids: many hyperplanes through z hold more than p-1 points, so
     the open depth m_F inside the hyperplane is needed."""
     rng = np.random.default_rng(41)
-    for p in (3, 4, 5):
-        X = rng.integers(-2, 3, size=({3: 40, 4: 30, 5: 20}[p], p)).astype(np.int32)
+    for p in (3, 4, 5, 6):
+        X = rng.integers(-2, 3, size=({3: 40, 4: 30, 5: 20, 6: 14}[p], p)).astype(np.int32)
         Z = np.vstack([X[:3], np.zeros((1, p), np.int32)]).astype(np.int32)
         got = crit.depth(X, Z)
         assert np.array_equal(got, oracle.depth_many(X, Z))
@@ -55,12 +56,15 @@ def test_rank_deficient(crit):
 
 
 def test_limits(td, crit):
-    X = np.zeros((8, 6), np.int32)
-    with pytest.raises(td.TdError):
-        crit.depth(X, X[:1])                     # p = 6 is not served
     X = np.array([[30000, 1, 2, 3], [1, 2, 3, 4], [5, 6, 7, -8], [1, 0, 0, 0], [0, 1, 0, 0]], np.int32)
     with pytest.raises(td.TdError):
         crit.depth(X, np.zeros((1, 4), np.int32))  # 4! * 30000^4 > 2^62
+    X = np.eye(6, dtype=np.int32) * 500
+    with pytest.raises(td.TdError):
+        crit.depth(X, np.zeros((1, 6), np.int32))  # 6! * 500^6 > 2^62
+    X = np.random.default_rng(3).integers(-2, 3, size=(8001, 6)).astype(np.int32)
+    with pytest.raises(td.TdError):
+        crit.depth(X, np.zeros((1, 6), np.int32))  # C(n, 5) past 64 bits: n <= 8000 at p = 6
 
 
 @pytest.mark.parametrize("name,count", [("W1", 16), ("W4", 64)])
@@ -98,3 +102,15 @@ def test_shards_merge_to_the_depth(td):
         c = td.Context(0, algorithm=td.TD_ALG_CRITICAL, shard_index=k, shard_count=3)
         parts.append(c.depth(X, Z).astype(np.int64))
     assert np.array_equal(np.minimum.reduce(parts), want)
+
+
+def test_golden_w5_sample_p6(crit):
+    """The p = 6 requests of the stored W5 sample (uniform integer data)."""
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W5S")
+    items = [it for it in g["items"] if it["p"] == 6][:6]
+    assert items
+    for it in items:
+        d = W.w5_request(4, it["index"])
+        assert d.checksum() == it["checksum"]
+        assert np.array_equal(crit.depth(d.X, d.Zq), np.array(it["T"])), it["index"]

@@ -202,3 +202,15 @@ def test_golden_w5_sample_stream(td):
     for it, t in pend:
         assert np.array_equal(s.wait(t), np.array(it["T"])), it["index"]
     s.close()
+
+
+@pytest.mark.parametrize("req,query,T", [(20, 27, 32), (376, 3, 51)])
+def test_upper_bound_cases(adia, rcom, req, query, T):
+    """The two queries of the request stream where the oracle's Algorithm 3
+    returns T + 1: the device search takes the same path, and Algorithm 1
+    gives T."""
+    from paper_1409_3901_gb300 import workloads as W
+    d = W.w5_request(4, req)
+    Z = d.Zq[query:query + 1]
+    assert np.array_equal(rcom.depth(d.X, Z), [T])
+    assert np.array_equal(adia.depth(d.X, Z), [T + 1])

@@ -182,16 +182,17 @@ def test_adia_search_counters():
     assert A == oracle.depth(X, z)
 
 
-def test_adia_is_an_upper_bound_not_the_depth():
-    """A query of the seeded request stream where Algorithm 3 stops above the
-    exact count (33 against 32) although its optimal subsets are free of
-    ties: the paper's observation that Algorithm 3 finds the depth does not
-    hold for every input."""
+@pytest.mark.parametrize("req,query,n,T", [(20, 27, 343, 32), (376, 3, 426, 51)])
+def test_adia_is_an_upper_bound_not_the_depth(req, query, n, T):
+    """Queries of the seeded request stream where Algorithm 3 stops one above
+    the exact count; in the first the optimal subsets are free of ties: the
+    paper's observation that Algorithm 3 finds the depth does not hold for
+    every input."""
     from paper_1409_3901_gb300 import workloads as W
-    d = W.w5_request(4, 20)
-    z = d.Zq[27]
-    assert d.n == 343 and d.p == 4
+    d = W.w5_request(4, req)
+    z = d.Zq[query]
+    assert d.n == n and d.p == 4
     A, st = oracle.adia(d.X, z)
     assert st["algorithm1"] == 0
-    assert oracle.depth(d.X, z) == 32
-    assert A == 33
+    assert oracle.depth(d.X, z) == T
+    assert A == T + 1

@@ -1073,6 +1073,13 @@ struct TdWarpSmem {
  * only the few sweeps that go past the coarse bound build. */
 #define TD_COARSE_WORDS (33 * 32)
 
+/* Histogram words (coarse and fine): the high half counts every event of the
+ * bucket, the low half its +1 events (points of orientation -), so that a
+ * point adds 0x10000 plus the sign bit of its y2.  Both halves stay below
+ * 2^15 (at most nnz events), in single words and in the sums of pass 1. */
+__device__ __forceinline__ int td_ev_plus(uint32_t w) { return (int)(w & 0xFFFFu); }
+__device__ __forceinline__ int td_ev_minus(uint32_t w) { return (int)(w >> 16) - (int)(w & 0xFFFFu); }
+
 /* q64 (16 int64: qa, qb) at 0, q32 (16 int) at 128, fab2 (16 packed pairs)
  * at 192, meta (8 int) at 320 */
 #define TD_WARP_META_BYTES 352
@@ -1210,7 +1217,7 @@ __device__ __forceinline__ int td_exact_pass(const float *xs, int npc, const TdW
         }
         if (act) {
             W.bid[i] = (uint16_t)(zero ? TD_SENT : (unsigned)j);
-            if (!zero) td_reds_add(hq + 4u * (unsigned)j, plus ? 0x10000u : 1u);
+            if (!zero) td_reds_add(hq + 4u * (unsigned)j, plus ? 0x10000u : 0x10001u);
             t += zero;
         }
     }
@@ -1501,7 +1508,7 @@ __device__ __forceinline__ TdPairCoef<D> td_pair_coef(const td_f2x (&FA)[D], con
 /* The FP32 buckets of the two points of one staged pair (planes pl[]), see
  * the certification argument below: floor(key B/2) when the interval
  * key +- delta lies in one bucket, else B (uncertain).  inc is the packed
- * event of the point: 1 (+1 event, orientation -) or 1 << 16 (-1 event,
+ * event of the point: 0x10001 (+1 event, orientation -) or 0x10000 (-1 event,
  * orientation +).
  *
  * The key is carried negated, kn = y1 rr - 1 = -key with rr = sign(y2) /
@@ -1548,8 +1555,8 @@ __device__ __forceinline__ void td_pair_slots(const float4 (&pl)[(D + 1) / 2], c
     const uint32_t blp = (uint32_t)__float_as_int(flp) + C.moff, blq = (uint32_t)__float_as_int(flq) + C.moff;
     sp = ((__float_as_int(flp) == __float_as_int(fhp)) & (blp < (uint32_t)C.B)) ? (int)blp : C.B;
     sq = ((__float_as_int(flq) == __float_as_int(fhq)) & (blq < (uint32_t)C.B)) ? (int)blq : C.B;
-    ip = (uint32_t)(0x10000 + (__float_as_int(y2p) >> 31) * 0xFFFF);
-    iq = (uint32_t)(0x10000 + (__float_as_int(y2q) >> 31) * 0xFFFF);
+    ip = 0x10000u + ((uint32_t)__float_as_int(y2p) >> 31);
+    iq = 0x10000u + ((uint32_t)__float_as_int(y2q) >> 31);
 }
 
 /* The coarse rows of the two points of one staged pair: floor(key * 16), the
@@ -1592,8 +1599,8 @@ __device__ __forceinline__ void td_pair_rows(const float4 (&pl)[(D + 1) / 2], co
     const uint32_t blq = min((uint32_t)__float_as_int(flq) + C.moffc, 32u);
     rp = __float_as_int(flp) == __float_as_int(fhp) ? (int)blp : 32;
     rq = __float_as_int(flq) == __float_as_int(fhq) ? (int)blq : 32;
-    ip = (uint32_t)(0x10000 + (__float_as_int(y2p) >> 31) * 0xFFFF);
-    iq = (uint32_t)(0x10000 + (__float_as_int(y2q) >> 31) * 0xFFFF);
+    ip = 0x10000u + ((uint32_t)__float_as_int(y2p) >> 31);
+    iq = 0x10000u + ((uint32_t)__float_as_int(y2q) >> 31);
 }
 
 /* Rescan of a sweep's points, for the few sweeps whose bound over the
@@ -1669,7 +1676,8 @@ template <int D>
 __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int nnz,
                                                  const td_f2x (&FA)[D], const td_f2x (&FB)[D], float Ea, float Eb,
                                                  bool narrow, const TdWarpSmem &W, int blog2, int lane, int best,
-                                                 uint64_t &n_exact, uint32_t &n_resolved, int &t_out, int &nzy_out)
+                                                 bool &clean, uint64_t &n_exact, uint32_t &n_resolved, int &t_out,
+                                                 int &nzy_out)
 {
     constexpr int NPL = (D + 1) / 2;        /* planes of the pair layout */
     const int B = 1 << blog2;               /* blog2 >= 7: at least 4 buckets per lane */
@@ -1698,14 +1706,16 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
      * the fine test. */
     constexpr int UNR = TD_ROUND / 32;
     constexpr int NPR = UNR / 2; /* pairs per lane and round */
-    /* the coarse histogram starts at zero (its storage holds the previous
-     * sweep's fine histogram, bucket ids or lists when that one went past
-     * the coarse bound; those stay readable until the sweep's caller is done) */
-    {
+    /* the coarse histogram starts at zero: pass 1 of the previous sweep
+     * left it so (clean), unless that sweep went past the coarse bound and
+     * built its fine histogram in the same storage.  At D = 6 the flag costs
+     * spills, and every sweep clears. */
+    constexpr bool KEEP_CLEAN = D <= 5;
+    if (!clean) {
         uint4 *z4 = reinterpret_cast<uint4 *>(W.hist);
         for (int j = lane; j < (TD_COARSE_WORDS >> 2); j += 32) z4[j] = make_uint4(0u, 0u, 0u, 0u);
-        __syncwarp();
     }
+    __syncwarp();
     auto round = [&](int i0) {
         int slot[UNR];
         uint32_t inc[UNR];
@@ -1727,7 +1737,8 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     const uint32_t hU = W.hist[32 * 32 + lane];
     /* uncertain points: the padding points of the last round are zeros,
      * whose key is NaN, so each of them added one event to row 32 too */
-    const int nu = td_wsum((int)(hU & 0xFFFFu) + (int)(hU >> 16)) - (((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz);
+    if (KEEP_CLEAN) W.hist[32 * 32 + lane] = 0u; /* left zero for the next sweep (see pass 1) */
+    const int nu = td_wsum((int)(hU >> 16)) - (((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz);
     n_exact += (uint64_t)nu;
 
     /* Pass 1: per-lane totals of the +1/-1 events, i.e. a histogram of 32
@@ -1741,7 +1752,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     const int per = B >> 5;
     int Pl, lol, hil;
     auto pass1 = [&](uint32_t acc, int nz) -> int {
-        const int cpl = (int)(acc & 0xFFFFu), cml = (int)(acc >> 16);
+        const int cpl = td_ev_plus(acc), cml = td_ev_minus(acc);
         const int A = td_wsum(cml); /* orientation + points: one -1 event each */
         const int netl = cpl - cml;
         const int excl = td_wscan_incl(netl, lane) - netl;
@@ -1752,14 +1763,17 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     };
     uint32_t acc = 0;
     {
-        const uint4 *row = reinterpret_cast<const uint4 *>(W.hist) + lane * 8;
+        /* lane l reads row l (and leaves it zero) */
+        uint4 *row = reinterpret_cast<uint4 *>(W.hist) + lane * 8;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int j = (k + lane) & 7;
             const uint4 v = row[j];
             acc += v.x + v.y + v.z + v.w;
+            if (KEEP_CLEAN) row[j] = make_uint4(0u, 0u, 0u, 0u);
         }
     }
+    clean = KEEP_CLEAN;
     /* First without the uncertain points (not yet in any histogram): for
      * every direction the walk value w over all nonzero points is w_c + w_u
      * with 0 <= w_u <= (uncertain nonzero points), so min(w, nzy - w) >=
@@ -1770,6 +1784,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     int G = pass1(acc, nnz - nu);
     int t = 0;
     if (G < best) {
+        clean = false;
         /* the fine histogram shares the coarse one's storage: clear it */
         uint4 *z4 = reinterpret_cast<uint4 *>(W.hist);
         const int nclr4 = max(B + 4, TD_COARSE_WORDS) >> 2;
@@ -1810,7 +1825,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
                     const int tt = base + lane;
                     const bool v = tt < per;
                     const uint32_t w = v ? W.hist[td_phys(L * per + tt, lp, chm)] : 0u;
-                    const int cp = (int)(w & 0xFFFFu), cm = (int)(w >> 16);
+                    const int cp = td_ev_plus(w), cm = td_ev_minus(w);
                     const int nt = cp - cm;
                     const int inc = td_wscan_incl(nt, lane);
                     const int Pb = carry + inc - nt;
@@ -1834,7 +1849,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
                 const uint32_t w4[4] = { v.x, v.y, v.z, v.w };
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int cp = (int)(w4[k] & 0xFFFFu), cm = (int)(w4[k] >> 16);
+                    const int cp = td_ev_plus(w4[k]), cm = td_ev_minus(w4[k]);
                     mn = min(mn, P);
                     mx = max(mx, P);
                     if (cp && cm) {
@@ -1878,7 +1893,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
                         const bool v = tt < per;
                         const int ph = td_phys(L * per + tt, lp, chm);
                         const uint32_t w = v ? W.hist[ph] : 0u;
-                        const int cp = (int)(w & 0xFFFFu), cm = (int)(w >> 16);
+                        const int cp = td_ev_plus(w), cm = td_ev_minus(w);
                         const int nt = cp - cm;
                         const int inc = td_wscan_incl(nt, lane);
                         const int Pb = carry + inc - nt;
@@ -1893,7 +1908,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
                     uint32_t w4[4] = { v.x, v.y, v.z, v.w };
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const int cp = (int)(w4[k] & 0xFFFFu), cm = (int)(w4[k] >> 16);
+                        const int cp = td_ev_plus(w4[k]), cm = td_ev_minus(w4[k]);
                         if (cand(P, cp, cm)) w4[k] = 0x80000000u | (uint32_t)P;
                         P += cp - cm;
                     }
@@ -2063,6 +2078,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     for (int r = 0; r < D; ++r) mxf[r] = (float)Q.mx[r]; /* < 2^22: exact */
     uint32_t n_dep = 0, n_tight = 0, n_res = 0;
     uint64_t n_exact = 0;
+    bool clean = false; /* the coarse histogram storage is zero */
     /* forward error bound of the FP32 projection: the fma chain adds at most
      * D u sum |q_i x_i|, the rounded coefficients (at most 2u each, see
      * td_i64_to_f32) 2u more; taken as (D + 3) u, applied to A = sum |q_i|
@@ -2112,8 +2128,8 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
         /* exact bounds below 2^31 (the binary32 sums are within (D + 2) u) */
         const bool narrow = fmaxf(Aa, Ab) < 2145386496.0f; /* 2^31 (1 - 2^-10) */
         int t, nzy;
-        const int G = td_sweep_filtered<D>(xs, npc, nnz, FA, FB, Ea, Eb, narrow, W, blog2, lane, best, n_exact,
-                                           n_res, t, nzy);
+        const int G = td_sweep_filtered<D>(xs, npc, nnz, FA, FB, Ea, Eb, narrow, W, blog2, lane, best, clean,
+                                           n_exact, n_res, t, nzy);
         int V = G;
         if (t > K && G < best) {
             ++n_tight;

@@ -85,7 +85,7 @@ typedef struct td_stream td_stream;
                              inside it: the exact count T by a second route, O(n^(p-1)) normals
                              of O(n) work each, one launch per query (a cross-check of
                              Algorithm 1).  p! M^p < 2^62 for the largest centred coordinate
-                             M, and n <= 8000 at p = 6 (TD_ERR_RANGE otherwise); td_options.mode is ignored; not
+                             M (TD_ERR_RANGE otherwise); td_options.mode is ignored; not
                              served by the stream API (td_stream_create returns
                              TD_ERR_INVALID). */
 

@@ -227,7 +227,10 @@ bool range_ok(const td_dataset &d)
 
 /* Proposition 1 with r = p-1 (TD_ALG_CRITICAL): p! M^p < 2^62 for
  * the largest centred coordinate M, so that every normal and every n.x is
- * exact in int64. */
+ * exact in int64.  The subset count C(n, 5) at p = 6 is formed on the device
+ * as a product of five factors before the last division, below 2^64 for
+ * n <= TD_MAX_N. */
+static_assert(TD_MAX_N <= 8000, "C(n, 5) in 64 bits");
 bool critical_range_ok(int p, int64_t M)
 {
     if (p > 6) return false;
@@ -236,11 +239,6 @@ bool critical_range_ok(int p, int64_t M)
     for (int i = 0; i < p; ++i) v *= (long double)M;
     return v < 4611686018427387904.0L; /* 2^62 */
 }
-
-/* The count of (p-1)-subsets, C(n, p-1), is formed on the device in 64 bits
- * with a product of p - 1 factors before the last division; at p = 6 that
- * product stays below 2^64 for n <= 8000. */
-bool critical_count_ok(int p, int64_t n) { return p < 6 || n <= 8000; }
 
 int64_t max_centred(const td_dataset &d)
 {
@@ -574,7 +572,6 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     }
     if (ctx->opt.algorithm == TD_ALG_CRITICAL)
         for (int s2 = 0; s2 < k; ++s2) {
-            if (!critical_count_ok(sets[s2].p, sets[s2].n)) return TD_ERR_RANGE;
             if (!devptr && !critical_range_ok(sets[s2].p, max_centred(sets[s2]))) return TD_ERR_RANGE;
         }
     if (st) memset(st, 0, sizeof(*st));

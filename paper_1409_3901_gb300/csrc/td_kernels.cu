@@ -646,10 +646,33 @@ __device__ int td_tight_depth(int t, const int64_t (&sint)[4][4], const TdScratc
 
 __device__ inline td_i128 td_i128_abs(td_i128 v) { return v < 0 ? -v : v; }
 
+/* gcd(|a|, |b|).  When both fit in 63 bits (the usual case) by the binary
+ * method (Stein): strip the common power of two, then subtract the smaller
+ * odd value from the larger and strip the twos until one is zero; max(x, y)
+ * falls every step, so the loop ends within 64 steps per bit pattern.  No
+ * division, where Euclid's int128 remainder is a long software sequence.
+ * Wider values use Euclid. */
 __device__ inline td_i128 td_i128_gcd(td_i128 a, td_i128 b)
 {
     a = td_i128_abs(a);
     b = td_i128_abs(b);
+    if ((a >> 63) == 0 && (b >> 63) == 0) {
+        uint64_t x = (uint64_t)a, y = (uint64_t)b;
+        if (x == 0) return (td_i128)y;
+        if (y == 0) return (td_i128)x;
+        const int sh = __ffsll((long long)(x | y)) - 1;
+        x >>= __ffsll((long long)x) - 1;
+        do {
+            y >>= __ffsll((long long)y) - 1;
+            if (x > y) {
+                const uint64_t t = x;
+                x = y;
+                y = t;
+            }
+            y -= x;
+        } while (y != 0);
+        return (td_i128)(x << sh);
+    }
     while (b != 0) {
         td_i128 r = a % b;
         a = b;
@@ -832,10 +855,17 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
  * (the per-tile set-up then costs well under 1%), at most 128, and at most
  * 1/64 of the query's range per CTA tile so that a short subset loop still
  * spreads over many CTAs; at least 4. */
+/* a / b for b > 0, by the 32-bit unsigned divide when both operands fit */
+__host__ __device__ inline int64_t td_div_nonneg(int64_t a, int64_t b)
+{
+    if (((uint64_t)a | (uint64_t)b) >> 32 == 0) return (int64_t)((uint32_t)a / (uint32_t)b);
+    return a / b;
+}
+
 __host__ __device__ inline int td_auto_spw(int nnz, int64_t nrange, int warps)
 {
     int64_t s = 65536 / (nnz > 0 ? nnz : 1);
-    const int64_t cap = nrange / (64 * (int64_t)(warps > 0 ? warps : 1));
+    const int64_t cap = td_div_nonneg(nrange, 64 * (int64_t)(warps > 0 ? warps : 1));
     s = s < cap ? s : cap;
     return s < 4 ? 4 : (s > 128 ? 128 : (int)s);
 }
@@ -857,22 +887,35 @@ __global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
         int spw = L.spw > 0 ? L.spw : td_auto_spw(Q.nnz, Q.hi - Q.lo, L.warps);
         int64_t ts = (int64_t)spw * L.warps;
         L.tile_size[q] = (int)ts;
-        int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? (Q.hi - Q.lo + ts - 1) / ts : 0;
+        int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? td_div_nonneg(Q.hi - Q.lo + ts - 1, ts) : 0;
         if (Q.d >= 2 && Q.d <= 6) sum[Q.d - 2] += cnt;
     }
 #pragma unroll
     for (int D = 0; D < TD_NDIM; ++D) s_part[D][threadIdx.x] = sum[D];
     __syncthreads();
-    if (threadIdx.x < TD_NDIM) {
-        const int D = threadIdx.x;
-        int64_t acc = 0;
-        for (int t = 0; t < T; ++t) {
-            int64_t v = s_part[D][t];
+    /* exclusive scan of the T partial sums of dimension D by warp D: each
+     * lane takes a run of T/32 (at most 32) consecutive entries */
+    if ((threadIdx.x >> 5) < TD_NDIM) {
+        const int D = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int run = (T + 31) >> 5, b0 = min(lane * run, T), b1 = min(b0 + run, T);
+        int64_t loc = 0;
+        for (int t = b0; t < b1; ++t) loc += s_part[D][t];
+        int64_t inc = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t v = __shfl_up_sync(TD_FULL, inc, o);
+            if (lane >= o) inc += v;
+        }
+        int64_t acc = inc - loc;
+        for (int t = b0; t < b1; ++t) {
+            const int64_t v = s_part[D][t];
             s_part[D][t] = acc;
             acc += v;
         }
-        L.tile_prefix[(int64_t)D * (nq + 1) + nq] = acc;
-        L.ticket[D * TD_TICKET_STRIDE] = 0ull;
+        if (lane == 31) {
+            L.tile_prefix[(int64_t)D * (nq + 1) + nq] = inc;
+            L.ticket[D * TD_TICKET_STRIDE] = 0ull;
+        }
     }
     __syncthreads();
     int64_t acc[TD_NDIM];
@@ -882,7 +925,7 @@ __global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
         const int q = L.order[j];
         const TdQuery &Q = L.q[q];
         const int64_t ts = L.tile_size[q];
-        const int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? (Q.hi - Q.lo + ts - 1) / ts : 0;
+        const int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? td_div_nonneg(Q.hi - Q.lo + ts - 1, ts) : 0;
 #pragma unroll
         for (int D = 0; D < TD_NDIM; ++D) {
             L.tile_prefix[(int64_t)D * (nq + 1) + j] = acc[D];

@@ -115,7 +115,7 @@ __device__ int td_adia_rank(const int64_t (*rows)[TD_MAXD], int cnt, int d)
                 g = td_i128_gcd(g, m[r][cc]);
             }
             if (g > 1)
-                for (int cc = 0; cc < d; ++cc) m[r][cc] /= g;
+                for (int cc = 0; cc < d; ++cc) m[r][cc] = td_i128_div_exact(m[r][cc], g);
         }
         ++rank;
     }

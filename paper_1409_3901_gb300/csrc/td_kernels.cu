@@ -681,6 +681,16 @@ __device__ inline td_i128 td_i128_gcd(td_i128 a, td_i128 b)
     return a;
 }
 
+/* v / g for a divisor g > 0 of v: nothing for g = 1, a 64-bit divide when
+ * both are below 2^62, the int128 divide otherwise */
+__device__ inline td_i128 td_i128_div_exact(td_i128 v, td_i128 g)
+{
+    if (g == 1) return v;
+    const td_i128 lim = (td_i128)1 << 62;
+    if (v < lim && v > -lim && g < lim) return (td_i128)((int64_t)v / (int64_t)g);
+    return v / g;
+}
+
 __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
 {
     const int q = blockIdx.x;
@@ -736,7 +746,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
                     td_i128 g = 0;
                     for (int c = 0; c < p; ++c) g = td_i128_gcd(g, v[c]);
                     if (g > 1)
-                        for (int c = 0; c < p; ++c) v[c] /= g;
+                        for (int c = 0; c < p; ++c) v[c] = td_i128_div_exact(v[c], g);
                 }
             }
             int lead = -1;
@@ -745,7 +755,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
             if (lead < 0) continue;
             td_i128 g = 0;
             for (int c = 0; c < p; ++c) g = td_i128_gcd(g, v[c]);
-            for (int c = 0; c < p; ++c) basis[r][c] = v[c] / g;
+            for (int c = 0; c < p; ++c) basis[r][c] = td_i128_div_exact(v[c], g);
             pc[r] = lead;
             ++r;
         }

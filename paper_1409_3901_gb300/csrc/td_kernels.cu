@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
 {
     const int q = blockIdx.x;
     __shared__ int s_z[TD_MAXD];
-    __shared__ int s_Z, s_max[TD_MAXD], s_pos, s_neg;
+    __shared__ int s_Z, s_max[TD_MAXD], s_pos, s_neg, s_amax;
     __shared__ int s_d, s_piv[TD_MAXD];
     TdQuery *Q = &L.q[q];
     const int set = Q->set;
@@ -710,6 +710,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         s_Z = 0;
         s_pos = 0;
         s_neg = 0;
+        s_amax = 0;
     }
     __syncthreads();
     int zc = 0;
@@ -770,8 +771,12 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
     /* per-coordinate maxima over the projected coordinates, and the sign
      * counts of the single coordinate when d == 1 */
     int lmax[TD_MAXD] = { 0, 0, 0, 0, 0, 0 };
-    int pos = 0, neg = 0;
+    int pos = 0, neg = 0, amx = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int c = 0; c < p; ++c) { /* every coordinate, for the bound below */
+            const int64_t v = (int64_t)X[(int64_t)i * p + c] - s_z[c];
+            amx = max(amx, (int)min(v < 0 ? -v : v, (int64_t)INT_MAX));
+        }
         for (int c = 0; c < d; ++c) {
             int64_t v = (int64_t)X[(int64_t)i * p + s_piv[c]] - s_z[s_piv[c]];
             int64_t a = v < 0 ? -v : v;
@@ -783,6 +788,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         }
     }
     for (int c = 0; c < d; ++c) atomicMax(&s_max[c], lmax[c]);
+    atomicMax(&s_amax, amx);
     if (d == 1) {
         atomicAdd(&s_pos, pos);
         atomicAdd(&s_neg, neg);
@@ -818,7 +824,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         L.qmin[q] = INT_MAX;
     }
     /* An upper bound of T from data directions u = +-x_j (Algorithm 3,
-     * Step 2): T <= #{i : u'x_i <= 0} for every u, exact in int64.  qmin
+     * Step 2): T <= #{i : u'x_i <= 0} for every u, exact in int32 or int64.  qmin
      * starts at that bound minus Z (T = Z + min V, and a sweep reports V
      * exactly whenever it is below qmin), so the coarse bound prunes from the
      * first sweep of every tile on.  No subset is skipped for it.  The bound
@@ -833,6 +839,13 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
     if (threadIdx.x == 0) s_ub = INT_MAX;
     __syncthreads();
     int ub = INT_MAX;
+    /* the dot products in 32 bits when p max|x_c|^2 < 2^31 over every
+     * centred coordinate (then every centred entry fits too) */
+    const int am = s_amax;
+    const bool n32 = am < 46341 && (int64_t)p * am * am < 2147483648LL;
+    int zc32[TD_MAXD];
+#pragma unroll
+    for (int c = 0; c < TD_MAXD; ++c) zc32[c] = s_z[c];
     for (int kd = threadIdx.x; kd < ndir; kd += blockDim.x) {
         const int j = (int)((int64_t)kd * n / ndir);
         int64_t xj[TD_MAXD];
@@ -844,11 +857,26 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         }
         if (!nz) continue;
         int le = 0, ge = 0;
-        for (int i = 0; i < n; ++i) {
-            int64_t dot = 0;
-            for (int c = 0; c < p; ++c) dot += xj[c] * ((int64_t)X[(int64_t)i * p + c] - s_z[c]);
-            le += dot <= 0;
-            ge += dot >= 0;
+        if (n32) {
+            int xj32[TD_MAXD];
+#pragma unroll
+            for (int c = 0; c < TD_MAXD; ++c) xj32[c] = (int)xj[c];
+            for (int i = 0; i < n; ++i) {
+                const int32_t *xi = X + (int64_t)i * p;
+                int dot = 0;
+#pragma unroll
+                for (int c = 0; c < TD_MAXD; ++c)
+                    if (c < p) dot += xj32[c] * (xi[c] - zc32[c]);
+                le += dot <= 0;
+                ge += dot >= 0;
+            }
+        } else {
+            for (int i = 0; i < n; ++i) {
+                int64_t dot = 0;
+                for (int c = 0; c < p; ++c) dot += xj[c] * ((int64_t)X[(int64_t)i * p + c] - s_z[c]);
+                le += dot <= 0;
+                ge += dot >= 0;
+            }
         }
         ub = min(ub, min(le, ge));
     }

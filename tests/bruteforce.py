@@ -15,6 +15,11 @@ sweeps.
 
 A second, polynomial check for p = 2 enumerates the halfplanes just beside
 every critical line through the origin.
+
+A third route takes the critical directions of Proposition 1 with r = p - 1:
+the normals of the hyperplanes spanned by p - 1 nonzero points, each tilted
+so that the points on the hyperplane take their best signs (found by the
+sign-vector enumeration inside the hyperplane).
 """
 from itertools import combinations
 from math import gcd
@@ -102,4 +107,54 @@ def depth_p2_halfplanes(X, z):
                     if s < 0:
                         cnt += 1
                 best = cnt if best is None else min(best, cnt)
+    return Z + best
+
+
+def _det(M):
+    """Exact integer determinant by cofactor expansion along the first row."""
+    n = len(M)
+    if n == 0:
+        return 1
+    if n == 1:
+        return M[0][0]
+    return sum((-1) ** c * M[0][c] * _det([row[:c] + row[c + 1:] for row in M[1:]])
+               for c in range(n) if M[0][c] != 0)
+
+
+def depth_critical_normals(X, z):
+    """T by the critical directions (Proposition 1 with r = p - 1), exactly.
+
+    For p - 1 nonzero points J with independent rows, n_J (the cofactors of
+    their p x (p-1) matrix, so n_J'x = det[x_J | x]) is normal to H = span J.
+    A direction s n_J + eps v with v generic in H keeps the points off H on
+    their side and splits the points on H by v alone, so the fewest points
+    strictly below is #{s n_J'x < 0} + the open depth of the points on H
+    inside H.  Every generic direction lies in an open cell whose closure has
+    a ray spanned by some n_J when the nonzero points span R^p (or all lie on
+    one hyperplane), hence T = Z + the minimum over J and s.  The open depth
+    inside H is the sign-vector enumeration on the points of H with one
+    coordinate where n_J is nonzero dropped (injective on H).
+    """
+    p = len(z)
+    xs = [tuple(int(a) - int(b) for a, b in zip(row, z)) for row in X]
+    Z = sum(1 for x in xs if all(v == 0 for v in x))
+    nz = [x for x in xs if any(v != 0 for v in x)]
+    if p == 1:
+        return depth_p1(X, z)
+    if not nz:
+        return Z
+    best = None
+    for J in combinations(range(len(nz)), p - 1):
+        rows = [nz[j] for j in J]
+        n = tuple((-1) ** k * _det([list(r[:k] + r[k + 1:]) for r in rows]) for k in range(p))
+        if all(v == 0 for v in n):
+            continue
+        jd = next(k for k in range(p) if n[k] != 0)
+        dots = [sum(a * b for a, b in zip(n, x)) for x in nz]
+        on_h = [x[:jd] + x[jd + 1:] for x, d in zip(nz, dots) if d == 0]
+        od = depth_bruteforce(on_h, (0,) * (p - 1))
+        v = min(sum(1 for d in dots if d < 0), sum(1 for d in dots if d > 0)) + od
+        best = v if best is None else min(best, v)
+    if best is None:
+        raise ValueError("the nonzero points span less than a hyperplane")
     return Z + best

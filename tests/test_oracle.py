@@ -2,6 +2,8 @@
 
 * exact brute force on tiny inputs (sign-vector enumeration, tests/bruteforce.py),
   on random, tie-heavy, duplicated, antipodal, rank-deficient and deep cases;
+* a second brute force through the critical directions (Proposition 1 with
+  r = p - 1, the points on each hyperplane tilted to their best signs);
 * the closed forms: p = 1 (Section 3) and an O(n^2) halfplane count for p = 2;
 * invariances of Eq. (1): row permutation, integer translation, integer
   unimodular maps, positive integer scaling of X - z;
@@ -14,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from bruteforce import depth_bruteforce, depth_p1, depth_p2_halfplanes
+from bruteforce import depth_bruteforce, depth_critical_normals, depth_p1, depth_p2_halfplanes
 from paper_literal import in_general_position, literal_alg2, literal_rcom
 
 
@@ -40,6 +42,22 @@ def _cases(seed, count, pmax=6, nmax=9, lims=(1, 2, 3, 40)):
 def test_oracle_matches_bruteforce_ties(seed):
     for X, z in _cases(1000 + seed, 250):
         assert oracle.depth(X, z) == depth_bruteforce(X, z), (X.tolist(), z.tolist())
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_oracle_matches_critical_normals(seed):
+    """A second brute force through the critical directions (Proposition 1
+    with r = p - 1), on the same tie-heavy families, wherever the nonzero
+    centred points span at least a hyperplane."""
+    checked = 0
+    for X, z in _cases(3000 + seed, 150, pmax=5):
+        xs = (X - z)[np.any(X != z, axis=1)]
+        p = X.shape[1]
+        if p == 1 or len(xs) == 0 or np.linalg.matrix_rank(xs.astype(float)) < p - 1:
+            continue
+        assert oracle.depth(X, z) == depth_critical_normals(X, z), (X.tolist(), z.tolist())
+        checked += 1
+    assert checked > 60
 
 
 @pytest.mark.parametrize("p", [3, 4, 5, 6])
@@ -108,6 +126,31 @@ def test_oracle_matches_bruteforce_twins(p):
         X = np.vstack([B, s * B])
         z = rng.integers(-4, 5, size=p)
         assert oracle.depth(X + z, z) == depth_bruteforce(X + z, z), (X.tolist(), z.tolist())
+
+
+@pytest.mark.parametrize("p", [3, 4, 5])
+def test_critical_normals_on_tight_sets_and_twins(p):
+    """The critical-direction brute force on the two families where the
+    tight-set correction decides the result (subsets whose span holds extra
+    points)."""
+    rng = np.random.default_rng(2500 + p)
+    checked = 0
+    for trial in range(60 if p <= 4 else 30):
+        if trial % 2 == 0:
+            X, z = _tight_case(rng, p)
+        else:
+            half = 4 if p <= 4 else 3
+            B = rng.integers(-2, 3, size=(half, p))
+            B[rng.random(B.shape) < 0.3] = 0
+            B[np.all(B == 0, axis=1), 0] = 1
+            X = np.vstack([B, rng.choice([1, 1, 2, -1, -2], size=(half, 1)) * B])
+            z = np.zeros(p, dtype=np.int64)
+        xs = X[np.any(X != 0, axis=1)]
+        if len(xs) == 0 or np.linalg.matrix_rank(xs.astype(float)) < p - 1:
+            continue
+        assert oracle.depth(X, z) == depth_critical_normals(X, z), (X.tolist(), z.tolist())
+        checked += 1
+    assert checked >= (20 if p <= 4 else 10)
 
 
 @pytest.mark.parametrize("p,r", [(3, 1), (3, 2), (4, 1), (4, 2), (4, 3), (5, 2), (5, 3), (6, 3), (6, 4), (6, 5)])

@@ -21,6 +21,7 @@ the normals of the hyperplanes spanned by p - 1 nonzero points, each tilted
 so that the points on the hyperplane take their best signs (found by the
 sign-vector enumeration inside the hyperplane).
 """
+from fractions import Fraction
 from itertools import combinations
 from math import gcd
 
@@ -158,3 +159,41 @@ def depth_critical_normals(X, z):
     if best is None:
         raise ValueError("the nonzero points span less than a hyperplane")
     return Z + best
+
+
+def _solve_exact(A, b):
+    """The unique solution of the square or tall system A x = b in fractions,
+    or None when the columns of A are dependent or the system is inconsistent."""
+    rows, cols = len(A), len(A[0])
+    M = [[Fraction(v) for v in A[r]] + [Fraction(b[r])] for r in range(rows)]
+    piv_row = 0
+    for c in range(cols):
+        pr = next((r for r in range(piv_row, rows) if M[r][c] != 0), None)
+        if pr is None:
+            return None
+        M[piv_row], M[pr] = M[pr], M[piv_row]
+        for r in range(rows):
+            if r != piv_row and M[r][c] != 0:
+                f = M[r][c] / M[piv_row][c]
+                M[r] = [a - f * b2 for a, b2 in zip(M[r], M[piv_row])]
+        piv_row += 1
+    if any(M[r][cols] != 0 for r in range(piv_row, rows)):
+        return None
+    return [M[r][cols] / M[r][r] for r in range(cols)]
+
+
+def in_convex_hull(X, z):
+    """z in conv(X), exactly: by Caratheodory, z is then a convex combination
+    of at most p + 1 affinely independent rows, whose barycentric coordinates
+    solve a system with a unique solution (Gaussian elimination in
+    fractions)."""
+    X = [tuple(int(v) for v in row) for row in X]
+    z = tuple(int(v) for v in z)
+    p = len(z)
+    for k in range(1, min(p + 1, len(X)) + 1):
+        for J in combinations(range(len(X)), k):
+            A = [[X[j][c] for j in J] for c in range(p)] + [[1] * k]
+            lam = _solve_exact(A, list(z) + [1])
+            if lam is not None and all(v >= 0 for v in lam):
+                return True
+    return False

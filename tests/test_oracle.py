@@ -8,6 +8,7 @@
 * invariances of Eq. (1): row permutation, integer translation, integer
   unimodular maps, positive integer scaling of X - z;
 * bounds: 0 outside the bounding box, >= 1 at data points, Z <= T <= (n+Z)/2;
+* T = 0 exactly when z lies outside conv(X) (an exact Caratheodory hull test);
 * the paper's literal Algorithm 1 in float64 on data in general position
   (Proposition 1 holds there), and the two tie cases where it is wrong;
 * the range form: a partition of the subset positions gives the full result.
@@ -16,7 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
-from bruteforce import depth_bruteforce, depth_critical_normals, depth_p1, depth_p2_halfplanes
+from bruteforce import depth_bruteforce, depth_critical_normals, depth_p1, depth_p2_halfplanes, in_convex_hull
 from paper_literal import in_general_position, literal_alg2, literal_rcom
 
 
@@ -151,6 +152,21 @@ def test_critical_normals_on_tight_sets_and_twins(p):
         assert oracle.depth(X, z) == depth_critical_normals(X, z), (X.tolist(), z.tolist())
         checked += 1
     assert checked >= (20 if p <= 4 else 10)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_zero_depth_exactly_outside_the_hull(seed):
+    """T = 0 iff z lies outside conv(X) (a closed halfspace through z misses
+    every data point iff z can be separated strictly), checked by an exact
+    hull test that shares nothing with either brute force."""
+    outside = inside = 0
+    for X, z in _cases(4000 + seed, 200, pmax=4, nmax=8):
+        t = oracle.depth(X, z)
+        hull = in_convex_hull(X, z)
+        assert (t == 0) == (not hull), (X.tolist(), z.tolist(), t)
+        outside += not hull
+        inside += hull
+    assert outside > 20 and inside > 20
 
 
 @pytest.mark.parametrize("p,r", [(3, 1), (3, 2), (4, 1), (4, 2), (4, 3), (5, 2), (5, 3), (6, 3), (6, 4), (6, 5)])

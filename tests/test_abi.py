@@ -149,3 +149,20 @@ def test_critical_form_not_served_by_streams(tukey):
     assert rc != tukey.TD_ERR_INVALID
     if ptr.value:
         tukey.td_destroy(ptr)
+
+
+def test_missing_library_fails_loudly(tukey, monkeypatch):
+    """No fallback: without the built library the binding raises."""
+    monkeypatch.setattr(tukey, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libtukeydepth.so"))
+    with pytest.raises(tukey.LibraryMissing):
+        tukey._load()
+
+
+def test_smoke_needs_a_device():
+    """smoke() runs the kernels on cuda:0 and refuses to run without one."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    import __graft_entry__
+    with pytest.raises(AssertionError):
+        __graft_entry__.smoke()

@@ -51,7 +51,7 @@ def test_oracle_matches_critical_normals(seed):
     with r = p - 1), on the same tie-heavy families, wherever the nonzero
     centred points span at least a hyperplane."""
     checked = 0
-    for X, z in _cases(3000 + seed, 150, pmax=5):
+    for X, z in _cases(3000 + seed, 150, pmax=6):
         xs = (X - z)[np.any(X != z, axis=1)]
         p = X.shape[1]
         if p == 1 or len(xs) == 0 or np.linalg.matrix_rank(xs.astype(float)) < p - 1:
@@ -129,7 +129,7 @@ def test_oracle_matches_bruteforce_twins(p):
         assert oracle.depth(X + z, z) == depth_bruteforce(X + z, z), (X.tolist(), z.tolist())
 
 
-@pytest.mark.parametrize("p", [3, 4, 5])
+@pytest.mark.parametrize("p", [3, 4, 5, 6])
 def test_critical_normals_on_tight_sets_and_twins(p):
     """The critical-direction brute force on the two families where the
     tight-set correction decides the result (subsets whose span holds extra

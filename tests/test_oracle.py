@@ -160,7 +160,7 @@ def test_zero_depth_exactly_outside_the_hull(seed):
     every data point iff z can be separated strictly), checked by an exact
     hull test that shares nothing with either brute force."""
     outside = inside = 0
-    for X, z in _cases(4000 + seed, 200, pmax=4, nmax=8):
+    for X, z in _cases(4000 + seed, 200, pmax=6, nmax=8):
         t = oracle.depth(X, z)
         hull = in_convex_hull(X, z)
         assert (t == 0) == (not hull), (X.tolist(), z.tolist(), t)

@@ -10,6 +10,7 @@ from .oracle import (  # noqa: F401
     depth,
     depth_many,
     depth_range,
+    subset_min,
     bivariate_closed,
     rank,
     adia,

@@ -58,6 +58,9 @@ def _load():
             lib.oracle_adia.argtypes = [i32p, ctypes.c_int64, ctypes.c_int, i32p, i64p, i64p]
             lib.oracle_adia.restype = ctypes.c_int
             lib.oracle_critical.argtypes = [i64p, ctypes.c_int64, i64p, ctypes.POINTER(ctypes.c_uint8)]
+            lib.oracle_subset_min.argtypes = [i32p, ctypes.c_int64, ctypes.c_int, i32p, i32p, ctypes.c_int64,
+                                              i64p, i64p]
+            lib.oracle_subset_min.restype = ctypes.c_int
             lib.oracle_critical.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -109,6 +112,23 @@ def depth_range(X, z, lo, hi):
                                   ctypes.byref(npos), ctr))
     v = int(part.value)
     return (None if v == np.iinfo(np.int64).max else v), int(npos.value), tuple(int(c) for c in ctr)
+
+
+def subset_min(X, z, subsets):
+    """Z + min V(S) over the listed subsets (rows of p-2 increasing indices
+    into the nonzero centred points in data order; the points must span R^p).
+    Returns (value or None when no listed subset is independent, dependent)."""
+    lib = _load()
+    X, Xp = _i32(X)
+    z, zp = _i32(z)
+    n, p = X.shape
+    S = np.ascontiguousarray(np.asarray(subsets, dtype=np.int32).reshape(-1, p - 2))
+    out = ctypes.c_int64(0)
+    dep = ctypes.c_int64(0)
+    _check(lib.oracle_subset_min(Xp, n, p, zp, S.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), S.shape[0],
+                                 ctypes.byref(out), ctypes.byref(dep)))
+    v = int(out.value)
+    return (None if v == np.iinfo(np.int64).max else v), int(dep.value)
 
 
 def bivariate_closed(Y):

@@ -968,6 +968,65 @@ int oracle_depth_range(const int32_t *X, int64_t n, int p, const int32_t *z,
     return OR_OK;
 }
 
+/* Z + the minimum of V(S) (Algorithm 1, step 1, with reading R6) over an
+ * explicit list of subsets S instead of all of them: for checking a part of
+ * the subset loop of another implementation whose enumeration order differs
+ * from the one above.  The subsets are `count` rows of p-2 indices into the
+ * nonzero centred points x_i = X_i - z taken in data order; the nonzero
+ * points must span R^p (rank p, p >= 3; otherwise OR_EINVAL, since R7 would
+ * change the subset size).  *out receives Z + min V(S) over the independent
+ * listed subsets, INT64_MAX if there is none; *dependent (may be NULL) the
+ * number of listed subsets of rank < p-2 (skipped, reading R2). */
+int oracle_subset_min(const int32_t *X, int64_t n, int p, const int32_t *z, const int32_t *subsets,
+                      int64_t count, int64_t *out, int64_t *dependent)
+{
+    if (!X || !z || !out || n < 1 || p < 3 || p > OR_MAXD || count < 0 || (count > 0 && !subsets))
+        return OR_EINVAL;
+    int64_t *x = centre(X, n, p, z);
+    if (!x) return OR_ENOMEM;
+    if (!coord_bound_ok(x, n, p)) { free(x); return OR_ERANGE; }
+    int piv[OR_MAXD];
+    if (rank_pivots(x, (int)n, p, piv) != p) { free(x); return OR_EINVAL; }
+    /* data index of every nonzero point, in data order */
+    int *nzi = (int *)malloc(sizeof(int) * (size_t)n);
+    i128 *y = (i128 *)malloc(sizeof(i128) * 2 * (size_t)n);
+    int64_t *tight = (int64_t *)malloc(sizeof(int64_t) * (size_t)n * (size_t)(p - 2));
+    if (!nzi || !y || !tight) { free(nzi); free(y); free(tight); free(x); return OR_ENOMEM; }
+    int nnz = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int zero = 1;
+        for (int c = 0; c < p; ++c)
+            if (x[i * p + c] != 0) zero = 0;
+        if (!zero) nzi[nnz++] = (int)i;
+    }
+    const int k = p - 2;
+    int64_t best = INT64_MAX, dep = 0;
+    int rc = OR_OK;
+    for (int64_t j = 0; j < count && rc == OR_OK; ++j) {
+        int S[OR_MAXD];
+        for (int t = 0; t < k; ++t) {
+            const int32_t v = subsets[j * k + t];
+            if (v < 0 || v >= nnz || (t > 0 && v <= subsets[j * k + t - 1])) { rc = OR_EINVAL; break; }
+            S[t] = nzi[v];
+        }
+        if (rc != OR_OK) break;
+        /* V(S) over all n points: the zero points are counted by N(S) */
+        int64_t V = 0;
+        const int r = subset_value(x, (int)n, p, S, y, tight, &V, NULL, NULL);
+        if (r < 0) rc = OR_ENOMEM;
+        else if (r > 0) ++dep;
+        else if (V < best) best = V;
+    }
+    free(nzi);
+    free(y);
+    free(tight);
+    free(x);
+    if (rc != OR_OK) return rc;
+    *out = best;
+    if (dependent) *dependent = dep;
+    return OR_OK;
+}
+
 /* Algorithm 2 alone on cnt points (pairs, int64): the closed bivariate count. */
 int oracle_bivariate_closed(const int64_t *Y, int64_t cnt, int64_t *count)
 {

@@ -318,3 +318,42 @@ def test_oracle_rejects_bad_input():
     big = np.array([[2_000_000_000, 0, 0, 0, 0, 0], [0, 1, 0, 0, 0, 0]], np.int64)
     with pytest.raises(oracle.OracleError):
         oracle.depth(big.astype(np.int32), np.array([-2_000_000_000, 0, 0, 0, 0, 0], np.int32))
+
+
+@pytest.mark.parametrize("p", [3, 4, 5, 6])
+def test_subset_min_over_colex_partitions(p):
+    """oracle.subset_min (Z + min V(S) over listed subsets, the form in which
+    sampled ranges of the library's colex subset loop are checked): over all
+    subsets it is the depth, which the brute force pins; over any partition
+    of the colex ranks into contiguous ranges the minimum of the parts is the
+    depth; a listed dependent subset (two equal points) is counted and
+    skipped; the order of the list does not matter."""
+    from math import comb
+
+    from subsets import colex_range, shard_range
+    rng = np.random.default_rng(700 + p)
+    n = {3: 30, 4: 18, 5: 13, 6: 11}[p]
+    for trial in range(3):
+        X = rng.integers(-3, 4, size=(n, p)).astype(np.int32)
+        X[-2:] = X[2:4]                                        # duplicates
+        z = X[0] if trial == 0 else rng.integers(-1, 2, size=p).astype(np.int32)
+        if oracle.rank(X, z)[0] < p:
+            continue
+        want = oracle.depth(X, z)
+        if n <= 13:
+            assert want == depth_bruteforce(X, z)
+        nnz = int(n - np.all(X == z, axis=1).sum())
+        k = p - 2
+        allc = colex_range(k, 0, comb(nnz, k))
+        v, dep = oracle.subset_min(X, z, allc)
+        assert v == want
+        v2, dep2 = oracle.subset_min(X, z, allc[::-1])
+        assert (v2, dep2) == (v, dep)
+        S = int(rng.integers(2, 9))
+        parts = [oracle.subset_min(X, z, colex_range(k, *shard_range(nnz, k, s, S)))[0] for s in range(S)]
+        assert min(x for x in parts if x is not None) == want
+    # two equal nonzero points make a dependent subset (p = 4: S = {i, j})
+    X = np.array([[1, 0, 0, 0], [1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1], [-1, -1, -1, -1]],
+                 np.int32)
+    v, dep = oracle.subset_min(X, np.zeros(4, np.int32), [[0, 1]])
+    assert v is None and dep == 1

@@ -109,12 +109,25 @@ typedef struct {
                                  unchanged; stats.early_skipped counts the subsets not swept.
                                  0 (default): every subset is swept. */
     int32_t algorithm;        /* TD_ALG_RCOM (default), TD_ALG_ADIA or TD_ALG_CRITICAL */
-    int32_t reserved;         /* must be 0 */
+    int32_t unseeded;         /* nonzero: each query's running minimum starts at +infinity instead
+                                 of the data-direction upper bound, so that under sharding out[q]
+                                 is exactly Z + the minimum of V(S) over the shard's own range
+                                 (INT32_MAX if it holds no independent subset) -- the form in
+                                 which a range can be checked against a reference.  Same depths
+                                 unsharded; slower.  0 (default): seeded. */
     int64_t shard_index;      /* multi-GPU sharding of Algorithm 1's subset loop: process only the */
     int64_t shard_count;      /* shard_index-th of shard_count contiguous ranges of subset positions
-                                 of every query (0 or 1: all).  out[q] is then the minimum over that
-                                 range (INT32_MAX if it holds no subset); the minimum of out[q] over
-                                 all shards is the depth. */
+                                 of every query (0 or 1: all).  The positions are the colex ranks
+                                 r = sum_i C(c_i, i+1) of the (d-2)-subsets c_0 < .. < c_(d-3) of
+                                 the query's nnz nonzero centred points in data order (d its
+                                 effective dimension); shard s of S takes the ranks
+                                 [floor(N s / S), floor(N (s+1) / S)), N = C(nnz, d-2), and a
+                                 query without a subset loop is answered by shard 0 alone (the
+                                 others report INT32_MAX).  out[q] is then Z + the minimum of
+                                 V(S) over that range, or the data-direction bound if that is
+                                 smaller (see unseeded), or INT32_MAX if the range holds no subset
+                                 and the bound was not taken; the minimum of out[q] over all shards
+                                 is the depth. */
     void *stream;             /* cudaStream_t to run on; NULL = the context's own stream */
 } td_options;
 
@@ -207,7 +220,8 @@ int td_stream_destroy(td_stream *s);
  * that each GPU loading this library holds until the process exits.
  *   - Limits: n <= TD_NOALLOC_MAX_N, m <= TD_NOALLOC_MAX_M (TD_ERR_INVALID
  *     beyond them: the array has no room), p <= TD_MAX_P, and the coordinate
- *     limit of td_coord_limit (TD_ERR_RANGE, checked on the device).
+ *     limit of td_coord_limit on every coordinate (TD_ERR_RANGE: the first
+ *     kernel tests it and gives an out-of-range query no further work).
  *   - The first call on a device looks the array up (cudaGetSymbolAddress)
  *     and so loads the module there; make that first call before any stream
  *     capture.
@@ -216,7 +230,8 @@ int td_stream_destroy(td_stream *s);
  *   - All calls share the one array: calls that overlap on the GPU (other
  *     host threads, or other streams still running an earlier call) race and
  *     must be serialised by the caller.  The sweep uses at most
- *     TD_NOALLOC_CTAS thread blocks. */
+ *     TD_NOALLOC_CTAS thread blocks.  Its shared-memory limits are raised,
+ *     never lowered, so it can run beside td_depth calls of other threads. */
 #define TD_NOALLOC_MAX_N 512
 #define TD_NOALLOC_MAX_M 4096
 #define TD_NOALLOC_CTAS 80

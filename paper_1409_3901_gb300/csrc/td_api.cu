@@ -99,7 +99,7 @@ struct Work {
 };
 
 struct GraphKey {
-    int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw, early_exit, algorithm;
+    int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw, early_exit, algorithm, unseeded;
     size_t smem;
     const void *ptrs[17];
     int64_t shard_index, shard_count;
@@ -405,6 +405,7 @@ TdLaunch make_launch(const Work &w, const Plan &P, const int32_t *x_arena, const
     L.scratch = (char *)w.scratch.p;
     L.scratch_per_warp = td_scratch_per_warp(P.nmax);
     L.early_exit = o.early_exit != 0;
+    L.unseeded = o.unseeded != 0;
     L.adia = o.algorithm == TD_ALG_ADIA;
     L.critical = o.algorithm == TD_ALG_CRITICAL;
     if (L.adia) {
@@ -634,6 +635,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         key.blog2 = blog2;
         key.spw = o.subsets_per_warp;
         key.early_exit = L.early_exit;
+        key.unseeded = L.unseeded;
         key.algorithm = o.algorithm;
         key.smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
         const Work &cw = ctx->w;
@@ -683,18 +685,16 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     TDCK(cudaMemcpyAsync(&C, ctx->w.ctr.p, sizeof(C), cudaMemcpyDeviceToHost, s));
     TDCK(cudaStreamSynchronize(s));
     if (C.errors != 0) return TD_ERR_INTERNAL;
-    /* range check for device pointers: the set-up kernel's maxima */
+    /* range check for device pointers: the set-up kernel compared every
+     * centred coordinate with the limit and gave an out-of-range query no
+     * work (TD_DIRECT_RANGE); its maximum serves the critical form's bound */
     if (devptr) {
         std::vector<TdQuery> hq(P.nq);
         TDCK(cudaMemcpy(hq.data(), ctx->w.q.p, P.nq * sizeof(TdQuery), cudaMemcpyDeviceToHost));
         for (int qi = 0; qi < P.nq; ++qi) {
-            int64_t lim = td_coord_limit(P.sets[hq[qi].set].p);
-            int64_t M = 0;
-            for (int c = 0; c < TD_MAXD; ++c) {
-                if (hq[qi].mx[c] > lim) return TD_ERR_RANGE;
-                M = std::max<int64_t>(M, hq[qi].mx[c]);
-            }
-            if (o.algorithm == TD_ALG_CRITICAL && !critical_range_ok(hq[qi].d, M)) return TD_ERR_RANGE;
+            if (hq[qi].direct == TD_DIRECT_RANGE || hq[qi].amax > td_coord_limit_of(P.sets[hq[qi].set].p))
+                return TD_ERR_RANGE;
+            if (o.algorithm == TD_ALG_CRITICAL && !critical_range_ok(hq[qi].d, hq[qi].amax)) return TD_ERR_RANGE;
         }
     }
     if (devptr) {
@@ -744,18 +744,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
 /* exported entry points                                                    */
 /* ======================================================================= */
 
-extern "C" int64_t td_coord_limit(int32_t p)
-{
-    switch (p) {
-    case 1:
-    case 2:
-    case 3: return 4194303; /* 2^22 - 1: exact in binary32 and in the magic-constant conversion */
-    case 4: return 524287;   /* 4 * 2 M^2 * M < 2^62 */
-    case 5: return 16383;    /* 5 * 3^(3/2) M^3 * M < 2^62 */
-    case 6: return 2047;     /* 6 * (2M)^4 * M < 2^62 */
-    default: return 0;
-    }
-}
+extern "C" int64_t td_coord_limit(int32_t p) { return td_coord_limit_of(p); }
 
 extern "C" const char *td_strerror(int code)
 {

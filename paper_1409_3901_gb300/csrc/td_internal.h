@@ -8,6 +8,25 @@
 #define TD_MAXD 6
 #define TD_NDIM 5            /* effective dimensions 2..6 with a subset loop */
 #define TD_TICKET_STRIDE 16  /* work counters 128 bytes apart */
+#define TD_DIRECT_RANGE (-2) /* TdQuery.direct of a query whose centred coordinates exceed the limit */
+
+/* Largest |X_ij - z_j| (every coordinate) the kernels accept for dimension p:
+ * it keeps every exact intermediate in 64-bit (coordinates, minors,
+ * projections) or 128-bit (cross products) integers, every coordinate exact
+ * in binary32, and inside the window of the magic-constant float-to-int
+ * conversion (|v| <= 2^22). */
+static inline __host__ __device__ int64_t td_coord_limit_of(int p)
+{
+    switch (p) {
+    case 1:
+    case 2:
+    case 3: return 4194303; /* 2^22 - 1 */
+    case 4: return 524287;  /* 4 * 2 M^2 * M < 2^62 */
+    case 5: return 16383;   /* 5 * 3^(3/2) M^3 * M < 2^62 */
+    case 6: return 2047;    /* 6 * (2M)^4 * M < 2^62 */
+    default: return 0;
+    }
+}
 
 /* Per-query state written by the set-up kernel (one per query). */
 struct TdQuery {
@@ -17,8 +36,9 @@ struct TdQuery {
     int32_t Z;             /* centred points equal to zero (counted by every closed halfspace) */
     int32_t d;             /* rank of the nonzero centred points (effective dimension) */
     int32_t k;             /* subset size d - 2 of Algorithm 1, or -1 when there is no subset loop */
-    int32_t direct;        /* final count when there is no subset loop (nnz == 0 or d <= 1), else -1 */
-    int32_t pad;
+    int32_t direct;        /* final count when there is no subset loop (nnz == 0 or d <= 1), -1 when
+                              there is one, TD_DIRECT_RANGE when the query is out of range */
+    int32_t amax;          /* max |x_ij| over every coordinate (saturated at INT32_MAX) */
     int32_t piv[TD_MAXD];  /* coordinates on which the span of the points projects injectively */
     int32_t mx[TD_MAXD];   /* max |x_i| per projected coordinate (FP32 error bounds) */
     int64_t nsub;          /* subset positions C(nnz, k) of the whole loop */
@@ -64,7 +84,7 @@ struct TdLaunch {
     int32_t early_exit;      /* nonzero: seed qmin with the data-direction bound, stop a query at 0 */
     int32_t adia;            /* nonzero: Algorithm 3 (search kernel before the sweep) */
     int32_t critical;        /* nonzero: Proposition 1 with r = p-1 (subsets of d-1 points) */
-    int32_t pad3;
+    int32_t unseeded;        /* nonzero: qmin starts at +inf, not at the data-direction bound */
     uint16_t *perm;          /* Algorithm 3: staging position of every nonzero point, per query, or null */
     int64_t perm_stride;     /* entries per query in perm */
     uint64_t *adia_keys;     /* Algorithm 3 node tables, per CTA of the search kernel */

@@ -52,7 +52,10 @@
 #include <stdint.h>
 #include <limits.h>
 
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "td_internal.h"
 #include "td_exact.cuh"
@@ -713,13 +716,41 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         s_amax = 0;
     }
     __syncthreads();
-    int zc = 0;
+    /* Z and the largest centred coordinate (every coordinate) */
+    int zc = 0, amx = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         bool zero = true;
-        for (int c = 0; c < p; ++c) zero &= (X[(int64_t)i * p + c] == s_z[c]);
+        for (int c = 0; c < p; ++c) {
+            const int64_t v = (int64_t)X[(int64_t)i * p + c] - s_z[c];
+            zero &= v == 0;
+            amx = max(amx, (int)min(v < 0 ? -v : v, (int64_t)INT_MAX));
+        }
         zc += zero;
     }
     atomicAdd(&s_Z, zc);
+    atomicMax(&s_amax, amx);
+    __syncthreads();
+    if (s_amax > td_coord_limit_of(p)) {
+        /* beyond the exact-arithmetic limit: no rank, no subset loop, no
+         * bound; the host reports TD_ERR_RANGE and writes no output */
+        if (threadIdx.x == 0) {
+            Q->n = n;
+            Q->Z = s_Z;
+            Q->nnz = n - s_Z;
+            Q->d = 0;
+            Q->k = -1;
+            Q->direct = TD_DIRECT_RANGE;
+            Q->amax = s_amax;
+            for (int c = 0; c < TD_MAXD; ++c) {
+                Q->piv[c] = 0;
+                Q->mx[c] = 0;
+            }
+            Q->nsub = 0;
+            Q->lo = Q->hi = 0;
+            L.qmin[q] = INT_MAX;
+        }
+        return;
+    }
     /* rank and pivot coordinates, exact: incremental elimination over the
      * nonzero points with primitive (gcd-normalised) basis rows. */
     if (threadIdx.x == 0) {
@@ -771,12 +802,8 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
     /* per-coordinate maxima over the projected coordinates, and the sign
      * counts of the single coordinate when d == 1 */
     int lmax[TD_MAXD] = { 0, 0, 0, 0, 0, 0 };
-    int pos = 0, neg = 0, amx = 0;
+    int pos = 0, neg = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        for (int c = 0; c < p; ++c) { /* every coordinate, for the bound below */
-            const int64_t v = (int64_t)X[(int64_t)i * p + c] - s_z[c];
-            amx = max(amx, (int)min(v < 0 ? -v : v, (int64_t)INT_MAX));
-        }
         for (int c = 0; c < d; ++c) {
             int64_t v = (int64_t)X[(int64_t)i * p + s_piv[c]] - s_z[s_piv[c]];
             int64_t a = v < 0 ? -v : v;
@@ -788,7 +815,6 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         }
     }
     for (int c = 0; c < d; ++c) atomicMax(&s_max[c], lmax[c]);
-    atomicMax(&s_amax, amx);
     if (d == 1) {
         atomicAdd(&s_pos, pos);
         atomicAdd(&s_neg, neg);
@@ -800,6 +826,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         Q->Z = Z;
         Q->nnz = n - Z;
         Q->d = d;
+        Q->amax = s_amax;
         for (int c = 0; c < TD_MAXD; ++c) {
             Q->piv[c] = s_piv[c];
             Q->mx[c] = c < d ? s_max[c] : 0;
@@ -832,7 +859,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
      * evenly spaced directions keep it near 1% of the subset loop (none for
      * a loop of fewer than 64 subsets). */
     __syncthreads();
-    if (Q->direct >= 0) return;
+    if (Q->direct >= 0 || L.unseeded) return;
     const int ndir = (int)min((int64_t)n, Q->nsub / 64);
     if (ndir <= 0) return;
     __shared__ int s_ub;
@@ -2170,16 +2197,18 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     int pi, pj, lr[K > 0 ? K : 1];
     td_lane_pair<D>(lane, npc, pi, pj, lr);
     int64_t cof[K > 0 ? K : 1]; /* cofactors of column 0 of this lane's minor, for c[1..K) */
-    /* minors in int32 when K! max|x|^K < 2^31 (max over the coordinates) */
+    /* minors in int32 when K! max|x|^K < 2^31 (max over the coordinates);
+     * max|x| < 2^22 and K <= 4, so the product is formed in int64 with an
+     * early stop once it reaches 2^31 (each factor is below 2^25) */
     bool nm;
     {
-        double mm = 0.0;
+        int64_t mm = 0;
 #pragma unroll
-        for (int r = 0; r < D; ++r) mm = fmax(mm, (double)mxf[r]);
-        double b = 1.0;
+        for (int r = 0; r < D; ++r) mm = max(mm, (int64_t)Q.mx[r]);
+        int64_t b = 1;
 #pragma unroll
-        for (int i = 1; i <= K; ++i) b *= (double)i * mm;
-        nm = b < 2147483647.0;
+        for (int i = 1; i <= K; ++i) b = b < ((int64_t)1 << 31) ? b * (int64_t)i * mm : b;
+        nm = b < 2147483647LL;
     }
     uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
     for (uint32_t r = 0; r < nr; ++r) {
@@ -2585,6 +2614,8 @@ __global__ void td_k_finalize(TdLaunch L)
     int r;
     if (Q.direct >= 0) {
         r = Q.direct;
+    } else if (Q.direct == TD_DIRECT_RANGE) {
+        r = INT_MIN; /* never copied out: the host reports TD_ERR_RANGE */
     } else if (L.qmin[q] == INT_MAX) {
         /* no independent subset in this shard's range */
         r = (L.shard_count > 1) ? INT_MAX : -1;
@@ -2667,15 +2698,30 @@ static td_kfn_plain td_plain_fn(int D)
     }
 }
 
-cudaError_t td_prepare_filtered(int D, size_t smem)
+/* The dynamic shared-memory limit of a kernel is a property of the kernel
+ * on the current device, shared by every context, stream and entry point of
+ * the process.  It is only ever raised: a call that needs less leaves it
+ * where it is, so that a launch another host thread has sized for more is
+ * never invalidated between its own attribute call and its launch. */
+static std::mutex g_attr_mu;
+static std::map<std::pair<int, const void *>, size_t> g_attr_smem;
+
+static cudaError_t td_raise_smem(const void *fn, size_t smem)
 {
-    return cudaFuncSetAttribute(td_filtered_fn(D), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    size_t &cur = g_attr_smem[std::make_pair(dev, fn)];
+    if (smem <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) cur = smem;
+    return e;
 }
 
-cudaError_t td_prepare_plain(int D, size_t smem)
-{
-    return cudaFuncSetAttribute(td_plain_fn(D), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
+cudaError_t td_prepare_filtered(int D, size_t smem) { return td_raise_smem((const void *)td_filtered_fn(D), smem); }
+
+cudaError_t td_prepare_plain(int D, size_t smem) { return td_raise_smem((const void *)td_plain_fn(D), smem); }
 
 cudaError_t td_launch_filtered(int D, const TdLaunch &L, int grid, size_t smem, cudaStream_t s)
 {
@@ -2725,7 +2771,7 @@ int td_adia_occupancy(int D, int nmax, size_t smem)
 {
     int blocks = 0;
     const td_kfn_adia fn = td_adia_fn(D, td_adia_warp_form(nmax));
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (td_raise_smem((const void *)fn, smem) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, TD_ADIA_THREADS, smem) != cudaSuccess) return 0;
     return blocks;
 }
@@ -2759,7 +2805,7 @@ static td_kfn_plain td_critical_fn(int D)
 int td_critical_occupancy(int D, size_t smem)
 {
     int blocks = 0;
-    if (cudaFuncSetAttribute(td_critical_fn(D), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (td_raise_smem((const void *)td_critical_fn(D), smem) != cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, td_critical_fn(D), TD_CRIT_THREADS, smem) != cudaSuccess)
         return 0;

@@ -84,15 +84,14 @@ __global__ void td_k_noalloc_init(TdLaunch L, TdSet set, unsigned long long *sta
     }
 }
 
-/* status[0] = device-side consistency failures, status[1] = queries whose
- * projected coordinates exceed the exact-arithmetic limit */
-__global__ void td_k_noalloc_status(TdLaunch L, int64_t limit, unsigned long long *status)
+/* status[0] = device-side consistency failures, status[1] = queries with a
+ * centred coordinate (any of the p) beyond the exact-arithmetic limit.  The
+ * set-up kernel makes that test before anything else and gives such a query
+ * no subset loop, so no kernel ever computes with its coordinates. */
+__global__ void td_k_noalloc_status(TdLaunch L, unsigned long long *status)
 {
     unsigned long long bad = 0;
-    for (int i = threadIdx.x; i < L.nq; i += blockDim.x) {
-        const TdQuery &Q = L.q[i];
-        for (int c = 0; c < TD_MAXD; ++c) bad += (int64_t)Q.mx[c] > limit ? 1ull : 0ull;
-    }
+    for (int i = threadIdx.x; i < L.nq; i += blockDim.x) bad += L.q[i].direct == TD_DIRECT_RANGE ? 1ull : 0ull;
     if (bad) atomicAdd(&status[1], bad);
     if (threadIdx.x == 0) status[0] = L.ctr->errors;
 }
@@ -189,7 +188,7 @@ extern "C" int td_depth_noalloc(const int32_t *X, int32_t n, int32_t p, const in
         if (td_launch_filtered(D, LD, grid, smemD, s) != cudaSuccess) return TD_ERR_CUDA;
     }
     if (td_launch_finalize(L, s) != cudaSuccess) return TD_ERR_CUDA;
-    td_k_noalloc_status<<<1, 256, 0, s>>>(L, td_coord_limit(p), status);
+    td_k_noalloc_status<<<1, 256, 0, s>>>(L, status);
     if (cudaGetLastError() != cudaSuccess) return TD_ERR_CUDA;
     unsigned long long hs[2] = { 0, 0 };
     if (cudaMemcpyAsync(hs, status, sizeof(hs), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TD_ERR_CUDA;

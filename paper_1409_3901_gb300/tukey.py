@@ -28,8 +28,6 @@ TD_ERR_NOTFOUND = -7
 TD_ERR_INTERNAL = -8
 TD_MAX_P = 6
 TD_ALG_RCOM, TD_ALG_ADIA, TD_ALG_CRITICAL = 0, 1, 2
-TD_ISSUE_FFMA, TD_ISSUE_FFMA2, TD_ISSUE_INT, TD_ISSUE_MIXED = 0, 1, 2, 3
-ISSUE_KINDS = {"ffma": TD_ISSUE_FFMA, "ffma2": TD_ISSUE_FFMA2, "int": TD_ISSUE_INT, "mixed": TD_ISSUE_MIXED}
 TD_MAX_N = 2048
 TD_MODE_FILTERED = 0
 TD_MODE_PLAIN_EXACT = 1
@@ -49,7 +47,7 @@ class td_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("device_pointers", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("subsets_per_warp", ctypes.c_int32),
                 ("buckets_log2", ctypes.c_int32), ("early_exit", ctypes.c_int32),
-                ("algorithm", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("algorithm", ctypes.c_int32), ("unseeded", ctypes.c_int32),
                 ("shard_index", ctypes.c_int64), ("shard_count", ctypes.c_int64),
                 ("stream", ctypes.c_void_p)]
 
@@ -93,7 +91,6 @@ def _load():
         "td_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "td_last_cuda_error": (ctypes.c_char_p, [vp]),
         "td_depth_noalloc": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, vp]),
-        "td_issue_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -119,14 +116,13 @@ td_stream_destroy = lib.td_stream_destroy
 td_strerror = lib.td_strerror
 td_last_cuda_error = lib.td_last_cuda_error
 td_depth_noalloc = lib.td_depth_noalloc
-td_issue_rate = lib.td_issue_rate
 TD_NOALLOC_MAX_N = 512
 TD_NOALLOC_MAX_M = 4096
 
 EXPORTED = ["td_coord_limit", "td_create", "td_set_options", "td_destroy", "td_depth",
             "td_depth_batched", "td_stream_create", "td_stream_submit", "td_stream_poll",
             "td_stream_wait", "td_stream_destroy", "td_strerror", "td_last_cuda_error",
-            "td_depth_noalloc", "td_issue_rate"]
+            "td_depth_noalloc"]
 
 
 def _check(rc, ctx=None):
@@ -139,7 +135,7 @@ def _check(rc, ctx=None):
 
 def options(mode=TD_MODE_FILTERED, device_pointers=False, use_graph=True, subsets_per_warp=0,
             buckets_log2=0, shard_index=0, shard_count=1, stream=None, early_exit=False,
-            algorithm=TD_ALG_RCOM):
+            algorithm=TD_ALG_RCOM, unseeded=False):
     o = td_options()
     o.mode = mode
     o.device_pointers = 1 if device_pointers else 0
@@ -148,18 +144,11 @@ def options(mode=TD_MODE_FILTERED, device_pointers=False, use_graph=True, subset
     o.buckets_log2 = buckets_log2
     o.early_exit = 1 if early_exit else 0
     o.algorithm = algorithm
+    o.unseeded = 1 if unseeded else 0
     o.shard_index = shard_index
     o.shard_count = shard_count
     o.stream = stream
     return o
-
-
-def issue_rate(kind, device=0):
-    """(lane operations per second, launch ms) of td_issue_rate for one kind
-    ("ffma", "ffma2", "int", "mixed")."""
-    rate, ms = ctypes.c_double(), ctypes.c_float()
-    _check(td_issue_rate(device, ISSUE_KINDS[kind], ctypes.byref(rate), ctypes.byref(ms)))
-    return rate.value, ms.value
 
 
 def _host_i32(a):

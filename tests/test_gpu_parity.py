@@ -130,10 +130,12 @@ def test_batched_matches_single(ctx, td):
 
 
 def test_golden_w3_sample_batched(ctx):
+    """Every stored W3S dataset (the cheap ones: C(n,p-2) n <= 6e7) in one
+    batched call, as the batched workload is served."""
     from paper_1409_3901_gb300 import workloads as W
     g = load_golden("W3S")
     sets = W.w3()
-    items = g["items"][:40]
+    items = g["items"]
     batch = []
     for it in items:
         d = sets[it["index"]]
@@ -142,6 +144,86 @@ def test_golden_w3_sample_batched(ctx):
     outs = ctx.depth_batched(batch)
     for it, o in zip(items, outs):
         assert np.array_equal(o, np.array(it["T"]))
+
+
+def test_golden_w3_large_batched(ctx):
+    """The large W3 datasets that W3S leaves out (largest n for p = 4 and 5,
+    and a stratified sample of the rest), their stored queries in one batched
+    call: the long subset loops of the batched workload."""
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W3L")
+    sets = W.w3()
+    batch = []
+    for it in g["items"]:
+        d = sets[it["index"]]
+        assert d.checksum() == it["checksum"]
+        batch.append((d.X, d.Zq[it["queries"]]))
+    outs = ctx.depth_batched(batch)
+    for it, o in zip(g["items"], outs):
+        assert np.array_equal(o, np.array(it["T"])), (it["index"], o.tolist(), it["T"])
+    assert ctx.last_stats.sweeps > 10 ** 8
+
+
+def test_golden_p6_ties(ctx, plain):
+    """p = 6 (K = 4, the deepest subset loop) with duplicates and collinear
+    rows, n = 64 in [-4, 4] and n = 120 in [-127, 127]; filtered form, and
+    the plain exact form on the smaller set."""
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("P6")
+    for it in g["items"]:
+        d = W.ties6(*it["args"])
+        assert d.checksum() == it["checksum"]
+        want = np.array(it["T"])
+        assert np.array_equal(ctx.depth(d.X, d.Zq), want), it["args"]
+        if d.n <= 64:
+            assert np.array_equal(plain.depth(d.X, d.Zq), want)
+
+
+def test_golden_sampled_shards(td):
+    """Where a whole query is too costly for the oracle (p = 6 with ties at
+    n = 300; the costliest p = 5 requests of the stream, n near 1000), sampled
+    ranges of the subset loop: with `unseeded`, shard s of S returns exactly
+    Z + min V(S) over its colex range, stored from the oracle over the same
+    subsets (INT32_MAX for a range without an independent subset)."""
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("SHARDS")
+    data = {}
+    for label, fn in (("ties6 n=300", lambda: W.ties6(63, 300, 60)),):
+        data[label] = fn()
+    w5 = W.w5(count=400)
+    checked = 0
+    for it in g["items"]:
+        label = it["dataset"]
+        if label not in data:
+            data[label] = w5[int(label[3:-1])]
+        d = data[label]
+        assert d.checksum() == it["checksum"]
+        c = td.Context(0, shard_index=it["shard_index"], shard_count=it["shard_count"], unseeded=True)
+        got = int(c.depth(d.X, d.Zq[it["query"]: it["query"] + 1])[0])
+        want = 2 ** 31 - 1 if it["value"] is None else it["value"]
+        assert got == want, (label, it["query"], it["shard_index"], got, want)
+        checked += 1
+    assert checked == len(g["items"]) > 0
+
+
+def test_stream_w5s_all_requests(td):
+    """All 38 stored W5S requests (p = 3 to 6) through td_stream_*, submitted
+    back to back so that they are coalesced into batched launches."""
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W5S")
+    ctx = td.Context(0)
+    s = ctx.stream(mem_budget_bytes=8 << 30)
+    tickets = []
+    for it in g["items"]:
+        d = W.w5_request(4, it["index"])
+        assert d.checksum() == it["checksum"]
+        t = s.submit(d.X, d.Zq)
+        assert t is not None
+        tickets.append((t, it))
+    assert {it["p"] for _, it in tickets} >= {3, 4, 5, 6}
+    for t, it in tickets:
+        out = s.wait(t, timeout_us=120_000_000)
+        assert np.array_equal(out, np.array(it["T"])), it["index"]
 
 
 def test_shards_merge_to_depth(td):
@@ -221,6 +303,29 @@ def test_errors_leave_outputs_untouched(ctx, td):
     with pytest.raises(td.TdError) as e:
         ctx.depth(np.zeros((3, 7), np.int32), np.zeros((1, 7), np.int32))
     assert e.value.code == td.TD_ERR_INVALID
+
+
+def test_device_pointer_range_check_covers_every_coordinate(td):
+    """With device pointers the range is checked on the device, over every
+    centred coordinate -- also one that depends on the others and so is not
+    a pivot coordinate of the set-up's elimination (rank-2 data in p = 3,
+    the third column 400 times the first).  TD_ERR_RANGE, out untouched."""
+    import torch
+    rng = np.random.default_rng(14)
+    c0 = rng.integers(-20000, 20001, size=60)
+    X = np.stack([c0, rng.integers(-50, 51, size=60), 400 * c0], axis=1).astype(np.int32)
+    assert np.abs(X.astype(np.int64)).max() > td.td_coord_limit(3)
+    Z = np.zeros((2, 3), np.int32)
+    with pytest.raises(td.TdError) as e:
+        td.Context(0).depth(X, Z)                    # host pointers: checked on the host
+    assert e.value.code == td.TD_ERR_RANGE
+    for alg in (td.TD_ALG_RCOM, td.TD_ALG_ADIA, td.TD_ALG_CRITICAL):
+        c = td.Context(0, device_pointers=True, algorithm=alg)
+        out = torch.full((2,), -5, dtype=torch.int32, device="cuda")
+        with pytest.raises(td.TdError) as e:
+            c.depth(torch.from_numpy(X).cuda(), torch.from_numpy(Z).cuda(), out)
+        assert e.value.code == td.TD_ERR_RANGE
+        assert (out.cpu().numpy() == -5).all()
 
 
 def test_device_pointers(td):

@@ -2,8 +2,10 @@
 
     python -m paper_1409_3901_gb300.build [--force]
 
-The translation units compile in parallel and are linked into one shared
-library next to this file.  Objects go to ``_build/`` (git-ignored).
+The translation units compile in parallel and are linked into the depth
+library next to this file.  The issue-rate probe that the benchmark uses to
+check its roofline peak is linked separately into libtdprobe.so.  Objects go
+to ``_build/`` (git-ignored).
 """
 import os
 import subprocess
@@ -15,8 +17,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtukeydepth.so")
-SOURCES = ["td_kernels.cu", "td_api.cu", "td_noalloc.cu", "td_issue_rate.cu"]
-HEADERS = ["td_internal.h", "td_exact.cuh", "td_adia.cuh", "td_critical.cuh"]
+PROBE_LIB = os.path.join(HERE, "libtdprobe.so")
+SOURCES = ["td_kernels.cu", "td_api.cu", "td_noalloc.cu"]
+PROBE_SOURCES = ["td_issue_rate.cu"]
+HEADERS = ["td_internal.h", "td_exact.cuh", "td_adia.cuh", "td_critical.cuh", "td_issue_rate.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "550"]
 
@@ -29,11 +33,11 @@ def _nvcc():
 
 
 def _stale():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
-    deps += [os.path.join(ROOT, "include", h) for h in ("tukey_depth.h", "td_issue_rate.h")]
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
+    deps = [os.path.join(CSRC, f) for f in SOURCES + PROBE_SOURCES + HEADERS]
+    deps.append(os.path.join(ROOT, "include", "tukey_depth.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -54,14 +58,15 @@ def build(force=False, verbose=False):
         subprocess.check_call(cmd)
         return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
-    if verbose:
-        print(" ".join(cmd), flush=True)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    with ThreadPoolExecutor(len(SOURCES) + len(PROBE_SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES + PROBE_SOURCES))
+    for lib, part in ((LIB, objs[:len(SOURCES)]), (PROBE_LIB, objs[len(SOURCES):])):
+        tmp = lib + ".%d.tmp" % os.getpid()
+        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + part
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        subprocess.check_call(cmd)
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -1,5 +1,7 @@
 /*
- * td_issue_rate.h -- issue-rate probe exported by libtukeydepth.so.
+ * td_issue_rate.h -- issue-rate probe exported by libtdprobe.so, the small
+ * measurement library that the benchmark loads beside libtukeydepth.so (the
+ * depth library itself does not contain it).
  *
  * The depth sweep (Algorithm 1 with Algorithm 2 inside, Section 3) is bound
  * by plain FP32/INT32 instruction issue, not by memory or tensor cores, so

@@ -64,10 +64,18 @@ def test_null_and_bad_arguments_rejected_without_device(tukey):
     assert tukey.td_stream_create(None, 0, None) == tukey.TD_ERR_INVALID
     done = ctypes.c_int()
     assert tukey.td_stream_poll(None, 1, ctypes.byref(done)) == tukey.TD_ERR_INVALID
+
+
+def test_probe_library_is_separate(tukey):
+    """The issue-rate probe lives in libtdprobe.so, not in the depth library,
+    and rejects bad arguments without a device."""
+    from paper_1409_3901_gb300 import probe
+    assert not hasattr(ctypes.CDLL(tukey.LIB_PATH), "td_issue_rate")
+    lib = probe.lib()
     rate = ctypes.c_double()
-    assert tukey.td_issue_rate(0, 0, None, None) == tukey.TD_ERR_INVALID
-    assert tukey.td_issue_rate(0, 4, ctypes.byref(rate), None) == tukey.TD_ERR_INVALID
-    assert tukey.td_issue_rate(0, -1, ctypes.byref(rate), None) == tukey.TD_ERR_INVALID
+    assert lib.td_issue_rate(0, 0, None, None) == tukey.TD_ERR_INVALID
+    assert lib.td_issue_rate(0, 4, ctypes.byref(rate), None) == tukey.TD_ERR_INVALID
+    assert lib.td_issue_rate(0, -1, ctypes.byref(rate), None) == tukey.TD_ERR_INVALID
 
 
 def test_create_reports_missing_device(tukey):
@@ -78,8 +86,9 @@ def test_create_reports_missing_device(tukey):
     rc = tukey.td_create(ctypes.byref(ptr), 0, None)
     assert rc in (tukey.TD_ERR_CUDA, tukey.TD_ERR_OOM)
     assert not ptr.value
+    from paper_1409_3901_gb300 import probe
     rate = ctypes.c_double()
-    assert tukey.td_issue_rate(0, 0, ctypes.byref(rate), None) == tukey.TD_ERR_CUDA
+    assert probe.lib().td_issue_rate(0, 0, ctypes.byref(rate), None) == tukey.TD_ERR_CUDA
 
 
 def test_structs_match_header_layout(tukey, tmp_path):

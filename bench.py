@@ -46,12 +46,18 @@ def _args():
     ap.add_argument("--plain-queries", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave out the batched (W3) and stream (W5) objects of the default line")
     ap.add_argument("--workload", choices=["W2", "W3", "W4", "W5", "W6", "W7"], default="W2",
                     help="W2 (default) is the benchmark line; W3 (256 datasets, one batched call), "
                          "W4 (p=5 with ties), W5 (request stream with Poisson arrivals), W6 (p=2) "
                          "and W7 (the Section 5.2 shapes, Algorithm 1 against Algorithm 3) print "
                          "their own lines")
     ap.add_argument("--stream-seconds", type=float, default=20.0)
+    ap.add_argument("--profile-case", choices=["rcom", "adia", "critical"], default=None,
+                    help="run the small fixed case that the ncu captures under profiles/ use "
+                         "(two td_depth calls on --profile-queries queries of --workload) and exit")
+    ap.add_argument("--profile-queries", type=int, default=4)
     return ap.parse_args()
 
 
@@ -77,13 +83,15 @@ def _ops_per_sweep(nnz, p):
 
 def _algorithmic_ops(d, sweeps_per_call):
     """Sum over queries of C(n'_q, p-2) * ops(n'_q), scaled to the sweeps the
-    library reports (dependent subsets are skipped)."""
+    library reports (dependent subsets are skipped; None: not scaled)."""
     tot_ops, tot_sw = 0.0, 0.0
     for z in d.Zq:
         nnz = int(d.n - np.all(d.X == z, axis=1).sum())
         sw = math.comb(nnz, d.p - 2)
         tot_ops += sw * _ops_per_sweep(nnz, d.p)
         tot_sw += sw
+    if sweeps_per_call is None or tot_sw == 0:
+        return tot_ops
     return tot_ops * (sweeps_per_call / tot_sw)
 
 
@@ -156,6 +164,96 @@ def _traffic_for_current_kernel():
     except Exception:
         pass
     return None
+
+
+def _batched_w3(tukey, W, dev, stream, flush, peak_tops, steps=1):
+    """The batched workload (256 datasets, p in {3,4,5}, 4096 queries) as one
+    td_depth_batched call with device-resident inputs, timed like `value`
+    (CUDA events on the launch stream, L2 flushed before the call)."""
+    import torch
+    sets = W.w3()
+    ctx = tukey.Context(dev.index, device_pointers=True, stream=stream.cuda_stream)
+    batch = [(torch.from_numpy(d.X).to(dev), torch.from_numpy(d.Zq).to(dev)) for d in sets]
+    ctx.depth_batched(batch)                           # warm-up (also captures the graph)
+    ms, ms_sweep, sw = 0.0, 0.0, 0
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.depth_batched(batch)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms += e0.elapsed_time(e1)
+        ms_sweep += ctx.last_stats.ms_sweep
+        sw += ctx.last_stats.sweeps
+    ops = sum(_algorithmic_ops(d, None) for d in sets) * steps
+    nq = sum(d.m for d in sets)
+    achieved = ops / (ms_sweep / 1e3) / 1e12
+    return {"workload": "W3: 256 datasets, p in {3,4,5}, n log-uniform in [100,2000] capped at "
+                        "C(n,p-2)*n <= 4e9, 16 queries each; one td_depth_batched call",
+            "datasets": len(sets), "queries": nq, "steps": steps,
+            "sweeps_per_s": sw / (ms / 1e3), "queries_per_s": nq * steps / (ms / 1e3),
+            "ms_per_call": ms / steps, "kernel_ms": ms_sweep / steps, "sweeps_per_call": sw // steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                         "frac": achieved / peak_tops, "kernel": "td_k_filtered<3..5>"},
+            "timing": "CUDA events on the launch stream around the call; L2 flushed before it"}
+
+
+def _stream_w5(tukey, W, dev, seconds, count=64):
+    """The request stream: the first `count` requests of the W5 stream (no
+    cost filter: p = 5 requests reach n = 1000, C(1000,3) subsets a query),
+    cycled, arriving Poisson at 70% of the back-to-back rate measured on the
+    same requests; latency from arrival to completion, split by p."""
+    import random
+    from math import comb
+    reqs = W.w5(count=count)
+    ctx = tukey.Context(dev.index)
+    s = ctx.stream(mem_budget_bytes=8 << 30)
+    t0 = time.perf_counter()
+    for tk in [s.submit(d.X, d.Zq) for d in reqs]:
+        s.wait(tk)
+    rate = len(reqs) / (time.perf_counter() - t0)
+    lam = 0.7 * rate
+    rnd = random.Random(5)
+    lat, done_sweeps, refused = [], 0, 0
+    t_start = time.perf_counter()
+    next_t = t_start
+    pending, k = [], 0
+    while time.perf_counter() - t_start < seconds or pending:
+        now = time.perf_counter()
+        if now >= next_t and now - t_start < seconds:
+            d = reqs[k % len(reqs)]
+            k += 1
+            tk = s.submit(d.X, d.Zq)
+            if tk is not None:
+                pending.append((tk, next_t, d))
+            else:
+                refused += 1
+            next_t += rnd.expovariate(lam)
+        still = []
+        for tk, ta, d in pending:
+            if s.poll(tk) is not None:
+                lat.append((time.perf_counter() - ta, d.p))
+                done_sweeps += comb(d.n, d.p - 2) * d.m
+            else:
+                still.append((tk, ta, d))
+        pending = still
+        time.sleep(0.0002)
+    el = time.perf_counter() - t_start
+
+    def pct(v):
+        v = sorted(v)
+        return {"p50_ms": 1e3 * v[len(v) // 2], "p99_ms": 1e3 * v[min(len(v) - 1, int(0.99 * len(v)))],
+                "requests": len(v)} if v else None
+    by_p = {str(p): pct([t for t, pp in lat if pp == p]) for p in (3, 4, 5, 6)}
+    out = {"workload": "W5: the first %d requests of the stream (p in {3,4,5,6}, n in [50,1000], "
+                       "p=6 n<=120, 1-64 queries), cycled, Poisson arrivals" % count,
+           "arrival_rate_per_s": lam, "calibrated_rate_per_s": rate, "seconds": el,
+           "throughput_requests_per_s": len(lat) / el, "throughput_sweeps_per_s": done_sweeps / el,
+           "refused": refused, "dropped_from_sample": 0, "by_p": by_p}
+    out.update(pct([t for t, _ in lat]))
+    return out
 
 
 def _cpu_baseline(d, seconds):
@@ -369,7 +467,8 @@ def run_ours(a):
                               % (props.multi_processor_count, sm_max, kind),
                 "ops_per_sweep": "n'(2p+6+2ceil(log2 n'))"}
     # the derived peak checked by measurement (after the timed region)
-    measured = {k: tukey.issue_rate(k, local)[0] / 1e12 for k in tukey.ISSUE_KINDS}
+    from paper_1409_3901_gb300 import probe
+    measured = {k: probe.issue_rate(k, local)[0] / 1e12 for k in probe.ISSUE_KINDS}
     measured["unit"] = "Tops/s"
     measured["note"] = ("td_issue_rate: independent chains over one full wave of blocks; "
                         "lane operations counted in the source (FMA = 1, f32x2 FMA = 2)")
@@ -387,6 +486,10 @@ def run_ours(a):
             "adia": adia_line,
             "stats_per_step": {k: v for k, v in ctx.last_stats.as_dict().items()},
             "clocks": clk}
+    if not a.no_extra:
+        from paper_1409_3901_gb300 import workloads as W
+        line["batched"] = _batched_w3(tukey, W, dev, stream, flush, peak_tops)
+        line["stream"] = _stream_w5(tukey, W, dev, a.stream_seconds)
     if not a.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(d, a.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -550,8 +653,41 @@ def run_w7(a, tukey, W):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(a):
+    """A small, fixed case for ncu: td_depth twice on a few queries of a
+    workload (the first call captures the CUDA graph, the second is the one to
+    profile).  Launch order of one call:
+
+    - rcom (Algorithm 1): set-up, tiles, td_k_filtered<2> .. <p>, finalize; at
+      p = 4 `-k regex:td_k_filtered -s 5 -c 1` selects the second call's
+      p = 4 sweep kernel, at p = 5 `-s 7`;
+    - adia (Algorithm 3): the search kernels td_k_adia<3> .. <p> come before
+      the sweep, so at p = 4 `-k regex:td_k_adia -s 3 -c 1` selects the second
+      call's p = 4 search;
+    - critical (Proposition 1, r = p - 1): one td_k_critical launch per query
+      and call, so with one query `-k regex:td_k_critical -s 1 -c 1` selects
+      the second call's.
+
+    Every ncu command on a shared GPU takes `--clock-control none`."""
+    from paper_1409_3901_gb300 import tukey, workloads as W
+    workload = "W2" if a.workload in ("W3", "W5", "W7") else a.workload
+    d = W.WORKLOADS[workload]()
+    nq = a.profile_queries
+    pick = [0, 40, 50, 63] if nq == 4 and d.m == 64 else list(range(0, d.m, max(1, d.m // nq)))[:nq]
+    Z = d.Zq[pick]
+    alg = {"rcom": tukey.TD_ALG_RCOM, "adia": tukey.TD_ALG_ADIA, "critical": tukey.TD_ALG_CRITICAL}[a.profile_case]
+    ctx = tukey.Context(0, algorithm=alg)
+    ctx.depth(d.X, Z)
+    out = ctx.depth(d.X, Z)
+    print(json.dumps({"profile_case": a.profile_case, "workload": workload, "queries": pick,
+                      "out": out.tolist(), "stats": ctx.last_stats.as_dict()}), flush=True)
+
+
 def main():
     a = _args()
+    if a.profile_case:
+        run_profile_case(a)
+        return
     if a.warmup < 3:
         a.warmup = 3
     if a.impl == "reference":

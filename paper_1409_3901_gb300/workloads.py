@@ -258,6 +258,37 @@ def w6(seed=5, m=16384):
                    "W6 p=2 n=2000 gaussian x40, %d queries" % m)
 
 
+def ties6(seed, n, lim, queries=4):
+    """p = 6 with ties, for the largest subset size of Algorithm 1 (K = 4):
+    uniform integers in [-lim, lim], then a tenth of the rows overwritten by
+    copies of other rows and up to five rows placed on the line through two
+    data rows (integer steps that stay inside the box); queries: half data
+    rows (a copied one first), half uniform points of the bounding box."""
+    st = Stream(seed, sub=11)
+    p = 6
+    X = st.integers(-lim, lim, n * p).reshape(n, p).astype(np.int64)
+    k = max(1, n // 10)
+    src = st.integers(0, n - 1, k)
+    dst = st.integers(0, n - 1, k)
+    X[dst] = X[src]
+    a, b = X[0].copy(), X[1].copy()
+    step = b - a
+    placed = 0
+    for t in range(2, 40):
+        if placed == 5:
+            break
+        v = a + t * step // 8 if t % 2 else a - t * step // 8
+        if np.all(np.abs(v) <= lim):
+            X[2 + placed] = v
+            placed += 1
+    X = X.astype(np.int32)
+    h = queries // 2
+    rows = np.vstack([X[dst[:1]], X[st.choice(n, h - 1)]]) if h > 0 else np.zeros((0, p), np.int32)
+    unif = _bbox_uniform(st, X, queries - h)
+    return Dataset(X, np.vstack([rows, unif]).astype(np.int32), "ties6 n=%d lim=%d" % (n, lim),
+                   {"seed": seed, "n": n, "lim": lim})
+
+
 W7_SHAPES = ((3, 1280), (4, 640), (5, 160), (6, 80))
 W7_ALPHAS = (0.0, 0.4, 0.8, 1.2)
 

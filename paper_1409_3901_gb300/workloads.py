@@ -262,8 +262,11 @@ def ties6(seed, n, lim, queries=4):
     """p = 6 with ties, for the largest subset size of Algorithm 1 (K = 4):
     uniform integers in [-lim, lim], then a tenth of the rows overwritten by
     copies of other rows and up to five rows placed on the line through two
-    data rows (integer steps that stay inside the box); queries: half data
-    rows (a copied one first), half uniform points of the bounding box."""
+    data rows (integer steps that stay inside the box); queries: a copied
+    data row, another data row, the lower coordinate-wise median, then
+    uniform points of the middle half of the bounding box (deep and shallow
+    points alike; uniform points of the whole box are mostly outside the
+    hull at p = 6)."""
     st = Stream(seed, sub=11)
     p = 6
     X = st.integers(-lim, lim, n * p).reshape(n, p).astype(np.int64)
@@ -282,11 +285,13 @@ def ties6(seed, n, lim, queries=4):
             X[2 + placed] = v
             placed += 1
     X = X.astype(np.int32)
-    h = queries // 2
-    rows = np.vstack([X[dst[:1]], X[st.choice(n, h - 1)]]) if h > 0 else np.zeros((0, p), np.int32)
-    unif = _bbox_uniform(st, X, queries - h)
-    return Dataset(X, np.vstack([rows, unif]).astype(np.int32), "ties6 n=%d lim=%d" % (n, lim),
-                   {"seed": seed, "n": n, "lim": lim})
+    med = np.sort(X, axis=0)[n // 2 - 1][None, :]
+    mid = (X.min(axis=0).astype(np.int64) + X.max(axis=0)) // 2
+    quarter = (X.max(axis=0).astype(np.int64) - X.min(axis=0)) // 4
+    centre = np.stack([st.integers(int(mid[c] - quarter[c]), int(mid[c] + quarter[c]), max(0, queries - 3))
+                       for c in range(p)], axis=1)
+    Zq = np.vstack([X[dst[:1]], X[st.choice(n, 1)], med, centre])[:queries].astype(np.int32)
+    return Dataset(X, Zq, "ties6 n=%d lim=%d" % (n, lim), {"seed": seed, "n": n, "lim": lim})
 
 
 W7_SHAPES = ((3, 1280), (4, 640), (5, 160), (6, 80))

@@ -40,6 +40,10 @@ L2_FLUSH_BYTES = 512 << 20
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--scaling", choices=["strong", "weak"], default="strong",
+                    help="with several ranks: strong (default) -- every rank sweeps its shard of the "
+                         "same workload and an all-reduce MIN merges the depths inside each step; "
+                         "weak -- every rank solves a batch of its own")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -68,11 +72,23 @@ def _dist():
     return ws, rank, local
 
 
-def _workload(rank):
+def _workload(rank, strong):
     from paper_1409_3901_gb300 import workloads as W
-    # weak scaling: rank r solves its own batch (seed 1 + r); rank 0 is the
-    # benchmark workload itself
-    return W.w2(seed=1 + rank)
+    # strong scaling: every rank holds the benchmark workload and sweeps its
+    # own shard of each query's subset loop; weak scaling: rank r solves its
+    # own batch (seed 1 + r), rank 0 the benchmark workload itself
+    return W.w2(seed=1 if strong else 1 + rank)
+
+
+def _golden_w2():
+    """The stored oracle counts of the benchmark workload, if present."""
+    path = os.path.join(ROOT, "tests", "golden", "W2.json")
+    try:
+        with open(path) as f:
+            g = json.load(f)
+        return g["checksum"], np.array(g["T"], dtype=np.int64)
+    except Exception:
+        return None, None
 
 
 def _ops_per_sweep(nnz, p):
@@ -200,6 +216,54 @@ def _batched_w3(tukey, W, dev, stream, flush, peak_tops, steps=1):
             "timing": "CUDA events on the launch stream around the call; L2 flushed before it"}
 
 
+def _tuning(tukey, W, dev, stream, flush, w2_default_ms, w3_default_ms):
+    """The autotuner on the two batched forms: a context tuned by td_autotune
+    for every (dimension, octave of n) the workload holds, timed like the
+    untuned line (CUDA events on the launch stream, L2 flushed first)."""
+    import torch
+
+    def timed(ctx, fn, steps):
+        fn()
+        ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms += e0.elapsed_time(e1)
+        return ms / steps
+
+    out = {}
+    d2 = W.w2()
+    c2 = tukey.Context(dev.index, device_pointers=True, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    r2 = c2.autotune(4, d2.n)
+    tune_s = time.perf_counter() - t0
+    X2, Z2 = torch.from_numpy(d2.X).to(dev), torch.from_numpy(d2.Zq).to(dev)
+    o2 = torch.empty(d2.m, dtype=torch.int32, device=dev)
+    out["W2"] = {"default_ms": w2_default_ms, "tuned_ms": timed(c2, lambda: c2.depth(X2, Z2, o2), 5),
+                 "choice": {"p4_oct%d" % math.ceil(math.log2(d2.n)): r2["best_spw"]}, "tune_seconds": tune_s,
+                 "candidates_ms": r2["candidates"], "size_rule_ms": r2["ms_default"]}
+    sets = W.w3()
+    c3 = tukey.Context(dev.index, device_pointers=True, stream=stream.cuda_stream)
+    choice = {}
+    t0 = time.perf_counter()
+    for p in sorted({d.p for d in sets}):
+        for oc in sorted({math.ceil(math.log2(d.n)) for d in sets if d.p == p}):
+            n = max(p + 2, min(2048, int(0.75 * 2 ** oc)))
+            choice["p%d_oct%d" % (p, oc)] = c3.autotune(p, n)["best_spw"]
+    tune_s = time.perf_counter() - t0
+    batch = [(torch.from_numpy(d.X).to(dev), torch.from_numpy(d.Zq).to(dev)) for d in sets]
+    out["W3"] = {"default_ms": w3_default_ms, "tuned_ms": timed(c3, lambda: c3.depth_batched(batch), 1),
+                 "choice": choice, "tune_seconds": tune_s}
+    out["note"] = ("td_autotune per (dimension, octave of n) on seeded synthetic data; best_spw 0 = the "
+                   "size rule; times of one call like value / batched")
+    return out
+
+
 def _stream_w5(tukey, W, dev, seconds, count=64):
     """The request stream: the first `count` requests of the W5 stream (no
     cost filter: p = 5 requests reach n = 1000, C(1000,3) subsets a query),
@@ -319,16 +383,24 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     from paper_1409_3901_gb300 import tukey
 
-    d = _workload(rank)
+    strong = ws > 1 and a.scaling == "strong"
+    d = _workload(rank, strong)
     stream = torch.cuda.current_stream(dev)
-    ctx = tukey.Context(local, device_pointers=True, stream=stream.cuda_stream)
+    shard = {"shard_index": rank, "shard_count": ws} if strong else {}
+    ctx = tukey.Context(local, device_pointers=True, stream=stream.cuda_stream, **shard)
     Xd = torch.from_numpy(d.X).to(dev)
     Zd = torch.from_numpy(d.Zq).to(dev)
     out = torch.empty(d.m, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
-    for _ in range(a.warmup):
+    def step():
         ctx.depth(Xd, Zd, out)
+        if strong:
+            # the exchange step of the sharded subset loop: MIN over the ranks
+            dist.all_reduce(out, op=dist.ReduceOp.MIN)
+
+    for _ in range(a.warmup):
+        step()
     torch.cuda.synchronize(dev)
     if ws > 1:
         dist.barrier()
@@ -343,7 +415,7 @@ def run_ours(a):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.depth(Xd, Zd, out)
+        step()
         e1.record(stream)
         evs.append((e0, e1))
         st = ctx.last_stats
@@ -364,21 +436,48 @@ def run_ours(a):
     else:
         sweeps_all = float(sweeps)
     value = sweeps_all / t_total
-    queries_per_s = ws * d.m * a.steps / t_total
+    queries_per_s = (1 if strong else ws) * d.m * a.steps / t_total
+    check = None
+    if strong:
+        ck, want = _golden_w2()
+        if want is not None and ck == d.checksum():
+            check = bool(np.array_equal(out.cpu().numpy().astype(np.int64), want))
 
-    # end to end through the public API with host buffers (copies inside)
-    host = tukey.Context(local, stream=stream.cuda_stream)
-    host.depth(d.X, d.Zq)
+    # end to end through the public API with host buffers (copies inside;
+    # with shards, the merged depths go through the MIN all-reduce)
+    host = tukey.Context(local, stream=stream.cuda_stream, **shard)
+
+    def e2e_step():
+        o = host.depth(d.X, d.Zq)
+        if strong:
+            t_ = torch.from_numpy(o).to(dev)
+            dist.all_reduce(t_, op=dist.ReduceOp.MIN)
+            o = t_.cpu().numpy()
+        return o
+
+    e2e_step()
     e2e_steps = max(3, min(a.steps, 5))
     torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
     t = time.perf_counter()
     e2e_sweeps = 0
     for _ in range(e2e_steps):
-        o = host.depth(d.X, d.Zq)
+        o = e2e_step()
         e2e_sweeps += host.last_stats.sweeps
     e2e_t = time.perf_counter() - t
+    if ws > 1:
+        et = torch.tensor([e2e_t, float(e2e_sweeps)], device=dev, dtype=torch.float64)
+        mx = et[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(et, op=dist.ReduceOp.SUM)
+        e2e_t, e2e_sweeps = float(mx.item()), float(et[1].item())
     e2e = {"value": e2e_sweeps / e2e_t, "unit": UNIT,
            "h2d_bytes_per_step": int(d.X.nbytes + d.Zq.nbytes), "d2h_bytes_per_step": int(o.nbytes)}
+    if rank != 0 and ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+        return
 
     # the plain exact one-query-per-launch form on the same GPU
     plain = tukey.Context(local, mode=tukey.TD_MODE_PLAIN_EXACT, device_pointers=True,
@@ -446,12 +545,6 @@ def run_ours(a):
                   "note": "td_options.early_exit: data-direction upper bound (Algorithm 3 Step 2) "
                           "seeds each query's minimum; a query stops at V = 0. Not the full-sweep metric."}
 
-    if rank != 0:
-        if ws > 1:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
-
     peaks, kind = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(dev)
@@ -475,9 +568,12 @@ def run_ours(a):
     roofline["issue_rate_measured"] = measured
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * t_total / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64/i128", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": d.m * ws, "seq_len": None,
-                       "parallelism": "dp%d" % ws, "l2": "flushed between steps (512 MB write)"},
+            "scaling": "strong" if strong else "weak", "vs_baseline": None, "dtype": "f32+i64/i128",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": d.m * (1 if strong else ws), "seq_len": None,
+                       "parallelism": ("subset-shards%d+allreduce-min" % ws) if strong else "dp%d" % ws,
+                       "l2": "flushed between steps (512 MB write)"},
+            "merged_depths_match_oracle": check,
             "queries_per_s": queries_per_s,
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
             "plain_exact": {"value": plain_rate, "unit": UNIT, "queries": int(Zp.shape[0]),
@@ -489,6 +585,8 @@ def run_ours(a):
     if not a.no_extra:
         from paper_1409_3901_gb300 import workloads as W
         line["batched"] = _batched_w3(tukey, W, dev, stream, flush, peak_tops)
+        line["tuning"] = _tuning(tukey, W, dev, stream, flush, 1e3 * t_total / a.steps,
+                                 line["batched"]["ms_per_call"])
         line["stream"] = _stream_w5(tukey, W, dev, a.stream_seconds)
     if not a.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(d, a.cpu_seconds)

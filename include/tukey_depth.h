@@ -100,8 +100,12 @@ typedef struct {
     int32_t device_pointers;  /* nonzero: X, Z, out are device pointers */
     int32_t use_graph;        /* nonzero (default): replay the launch sequence of a batched call
                                  from a captured CUDA graph when the shapes repeat */
-    int32_t subsets_per_warp; /* work-tile size (subsets per warp per tile); 0 = autotuned */
-    int32_t buckets_log2;     /* angular buckets per sweep = 2^buckets_log2; 0 = autotuned */
+    int32_t subsets_per_warp; /* work-tile size (subsets per warp per tile); 0 = the value td_autotune
+                                 (or td_set_tuned) stored in the context for the query's effective
+                                 dimension and octave of its nonzero point count, else a size rule
+                                 (about 2^16 point evaluations per warp and tile, 4 to 256) */
+    int32_t buckets_log2;     /* angular buckets of the rare exact path = 2^buckets_log2; 0 = about
+                                 one per two points (7 to 11); measured to make no difference */
     int32_t early_exit;       /* nonzero: filtered mode stops sweeping a query once its running
                                  minimum of V(S) reaches 0, the least value (then T = Z).  The
                                  running minimum always starts at the upper bound of data
@@ -207,6 +211,35 @@ int td_stream_poll(td_stream *s, uint64_t ticket, int *done);
  * the request stays in flight).  timeout_us < 0 waits without limit. */
 int td_stream_wait(td_stream *s, uint64_t ticket, int64_t timeout_us);
 int td_stream_destroy(td_stream *s);
+
+/* Autotuner (no counterpart in the paper: the choice of work-tile size of
+ * the persistent sweep).  Times the filtered sweep kernel of dimension p on a
+ * seeded synthetic dataset of n points (uniform integers in [-127, 127]) with
+ * enough queries for a few milliseconds of sweeping, first with the size rule
+ * and then with each candidate work-tile size (8 to 256 subsets per warp), the
+ * median of three calls each (td_stats.ms_sweep), and keeps the fastest in the
+ * context for queries of effective dimension p whose nonzero point count lies
+ * in the octave of n (ceil(log2 n), and that of n - 1); later calls with
+ * subsets_per_warp = 0 use it.  The results never depend on the choice.
+ * res (may be NULL) receives the candidates, their times and the choice
+ * (best_spw = 0: the size rule was fastest).  Runs synchronously on the
+ * context's stream; the context's options are unchanged on return.  Limits:
+ * 3 <= p <= TD_MAX_P, p < n <= TD_MAX_N (TD_ERR_INVALID). */
+#define TD_TUNE_MAX 8
+typedef struct {
+    int32_t p, n, queries, candidates;
+    int32_t spw[TD_TUNE_MAX]; /* candidate subsets per warp */
+    float ms[TD_TUNE_MAX];    /* their sweep-kernel times (ms, median of three calls) */
+    float ms_default;         /* the size rule's time */
+    int32_t best_spw;         /* the choice stored in the context (0 = the size rule) */
+    float best_ms;
+} td_tune_result;
+int td_autotune(td_ctx *ctx, int32_t p, int32_t n, td_tune_result *res);
+
+/* Store a work-tile size for effective dimension d (2..6) and octave
+ * (0..11: queries with 2^(octave-1) < nonzero points <= 2^octave), e.g. one
+ * that td_autotune chose in an earlier process; 0 restores the size rule. */
+int td_set_tuned(td_ctx *ctx, int32_t d, int32_t octave, int32_t subsets_per_warp);
 
 /* Allocation-free depth (no counterpart in the paper; a deployment need).
  * For callers that must not allocate device memory: code running under a

@@ -531,7 +531,7 @@ template <int D, bool WARP>
 __global__ void __launch_bounds__(TD_ADIA_THREADS, 1) td_k_adia(TdLaunch L)
 {
     constexpr int K = D - 2, K1 = D - 1;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_tmp[32], s_w[32], s_res[4];
     __shared__ int s_node[TD_MAXD], s_S[TD_MAXD], s_V[TD_MAXD];
     __shared__ int s_d0, s_ns, s_done, s_fail, s_improved, s_pick, s_nk;

@@ -100,6 +100,7 @@ struct Work {
 
 struct GraphKey {
     int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw, early_exit, algorithm, unseeded;
+    uint16_t spw_tab[TD_NDIM][TD_NOCT];
     size_t smem;
     const void *ptrs[17];
     int64_t shard_index, shard_count;
@@ -121,6 +122,7 @@ struct td_ctx {
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey;
     bool gvalid = false;
+    uint16_t tune[TD_NDIM][TD_NOCT] = {}; /* td_autotune: subsets per warp by dimension and octave */
 };
 
 /* one request of a stream: a copy of its inputs until its batch runs */
@@ -379,10 +381,11 @@ int stage_inputs(td_ctx *ctx, Work &w, HostBuf &stage, const Plan &P, const td_d
 }
 
 TdLaunch make_launch(const Work &w, const Plan &P, const int32_t *x_arena, const td_options &o, int warps,
-                     int blog2)
+                     int blog2, const uint16_t (*tune)[TD_NOCT])
 {
     TdLaunch L;
     memset(&L, 0, sizeof(L));
+    if (tune) memcpy(L.spw_tab, tune, sizeof(L.spw_tab));
     L.X = x_arena;
     L.Zq = (const int32_t *)w.Zq.p;
     L.sets = (const TdSet *)w.sets.p;
@@ -620,7 +623,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     int rc = stage_inputs(ctx, ctx->w, ctx->hstage, P, sets, k, devptr, s, &x_arena);
     if (rc != TD_OK) return rc;
     TDCK(cudaMemsetAsync(ctx->w.ctr.p, 0, sizeof(TdCounters), s));
-    TdLaunch L = make_launch(ctx->w, P, x_arena, o, kWarpsFiltered, blog2);
+    TdLaunch L = make_launch(ctx->w, P, x_arena, o, kWarpsFiltered, blog2, ctx->tune);
     TDCK(cudaEventRecord(ctx->ev0, s));
     int launches = 0;
     if (o.mode == TD_MODE_FILTERED && o.use_graph && o.algorithm != TD_ALG_CRITICAL) {
@@ -636,6 +639,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         key.spw = o.subsets_per_warp;
         key.early_exit = L.early_exit;
         key.unseeded = L.unseeded;
+        memcpy(key.spw_tab, L.spw_tab, sizeof(key.spw_tab));
         key.algorithm = o.algorithm;
         key.smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
         const Work &cw = ctx->w;
@@ -852,6 +856,132 @@ extern "C" int td_depth_batched(td_ctx *ctx, const td_dataset *sets, int32_t k, 
 }
 
 /* ----------------------------------------------------------------------- */
+/* autotuner                                                                */
+/* ----------------------------------------------------------------------- */
+
+namespace {
+
+/* candidates of the work-tile size (subsets per warp) */
+const int kTuneSpw[TD_TUNE_MAX] = { 8, 16, 32, 64, 128, 256, 0, 0 };
+const int kTuneCount = 6;
+
+/* A seeded synthetic dataset of n points in dimension p, uniform integers in
+ * [-127, 127] (a 64-bit xorshift generator), and m queries: data rows and
+ * uniform points alternately. */
+void tune_data(int n, int p, int m, std::vector<int32_t> &X, std::vector<int32_t> &Z)
+{
+    uint64_t x = 0x9E3779B97F4A7C15ull ^ ((uint64_t)n << 8) ^ (uint64_t)p;
+    auto next = [&]() {
+        x ^= x << 13;
+        x ^= x >> 7;
+        x ^= x << 17;
+        return (int32_t)((x >> 11) % 255) - 127;
+    };
+    X.resize((size_t)n * p);
+    for (auto &v : X) v = next();
+    Z.resize((size_t)m * p);
+    for (int q = 0; q < m; ++q)
+        for (int c = 0; c < p; ++c) Z[(size_t)q * p + c] = (q & 1) ? next() : X[(size_t)((q * 7919) % n) * p + c];
+}
+
+/* Median device time of the sweep kernels over three calls (one untimed
+ * call first, which also captures the graph). */
+int tune_time(td_ctx *ctx, const td_dataset &d, float *ms)
+{
+    float t[3];
+    td_stats st;
+    int rc = run_batch(ctx, &d, 1, &st);
+    for (int r = 0; r < 3 && rc == TD_OK; ++r) {
+        rc = run_batch(ctx, &d, 1, &st);
+        t[r] = st.ms_sweep;
+    }
+    if (rc != TD_OK) return rc;
+    std::sort(t, t + 3);
+    *ms = t[1];
+    return TD_OK;
+}
+
+}  // namespace
+
+extern "C" int td_autotune(td_ctx *ctx, int32_t p, int32_t n, td_tune_result *res)
+{
+    if (!ctx || p < 3 || p > TD_MAX_P || n < p + 1 || n > TD_MAX_N) return TD_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    /* queries enough for a few milliseconds of sweeping: about 3e9 point
+     * evaluations (C(n, p-2) n each) */
+    double cost = (double)n;
+    for (int i = 0; i < p - 2; ++i) cost *= (double)(n - i) / (i + 1);
+    const int m = (int)std::max(1.0, std::min(64.0, 3e9 / cost));
+    std::vector<int32_t> X, Z, out((size_t)m);
+    tune_data(n, p, m, X, Z);
+    td_dataset d;
+    d.n = n;
+    d.p = p;
+    d.X = X.data();
+    d.m = m;
+    d.Z = Z.data();
+    d.out = out.data();
+    const td_options saved = ctx->opt;
+    uint16_t saved_tab[TD_NDIM][TD_NOCT];
+    memcpy(saved_tab, ctx->tune, sizeof(saved_tab));
+    td_options o = saved;
+    o.mode = TD_MODE_FILTERED;
+    o.device_pointers = 0;
+    o.early_exit = 0;
+    o.algorithm = TD_ALG_RCOM;
+    o.unseeded = 0;
+    o.shard_index = 0;
+    o.shard_count = 1;
+    o.buckets_log2 = 0;
+    ctx->opt = o;
+    const int D = p, oct = td_octave(n), oct1 = td_octave(n - 1);
+    td_tune_result r;
+    memset(&r, 0, sizeof(r));
+    r.p = p;
+    r.n = n;
+    r.queries = m;
+    int rc = TD_OK;
+    /* the size rule (no table entry, subsets_per_warp = 0) first */
+    ctx->tune[D - 2][oct] = ctx->tune[D - 2][oct1] = 0;
+    ctx->opt.subsets_per_warp = 0;
+    rc = tune_time(ctx, d, &r.ms_default);
+    r.best_ms = r.ms_default;
+    r.best_spw = 0;
+    for (int k = 0; k < kTuneCount && rc == TD_OK; ++k) {
+        ctx->opt.subsets_per_warp = kTuneSpw[k];
+        float ms = 0.f;
+        rc = tune_time(ctx, d, &ms);
+        r.spw[k] = kTuneSpw[k];
+        r.ms[k] = ms;
+        if (rc == TD_OK && ms < r.best_ms) {
+            r.best_ms = ms;
+            r.best_spw = kTuneSpw[k];
+        }
+    }
+    r.candidates = kTuneCount;
+    ctx->opt = saved;
+    memcpy(ctx->tune, saved_tab, sizeof(saved_tab));
+    if (rc != TD_OK) return rc;
+    /* the fastest, kept for rows of this dimension and octave (0: the size
+     * rule was fastest) */
+    ctx->tune[D - 2][oct] = (uint16_t)r.best_spw;
+    ctx->tune[D - 2][oct1] = (uint16_t)r.best_spw;
+    ctx->gvalid = false;
+    if (res) *res = r;
+    return TD_OK;
+}
+
+extern "C" int td_set_tuned(td_ctx *ctx, int32_t d, int32_t octave, int32_t subsets_per_warp)
+{
+    if (!ctx || d < 2 || d > 6 || octave < 0 || octave >= TD_NOCT || subsets_per_warp < 0 ||
+        subsets_per_warp > 4096)
+        return TD_ERR_INVALID;
+    ctx->tune[d - 2][octave] = (uint16_t)subsets_per_warp;
+    ctx->gvalid = false;
+    return TD_OK;
+}
+
+/* ----------------------------------------------------------------------- */
 /* stream API                                                               */
 /* ----------------------------------------------------------------------- */
 
@@ -940,7 +1070,7 @@ int pump(td_stream *s)
     const int32_t *x_arena = nullptr;
     int rc = stage_inputs(ctx, sl.w, sl.hstage, P, sets.data(), (int)sets.size(), false, s->s, &x_arena);
     if (rc != TD_OK) return rc;
-    TdLaunch L = make_launch(sl.w, P, x_arena, o, kWarpsFiltered, blog2);
+    TdLaunch L = make_launch(sl.w, P, x_arena, o, kWarpsFiltered, blog2, ctx->tune);
     L.scratch = (char *)s->scratch.p;
     TDCK(cudaMemsetAsync(sl.w.ctr.p, 0, sizeof(TdCounters), s->s));
     int nl = 0;

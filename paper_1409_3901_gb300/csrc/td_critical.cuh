@@ -118,7 +118,7 @@ __device__ void td_warp_critical(const int32_t *xi, int PSI, int nnz, uint64_t r
 template <int D>
 __global__ void __launch_bounds__(TD_CRIT_THREADS, 1) td_k_critical(TdLaunch L, int q)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_tmp[32];
     __shared__ int s_best[TD_CRIT_THREADS / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;

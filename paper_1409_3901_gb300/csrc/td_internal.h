@@ -9,6 +9,15 @@
 #define TD_NDIM 5            /* effective dimensions 2..6 with a subset loop */
 #define TD_TICKET_STRIDE 16  /* work counters 128 bytes apart */
 #define TD_DIRECT_RANGE (-2) /* TdQuery.direct of a query whose centred coordinates exceed the limit */
+#define TD_NOCT 12           /* octaves of the nonzero point count: ceil(log2 nnz) in [0, 11] */
+
+/* octave of a row of nnz nonzero points (1 <= nnz <= 2048): ceil(log2 nnz) */
+static inline __host__ __device__ int td_octave(int nnz)
+{
+    int b = 0;
+    while (b < TD_NOCT - 1 && (1 << b) < nnz) ++b;
+    return b;
+}
 
 /* Largest |X_ij - z_j| (every coordinate) the kernels accept for dimension p:
  * it keeps every exact intermediate in 64-bit (coordinates, minors,
@@ -75,7 +84,8 @@ struct TdLaunch {
     int32_t *out;            /* per-query output */
     TdCounters *ctr;
     int64_t shard_index, shard_count;
-    int32_t spw;             /* subsets per warp per tile (0 = by size) */
+    int32_t spw;             /* subsets per warp per tile (0 = the tuned table, else by size) */
+    uint16_t spw_tab[TD_NDIM][TD_NOCT]; /* tuned subsets per warp by dimension and octave (0 = by size) */
     int32_t blog2;           /* angular buckets log2 (0 = by size) */
     int32_t nmax;            /* largest nnz over the queries (smem sizing) */
     int32_t pmax;            /* largest p over the datasets */

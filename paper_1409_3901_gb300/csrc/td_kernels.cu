@@ -158,6 +158,19 @@ __device__ __forceinline__ td_f2x td_add2_rp(td_f2x a, td_f2x b)
  * packed operand pairs.  Planes are npc pairs apart. */
 __device__ __forceinline__ int td_pair_of(int i) { return ((i >> 6) << 5) | (i & 31); }
 
+/* Pairs between planes for rows of up to nmax points: nmax rounded up to a
+ * round of 128 points, halved, plus one pair of padding, so that the planes
+ * of one point fall in different shared-memory banks (the lanes that form a
+ * subset's minors read several coordinates of one point at once). */
+__host__ __device__ inline int td_plane_pairs(int nmax) { return (((nmax + 127) & ~127) >> 1) + 1; }
+
+/* Bytes of `planes` staging planes, rounded up to 128 so that the warp
+ * regions after them stay 128-byte aligned. */
+__host__ __device__ inline size_t td_staging_bytes(int nmax, int planes)
+{
+    return ((size_t)planes * td_plane_pairs(nmax) * 16 + 127) & ~(size_t)127;
+}
+
 __device__ __forceinline__ int td_xidx(int npc, int i, int r)
 {
     return (((r >> 1) * npc + td_pair_of(i)) << 2) + ((r & 1) << 1) + ((i >> 5) & 1);
@@ -917,7 +930,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
 /* ====================================================================== */
 
 /* Subsets per warp and tile: about 2^16 point evaluations per warp and tile
- * (the per-tile set-up then costs well under 1%), at most 128, and at most
+ * (the per-tile set-up then costs well under 1%), at most 256, and at most
  * 1/64 of the query's range per CTA tile so that a short subset loop still
  * spreads over many CTAs; at least 4. */
 /* a / b for b > 0, by the 32-bit unsigned divide when both operands fit */
@@ -932,7 +945,7 @@ __host__ __device__ inline int td_auto_spw(int nnz, int64_t nrange, int warps)
     int64_t s = 65536 / (nnz > 0 ? nnz : 1);
     const int64_t cap = td_div_nonneg(nrange, 64 * (int64_t)(warps > 0 ? warps : 1));
     s = s < cap ? s : cap;
-    return s < 4 ? 4 : (s > 128 ? 128 : (int)s);
+    return s < 4 ? 4 : (s > 256 ? 256 : (int)s);
 }
 
 /* Tiles of every query, and for each effective dimension D = 2..6 the prefix
@@ -949,7 +962,9 @@ __global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
     for (int j = beg; j < end; ++j) {
         const int q = L.order[j];
         const TdQuery &Q = L.q[q];
-        int spw = L.spw > 0 ? L.spw : td_auto_spw(Q.nnz, Q.hi - Q.lo, L.warps);
+        int spw = L.spw;
+        if (spw <= 0 && Q.d >= 2 && Q.d <= 6 && Q.nnz > 0) spw = L.spw_tab[Q.d - 2][td_octave(Q.nnz)];
+        if (spw <= 0) spw = td_auto_spw(Q.nnz, Q.hi - Q.lo, L.warps);
         int64_t ts = (int64_t)spw * L.warps;
         L.tile_size[q] = (int)ts;
         int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? td_div_nonneg(Q.hi - Q.lo + ts - 1, ts) : 0;
@@ -1192,6 +1207,16 @@ __device__ __forceinline__ int td_ev_minus(uint32_t w) { return (int)(w >> 16) -
  * at 192, meta (8 int) at 320 */
 #define TD_WARP_META_BYTES 352
 
+/* A warp's shared region: the histogram storage (rbytes), gcount and the
+ * basis block, rounded to 128 bytes so that every region -- and every
+ * 128-byte row of a coarse histogram -- starts 128-byte aligned (the
+ * staging planes before them are multiples of 1024 bytes and the dynamic
+ * shared memory is declared 128-byte aligned). */
+__host__ __device__ inline size_t td_warp_region_bytes(size_t rbytes)
+{
+    return (rbytes + 16 + TD_WARP_META_BYTES + 127) & ~(size_t)127;
+}
+
 /* the two basis columns from the warp's shared block (32-bit words: qa at
  * [0, D), qb at [8, 8 + D), 16-byte aligned) */
 template <int D>
@@ -1378,17 +1403,6 @@ __device__ __forceinline__ void td_lane_pair(int lane, int npc, int &pi, int &pj
     }
 }
 
-/* Cooperative subset basis, published to the warp's shared block.  Lane l <
- * C(D,2) computes the Plucker coordinate P of the l-th row pair (i, j) in
- * lexicographic order: the entries Q_ij = P, Q_ji = -P of the antisymmetric
- * integer matrix whose columns are functionals vanishing on span S.  The warp
- * picks a pair (a, b) with P_ab != 0 and |P_ab| largest up to binary32
- * rounding (one max-reduction of a 32-bit key; any nonzero P_ab gives a
- * valid basis).  Lane e < 16 then writes entry t = e % 8 of column a (e < 8)
- * or b: exact, truncated to int32 and rounded to binary32 (twice, packed),
- * fetching its P with one shuffle; every lane writes the same intrinsic
- * coordinates (the rows other than a and b) and subset ids.  Returns false
- * (uniformly) when every P vanishes (rank < K). */
 /* Cofactors of column 0 of a K x K matrix (column 0 unused):
  * cof[i] = (-1)^i det(m without row i and column 0), so that
  * det(m) = sum_i m[i][0] cof[i]. */
@@ -1414,19 +1428,30 @@ __device__ __forceinline__ void td_cofactors0(const T (&m)[K > 0 ? K : 1][K > 0 
     }
 }
 
+/* Cooperative subset basis.  Lane l < C(D,2) computes the Plucker
+ * coordinate P of the l-th row pair (i, j) in lexicographic order: the
+ * entries Q_ij = P, Q_ji = -P of the antisymmetric integer matrix whose
+ * columns are functionals vanishing on span S.  The warp picks a pair (a, b)
+ * with P_ab != 0 and |P_ab| largest up to binary32 rounding (one
+ * max-reduction of a 32-bit key; any nonzero P_ab gives a valid basis).
+ * Every sweep needs only the two columns a and b rounded to binary32
+ * (td_basis_publish); the few sweeps that place points exactly also need
+ * them exact, truncated to int32, and the subset's intrinsic rows and point
+ * ids (td_basis_publish_exact, which repeats the pick from the cached
+ * cofactors and so chooses the same pair). */
+
+/* This lane's Plucker coordinate P (0 for lanes past C(D,2)).  lr[i]: this
+ * lane's i-th row of its minor, as the offset of that coordinate within a
+ * point's slots (td_xidx less the point part).  The minor is expanded along
+ * column 0 (point c[0], the one the colex successor changes most often):
+ * the cofactors cof[] of the other columns are recomputed only when refresh
+ * is set (c[1..K) changed).  NM: the arithmetic is int32 (the caller has
+ * checked K! max|x|^K < 2^31, which bounds every intermediate), else int64. */
 template <int D, bool NM>
-__device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const int (&c)[D > 2 ? D - 2 : 1],
-                                                 int lane, int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
-                                                 const TdWarpSmem &W, int64_t (&cof)[D > 2 ? D - 2 : 1],
-                                                 bool refresh)
+__device__ __forceinline__ int64_t td_basis_minor(const float *xs, const int (&c)[D > 2 ? D - 2 : 1], int lane,
+                                                  int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
+                                                  int64_t (&cof)[D > 2 ? D - 2 : 1], bool refresh)
 {
-    /* lr[i]: this lane's i-th row of its minor, as the offset of that
-     * coordinate within a point's slots (td_xidx less the point part).
-     * The minor is expanded along column 0 (point c[0], the one the colex
-     * successor changes most often): the cofactors cof[] of the other
-     * columns are recomputed only when refresh is set (c[1..K) changed).
-     * NM: the arithmetic is int32 (the caller has checked
-     * K! max|x|^K < 2^31, which bounds every intermediate), else int64. */
     constexpr int K = D - 2;
     constexpr int NP = D * (D - 1) / 2;
     using T = typename std::conditional<NM, int32_t, int64_t>::type;
@@ -1447,23 +1472,34 @@ __device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const
 #pragma unroll
     for (int i = 0; i < K; ++i)
         M += (T)td_f2i(xs[lr[i] + ((td_pair_of(c[0]) << 2) | ((c[0] >> 5) & 1))]) * (T)cof[i];
-    int64_t P;
+    int64_t P = ((pi + pj) & 1) ? (int64_t)M : -(int64_t)M; /* -(-1)^(i+j) M */
+    return lane < NP ? P : 0;
+}
+
+/* The pick: the lane holding the chosen pair, or -1 (uniformly) when every
+ * P vanishes (rank < K). */
+template <bool NM>
+__device__ __forceinline__ int td_basis_pick(int64_t P, int lane)
+{
     uint32_t key;
     if constexpr (NM) {
-        int32_t P32 = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
-        if (lane >= NP) P32 = 0;
+        const int32_t P32 = (int32_t)P;
         key = P32 != 0 ? ((__float_as_uint(__int2float_rn(P32 < 0 ? -P32 : P32)) & ~31u) | (uint32_t)(31 - lane)) : 0u;
-        P = P32;
     } else {
-        P = ((pi + pj) & 1) ? M : -M; /* -(-1)^(i+j) M */
-        if (lane >= NP) P = 0;
         key = P != 0 ? ((__float_as_uint(fabsf(td_i64_to_f32_bf(P))) & ~31u) | (uint32_t)(31 - lane)) : 0u;
     }
     const uint32_t kmax = __reduce_max_sync(TD_FULL, key);
-    if (kmax == 0u) return false;
-    const int wl = 31 - (int)(kmax & 31u);
-    const int a = __shfl_sync(TD_FULL, pi, wl), b = __shfl_sync(TD_FULL, pj, wl);
-    /* entry t of column col: Q_t,col = +-P of the pair (min, max), 0 for t == col */
+    return kmax == 0u ? -1 : 31 - (int)(kmax & 31u);
+}
+
+/* Entry t = e % 8 of column a (e < 8) or b (8 <= e < 16) of lane e:
+ * Q_t,col = +-P of the pair (min, max), 0 for t == col, fetched with one
+ * shuffle; also returns a and b. */
+template <int D, bool NM>
+__device__ __forceinline__ int64_t td_basis_entry(int64_t P, int wl, int lane, int pi, int pj, int &a, int &b)
+{
+    a = __shfl_sync(TD_FULL, pi, wl);
+    b = __shfl_sync(TD_FULL, pj, wl);
     const int e = lane & 15, t = e & 7, col = (e >> 3) ? b : a;
     const int x = min(t, col), y = max(t, col);
     const int src = x * (2 * D - x - 1) / 2 + (y - x - 1);
@@ -1472,24 +1508,63 @@ __device__ __forceinline__ bool td_basis_publish(const float *xs, int npc, const
         Pv = __shfl_sync(TD_FULL, (int32_t)P, t == col ? 0 : src);
     else
         Pv = __shfl_sync(TD_FULL, P, t == col ? 0 : src);
-    const int64_t v = t == col ? 0 : (t < col ? Pv : -Pv);
+    return t == col ? 0 : (t < col ? Pv : -Pv);
+}
+
+/* Every sweep: the two basis columns rounded to binary32, each value twice
+ * (packed pairs), to the warp's shared block.  Returns false (uniformly)
+ * when the subset is dependent. */
+template <int D, bool NM>
+__device__ __forceinline__ bool td_basis_publish(const float *xs, const int (&c)[D > 2 ? D - 2 : 1], int lane,
+                                                 int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
+                                                 const TdWarpSmem &W, int64_t (&cof)[D > 2 ? D - 2 : 1],
+                                                 bool refresh)
+{
+    const int64_t P = td_basis_minor<D, NM>(xs, c, lane, pi, pj, lr, cof, refresh);
+    const int wl = td_basis_pick<NM>(P, lane);
+    if (wl < 0) return false;
+    int a, b;
+    const int64_t v = td_basis_entry<D, NM>(P, wl, lane, pi, pj, a, b);
     __syncwarp();
-    if (lane < 16 && t < D) {
+    const int e = lane & 15;
+    if (lane < 16 && (e & 7) < D) {
         const float f = NM ? __int2float_rn((int32_t)v) : td_i64_to_f32_bf(v);
+        W.fab2[e] = td_pk(f, f);
+    }
+    __syncwarp();
+    return true;
+}
+
+/* The sweeps that go past the coarse bound: the same two columns exact
+ * (int64) and truncated to int32, the subset's intrinsic rows (the rows
+ * other than a and b) and point ids, to the warp's shared block. */
+template <int D, bool NM>
+__device__ __forceinline__ void td_basis_publish_exact(const float *xs, const int (&c)[D > 2 ? D - 2 : 1], int lane,
+                                                    int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
+                                                    const TdWarpSmem &W, int64_t (&cof)[D > 2 ? D - 2 : 1])
+{
+    constexpr int K = D - 2;
+    const int64_t P = td_basis_minor<D, NM>(xs, c, lane, pi, pj, lr, cof, false);
+    const int wl = td_basis_pick<NM>(P, lane); /* >= 0: the sweep found the subset independent */
+    int a, b;
+    const int64_t v = td_basis_entry<D, NM>(P, wl, lane, pi, pj, a, b);
+    __syncwarp();
+    const int e = lane & 15;
+    if (lane < 16 && (e & 7) < D) {
         W.qa[e] = v;
         W.q32[e] = (int32_t)v;
-        W.fab2[e] = td_pk(f, f);
     }
 #pragma unroll
     for (int r = 0; r < K; ++r) {
         int rr = r;
         rr += (rr >= a);
         rr += (rr >= b);
-        W.meta[r] = rr;        /* the same value from every lane */
-        W.meta[4 + r] = c[r];
+        if (lane == 0) {
+            W.meta[r] = rr;
+            W.meta[4 + r] = c[r];
+        }
     }
     __syncwarp();
-    return true;
 }
 
 /* Publish the exact basis and the subset to the warp's shared area. */
@@ -1780,12 +1855,23 @@ __device__ __noinline__ int td_rescan(const float *xs, int npc, int nnz, const T
  * 0 or of 2, so key - delta < 0 or key + delta > 2 and the two floors differ
  * (for y1_f = 0 the interval is wider than B; s = 0 gives NaN or an
  * infinite key, which fails the range test). */
-template <int D>
+/* The coarse histogram is cumulative: the sweep loop adds to it and pass 1
+ * reads each row's total and subtracts the total it read at the previous
+ * sweep (prev_row, prev_u, kept per lane), instead of clearing the table.
+ * A counter word is the integer sum of its packed increments modulo 2^32,
+ * and one sweep adds less than 2^31 to a row, so the difference is this
+ * sweep's packed count exactly.  clean: the table and the prev_* registers
+ * agree (false after a sweep that built its fine histogram in the same
+ * storage, and at the start of a tile: the table is then cleared and the
+ * prev_* registers reset).  publish_exact() writes the exact basis and the
+ * subset's rows and ids before the first exact step of a sweep. */
+template <int D, typename PUB>
 __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int nnz,
                                                  const td_f2x (&FA)[D], const td_f2x (&FB)[D], float Ea, float Eb,
                                                  bool narrow, const TdWarpSmem &W, int blog2, int lane, int best,
-                                                 bool &clean, uint64_t &n_exact, uint32_t &n_resolved, int &t_out,
-                                                 int &nzy_out)
+                                                 bool &clean, uint32_t &prev_row, uint32_t &prev_u,
+                                                 uint64_t &n_exact, uint32_t &n_resolved, int &t_out,
+                                                 int &nzy_out, PUB &&publish_exact)
 {
     constexpr int NPL = (D + 1) / 2;        /* planes of the pair layout */
     const int B = 1 << blog2;               /* blog2 >= 7: at least 4 buckets per lane */
@@ -1814,14 +1900,16 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
      * the fine test. */
     constexpr int UNR = TD_ROUND / 32;
     constexpr int NPR = UNR / 2; /* pairs per lane and round */
-    /* the coarse histogram starts at zero: pass 1 of the previous sweep
-     * left it so (clean), unless that sweep went past the coarse bound and
-     * built its fine histogram in the same storage.  At D = 6 the flag costs
-     * spills, and every sweep clears. */
+    /* the coarse histogram carries the previous sweeps' counts (clean),
+     * unless a sweep went past the coarse bound and built its fine
+     * histogram in the same storage.  At D = 6 the flag costs spills, and
+     * every sweep clears. */
     constexpr bool KEEP_CLEAN = D <= 5;
     if (!clean) {
         uint4 *z4 = reinterpret_cast<uint4 *>(W.hist);
         for (int j = lane; j < (TD_COARSE_WORDS >> 2); j += 32) z4[j] = make_uint4(0u, 0u, 0u, 0u);
+        prev_row = 0u;
+        prev_u = 0u;
     }
     __syncwarp();
     auto round = [&](int i0) {
@@ -1842,10 +1930,11 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     /* the last, partial round runs like the others over its padding zeros */
     for (int i0 = 0; i0 < nnz; i0 += 32 * UNR) round(i0);
     __syncwarp();
-    const uint32_t hU = W.hist[32 * 32 + lane];
+    const uint32_t hUt = W.hist[32 * 32 + lane];
+    const uint32_t hU = hUt - prev_u;
+    prev_u = hUt;
     /* uncertain points: the padding points of the last round are zeros,
      * whose key is NaN, so each of them added one event to row 32 too */
-    if (KEEP_CLEAN) W.hist[32 * 32 + lane] = 0u; /* left zero for the next sweep (see pass 1) */
     const int nu = td_wsum((int)(hU >> 16)) - (((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz);
     n_exact += (uint64_t)nu;
 
@@ -1869,17 +1958,19 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
         hil = Pl + cpl;
         return min(td_wmin(lol), nz - td_wmax(hil));
     };
-    uint32_t acc = 0;
+    uint32_t acc;
     {
-        /* lane l reads row l (and leaves it zero) */
-        uint4 *row = reinterpret_cast<uint4 *>(W.hist) + lane * 8;
+        /* lane l reads row l, its quad k ^ (l mod 8) at step k (the warp
+         * region, hence every 128-byte row, is 128-byte aligned) */
+        const unsigned rb = (td_saddr(W.hist) + 128u * (unsigned)lane) | ((unsigned)(lane & 7) << 4);
+        uint32_t tot = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int j = (k + lane) & 7;
-            const uint4 v = row[j];
-            acc += v.x + v.y + v.z + v.w;
-            if (KEEP_CLEAN) row[j] = make_uint4(0u, 0u, 0u, 0u);
+            const float4 v = td_lds128(rb ^ (unsigned)(k << 4));
+            tot += __float_as_uint(v.x) + __float_as_uint(v.y) + __float_as_uint(v.z) + __float_as_uint(v.w);
         }
+        acc = tot - prev_row;
+        prev_row = tot;
     }
     clean = KEEP_CLEAN;
     /* First without the uncertain points (not yet in any histogram): for
@@ -1892,6 +1983,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     int G = pass1(acc, nnz - nu);
     int t = 0;
     if (G < best) {
+        publish_exact();
         clean = false;
         /* the fine histogram shares the coarse one's storage: clear it */
         uint4 *z4 = reinterpret_cast<uint4 *>(W.hist);
@@ -2186,7 +2278,8 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     for (int r = 0; r < D; ++r) mxf[r] = (float)Q.mx[r]; /* < 2^22: exact */
     uint32_t n_dep = 0, n_tight = 0, n_res = 0;
     uint64_t n_exact = 0;
-    bool clean = false; /* the coarse histogram storage is zero */
+    bool clean = false; /* the coarse histogram agrees with prev_row / prev_u */
+    uint32_t prev_row = 0u, prev_u = 0u;
     /* forward error bound of the FP32 projection: the fma chain adds at most
      * D u sum |q_i x_i|, the rounded coefficients (at most 2u each, see
      * td_i64_to_f32) 2u more; taken as (D + 3) u, applied to A = sum |q_i|
@@ -2218,8 +2311,8 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
             if (K >= 2) refresh = !(c[0] + 1 < c[K >= 2 ? 1 : 0]);
             td_next_colex<K>(c);
         }
-        if (!(nm ? td_basis_publish<D, true>(xs, npc, c, lane, pi, pj, lr, W, cof, refresh)
-                 : td_basis_publish<D, false>(xs, npc, c, lane, pi, pj, lr, W, cof, refresh))) {
+        if (!(nm ? td_basis_publish<D, true>(xs, c, lane, pi, pj, lr, W, cof, refresh)
+                 : td_basis_publish<D, false>(xs, c, lane, pi, pj, lr, W, cof, refresh))) {
             ++n_dep;
             continue;
         }
@@ -2238,8 +2331,12 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
         /* exact bounds below 2^31 (the binary32 sums are within (D + 2) u) */
         const bool narrow = fmaxf(Aa, Ab) < 2145386496.0f; /* 2^31 (1 - 2^-10) */
         int t, nzy;
+        auto publish_exact = [&]() {
+            if (nm) td_basis_publish_exact<D, true>(xs, c, lane, pi, pj, lr, W, cof);
+            else td_basis_publish_exact<D, false>(xs, c, lane, pi, pj, lr, W, cof);
+        };
         const int G = td_sweep_filtered<D>(xs, npc, nnz, FA, FB, Ea, Eb, narrow, W, blog2, lane, best, clean,
-                                           n_exact, n_res, t, nzy);
+                                           prev_row, prev_u, n_exact, n_res, t, nzy, publish_exact);
         int V = G;
         if (t > K && G < best) {
             ++n_tight;
@@ -2286,7 +2383,7 @@ __device__ __forceinline__ int td_query_of_tile(const int64_t *prefix, int nq, i
 template <int D>
 __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int64_t s_tile;
     __shared__ int s_tmp[32];
     __shared__ int s_best[TD_WARPS_MAX];
@@ -2295,11 +2392,16 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     unsigned long long *ticket = L.ticket + (D - 2) * TD_TICKET_STRIDE;
     const int64_t total = prefix[L.nq];
     if (total == 0) return;
+    if (td_saddr(smem) & 127u) {
+        /* the row addressing of pass 1 needs 128-byte aligned warp regions */
+        if (threadIdx.x == 0) atomicAdd(&L.ctr->errors, 1ull);
+        return;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nmaxp = max(128, td_pow2_at_least(L.nmax));
     /* staging area: ceil(pmax/2) planes of npc pairs (sizing); this
      * dimension uses the first ceil(D/2) */
-    const int npc = ((L.nmax + TD_ROUND - 1) & ~(TD_ROUND - 1)) >> 1;
+    const int npc = td_plane_pairs(L.nmax);
     const int nplanes_max = (L.pmax + 1) >> 1;
     const int blog2_cap = L.blog2;
     /* layout: xs (pair planes) | per warp: region { fine hist [Bmax + 4]
@@ -2309,12 +2411,12 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     /* D = 2 (one subset a query): every warp takes its own queries, with its
      * own staging area of npc pairs in front of its region, and no block
      * barrier */
-    const size_t xs_warp = (D == 2) ? (size_t)npc * 16 : 0;
-    const size_t off = (D == 2) ? 0 : (size_t)nplanes_max * npc * 16;
+    const size_t xs_warp = (D == 2) ? td_staging_bytes(L.nmax, 1) : 0;
+    const size_t off = (D == 2) ? 0 : td_staging_bytes(L.nmax, nplanes_max);
     const int Bmax = 1 << blog2_cap;
     const size_t hbytes = (size_t)(Bmax + 4) * 4;
     const size_t rbytes = max((size_t)TD_COARSE_WORDS * 4, hbytes);
-    const size_t per_warp = (rbytes + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
+    const size_t per_warp = td_warp_region_bytes(rbytes);
     unsigned char *wb = smem + off + (per_warp + xs_warp) * w + xs_warp;
     float *xs = reinterpret_cast<float *>(D == 2 ? wb - xs_warp : smem);
     TdWarpSmem W;
@@ -2519,7 +2621,7 @@ __device__ void td_warp_plain(const TdLaunch &L, int q, const int32_t *xi, int P
 template <int D>
 __global__ void __launch_bounds__(128, 1) td_k_plain(TdLaunch L, int q)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_tmp[32];
     __shared__ int s_best[TD_WARPS_MAX];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -2634,15 +2736,14 @@ size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
 {
     int nmaxp = td_pow2_at_least(nmax);
     nmaxp = nmaxp < 128 ? 128 : nmaxp;
-    /* ceil(pmax/2) planes of (nmax rounded up to 128)/2 pairs, 16 bytes each,
+    /* ceil(pmax/2) planes of td_plane_pairs(nmax) pairs, 16 bytes each,
      * shared by the CTA; for the D = 2 kernel (pmax = 2) one plane per warp */
-    const size_t plane = (size_t)(((nmax + TD_ROUND - 1) & ~(TD_ROUND - 1)) / 2) * 16;
     const size_t hbytes = (size_t)((1 << blog2) + 4) * 4;
     size_t rbytes = hbytes;
     if (rbytes < (size_t)TD_COARSE_WORDS * 4) rbytes = (size_t)TD_COARSE_WORDS * 4;
-    size_t per_warp = (rbytes + 16 + TD_WARP_META_BYTES + 15) & ~(size_t)15;
-    if (pmax == 2) return (plane + per_warp) * warps;
-    return (size_t)((pmax + 1) / 2) * plane + per_warp * warps;
+    size_t per_warp = td_warp_region_bytes(rbytes);
+    if (pmax == 2) return (td_staging_bytes(nmax, 1) + per_warp) * warps;
+    return td_staging_bytes(nmax, (pmax + 1) / 2) + per_warp * warps;
 }
 
 size_t td_plain_smem(int nmax, int pmax, int warps)

@@ -70,6 +70,22 @@ class td_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+TD_TUNE_MAX = 8
+
+
+class td_tune_result(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("n", ctypes.c_int32), ("queries", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("spw", ctypes.c_int32 * TD_TUNE_MAX),
+                ("ms", ctypes.c_float * TD_TUNE_MAX), ("ms_default", ctypes.c_float),
+                ("best_spw", ctypes.c_int32), ("best_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        k = self.candidates
+        return {"p": self.p, "n": self.n, "queries": self.queries,
+                "candidates": {int(self.spw[i]): float(self.ms[i]) for i in range(k)},
+                "ms_default": self.ms_default, "best_spw": self.best_spw, "best_ms": self.best_ms}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise LibraryMissing("libtukeydepth.so is not built: run `python -m paper_1409_3901_gb300.build`")
@@ -91,6 +107,8 @@ def _load():
         "td_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "td_last_cuda_error": (ctypes.c_char_p, [vp]),
         "td_depth_noalloc": (ctypes.c_int, [vp, i32, i32, vp, i32, vp, vp]),
+        "td_autotune": (ctypes.c_int, [vp, i32, i32, P(td_tune_result)]),
+        "td_set_tuned": (ctypes.c_int, [vp, i32, i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -116,13 +134,15 @@ td_stream_destroy = lib.td_stream_destroy
 td_strerror = lib.td_strerror
 td_last_cuda_error = lib.td_last_cuda_error
 td_depth_noalloc = lib.td_depth_noalloc
+td_autotune = lib.td_autotune
+td_set_tuned = lib.td_set_tuned
 TD_NOALLOC_MAX_N = 512
 TD_NOALLOC_MAX_M = 4096
 
 EXPORTED = ["td_coord_limit", "td_create", "td_set_options", "td_destroy", "td_depth",
             "td_depth_batched", "td_stream_create", "td_stream_submit", "td_stream_poll",
             "td_stream_wait", "td_stream_destroy", "td_strerror", "td_last_cuda_error",
-            "td_depth_noalloc"]
+            "td_depth_noalloc", "td_autotune", "td_set_tuned"]
 
 
 def _check(rc, ctx=None):
@@ -228,8 +248,41 @@ class Context:
         self.last_stats = st
         return outs
 
+    def autotune(self, p, n):
+        """td_autotune: measure the work-tile sizes for dimension p and rows
+        of about n points, keep the fastest in this context; returns the
+        measurements."""
+        r = td_tune_result()
+        _check(td_autotune(self.ptr, int(p), int(n), ctypes.byref(r)), self.ptr)
+        return r.as_dict()
+
+    def set_tuned(self, d, octave, subsets_per_warp):
+        _check(td_set_tuned(self.ptr, int(d), int(octave), int(subsets_per_warp)), self.ptr)
+
     def stream(self, mem_budget_bytes):
         return Stream(self, mem_budget_bytes)
+
+
+def depth_sharded(X, Z, device=0, group=None, **opts):
+    """T(z) for every row z of Z, with Algorithm 1's subset loop split over
+    the ranks of a torch.distributed process group: rank r of W computes
+    shard r of W (td_options.shard_index / shard_count: contiguous ranges of
+    each query's colex subset positions) on `device`, and one all-reduce MIN
+    over the ranks -- the only exchange step -- merges the shards into the
+    depth, returned on every rank.  Host arrays (numpy) with a gloo group,
+    or CUDA int32 tensors (device pointers) with an nccl group."""
+    import torch
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    on_device = isinstance(X, torch.Tensor) and X.is_cuda
+    ctx = Context(device, shard_index=rank, shard_count=world, device_pointers=on_device, **opts)
+    try:
+        out = ctx.depth(X, Z)
+    finally:
+        ctx.close()
+    t = out if on_device else torch.from_numpy(np.ascontiguousarray(out))
+    dist.all_reduce(t, op=dist.ReduceOp.MIN, group=group)
+    return t if on_device else t.numpy()
 
 
 class Stream:

@@ -57,6 +57,11 @@ def test_coord_limits_and_strerror(tukey):
     assert tukey.td_strerror(-99) == b"unknown error"
 
 
+def test_autotune_arguments_rejected_without_device(tukey):
+    assert tukey.td_autotune(None, 4, 100, None) == tukey.TD_ERR_INVALID
+    assert tukey.td_set_tuned(None, 4, 5, 64) == tukey.TD_ERR_INVALID
+
+
 def test_null_and_bad_arguments_rejected_without_device(tukey):
     assert tukey.td_create(None, 0, None) == tukey.TD_ERR_INVALID
     assert tukey.td_depth(None, None, 1, 1, None, 0, None, None) == tukey.TD_ERR_INVALID
@@ -98,7 +103,8 @@ def test_structs_match_header_layout(tukey, tmp_path):
     import subprocess
     if shutil.which("gcc") is None:
         pytest.skip("no C compiler")
-    structs = {"td_options": tukey.td_options, "td_dataset": tukey.td_dataset, "td_stats": tukey.td_stats}
+    structs = {"td_options": tukey.td_options, "td_dataset": tukey.td_dataset, "td_stats": tukey.td_stats,
+               "td_tune_result": tukey.td_tune_result}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tukey_depth.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))

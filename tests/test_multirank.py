@@ -1,9 +1,11 @@
-"""Multi-rank path on the CPU: two gloo ranks split each query's subset loop
-(Algorithm 1, Section 3) into the contiguous position ranges the library's
-shard options use, compute their partial minima with the oracle, and merge
-them with an all-reduce MIN; the merge must give the depth.  A rank that
-drops out before the merge is detected on the host (the barrier times out)
-and never yields a partial result."""
+"""Multi-rank path.  On the CPU: two gloo ranks split each query's subset
+loop (Algorithm 1, Section 3) into contiguous position ranges, compute their
+partial minima with the oracle, and merge them with an all-reduce MIN; the
+merge must give the depth.  A rank that drops out before the merge is
+detected on the host (the barrier times out) and never yields a partial
+result.  On the GPU: the product path itself (tukey.depth_sharded), two
+gloo ranks each running the library's shard on device 0 (kernels that never
+wait on each other) and merging with the MIN all-reduce."""
 import datetime
 import os
 import socket
@@ -89,3 +91,42 @@ def test_shard_ranges_partition():
             rs = [_shard_range(npos, s, S) for s in range(S)]
             assert rs[0][0] == 0 and rs[-1][1] == npos
             assert all(a[1] == b[0] for a, b in zip(rs[:-1], rs[1:]))
+
+
+def _lib_worker(rank, world, port, X, Zq, out_path):
+    import torch
+    import torch.distributed as dist
+    from paper_1409_3901_gb300 import tukey
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=120))
+    merged = tukey.depth_sharded(X, Zq, device=0)
+    ctx = tukey.Context(0, shard_index=rank, shard_count=world)
+    own = ctx.depth(X, Zq)                     # this rank's shard alone
+    np.save(out_path + ".%d.npy" % rank, np.stack([merged, own]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_library_shards_on_two_ranks_merge_to_depth(tmp_path):
+    """tukey.depth_sharded on two gloo ranks sharing device 0: the merged MIN
+    equals the oracle's depth on both ranks, and so does the minimum of the
+    two ranks' own shards (W1, p = 3, and a p = 4 tie case)."""
+    import oracle
+    from gpu_common import load_golden
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W1")
+    d = W.w1()
+    assert d.checksum() == g["checksum"]
+    rng = np.random.default_rng(22)
+    X4 = rng.integers(-8, 9, size=(40, 4)).astype(np.int32)
+    X4[5:9] = X4[0]
+    Z4 = np.vstack([X4[:3], rng.integers(-5, 6, size=(3, 4))]).astype(np.int32)
+    for X, Zq, want in ((d.X, d.Zq, np.array(g["T"])), (X4, Z4, oracle.depth_many(X4, Z4))):
+        out = str(tmp_path / "m")
+        mp.start_processes(_lib_worker, args=(2, _free_port(), X, Zq, out), nprocs=2, start_method="spawn")
+        r0, r1 = np.load(out + ".0.npy"), np.load(out + ".1.npy")
+        assert np.array_equal(r0[0], want) and np.array_equal(r1[0], want)
+        assert np.array_equal(np.minimum(r0[1], r1[1]), want)

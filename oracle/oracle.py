@@ -155,7 +155,7 @@ def rank(X, z):
 
 
 ADIA_STATS = ("pops", "step4_subsets", "nodes", "max_stack", "union_points", "step5_subsets",
-              "d0_after_search", "algorithm1")
+              "d0_after_search", "algorithm1", "union_hash")
 
 
 def adia(X, z):
@@ -165,7 +165,7 @@ def adia(X, z):
     z, zp = _i32(z)
     n, p = X.shape
     out = ctypes.c_int64(0)
-    st = (ctypes.c_int64 * 8)()
+    st = (ctypes.c_int64 * 9)()
     _check(lib.oracle_adia(Xp, n, p, zp, ctypes.byref(out), st))
     return int(out.value), dict(zip(ADIA_STATS, (int(v) for v in st)))
 

@@ -719,9 +719,11 @@ static void sort_ints(int *a, int len)
 /* Algorithm 3 on cnt points (rows of pts, length d, already reduced by R7 so
  * that they span R^d) with the centred input coordinates orig (rows of length
  * p) for Step 2.  Returns the count (Z included), -1 on allocation failure, or
- * -4 on an internal inconsistency.  st[0..8): pops, subsets evaluated in
+ * -4 on an internal inconsistency.  st[0..9): pops, subsets evaluated in
  * Step 4, nodes pushed, largest stack, points in the union of Step 5(a),
- * subsets of Step 5(b), d0 after Step 4, 1 if Algorithm 1 was used (A5/A7). */
+ * subsets of Step 5(b), d0 after Step 4, 1 if Algorithm 1 was used (A5/A7),
+ * and the sum of (i + 1)^3 over the union's nonzero points i (data order),
+ * which makes the union itself observable (st must hold 9 zeros). */
 static int64_t adia_count(const int64_t *pts, int cnt, int d, const int64_t *orig, int p, int64_t *st)
 {
     const int k = d - 2, k1 = d - 1;
@@ -900,6 +902,7 @@ static int64_t adia_count(const int64_t *pts, int cnt, int d, const int64_t *ori
     for (int a = 0; a < nnz; ++a)
         if (inK[nz[a]]) Kl[nk++] = nz[a];
     st[4] = nk;
+    for (int a = 0; a < nk; ++a) st[8] += (int64_t)(Kl[a] + 1) * (Kl[a] + 1) * (Kl[a] + 1);
     if (nk >= k) {
         int c5[OR_MAXD], Ss[OR_MAXD];
         comb_first(c5, k);
@@ -1056,7 +1059,7 @@ int oracle_rank(const int32_t *X, int64_t n, int p, const int32_t *z, int32_t *p
 }
 
 /* Algorithm 3 (ADIA) for X (n x p) and z: *T receives its count (never below
- * oracle_depth's; readings A1-A7).  stats (may be NULL) receives 8 counters,
+ * oracle_depth's; readings A1-A7).  stats (may be NULL) receives 9 counters,
  * see adia_count.  Returns 0, OR_EINVAL, OR_ERANGE, OR_ENOMEM, or -4 on an
  * internal inconsistency. */
 int oracle_adia(const int32_t *X, int64_t n, int p, const int32_t *z, int64_t *T, int64_t *stats)
@@ -1065,7 +1068,7 @@ int oracle_adia(const int32_t *X, int64_t n, int p, const int32_t *z, int64_t *T
     int64_t *x = centre(X, n, p, z);
     if (!x) return OR_ENOMEM;
     if (!coord_bound_ok(x, n, p)) { free(x); return OR_ERANGE; }
-    int64_t st[8] = { 0 };
+    int64_t st[9] = { 0 };
     int allzero = 1;
     for (int64_t i = 0; i < n * p; ++i)
         if (x[i] != 0) { allzero = 0; break; }
@@ -1088,7 +1091,7 @@ int oracle_adia(const int32_t *X, int64_t n, int p, const int32_t *z, int64_t *T
     if (r < 0) return (int)r;
     *T = r;
     if (stats)
-        for (int i = 0; i < 8; ++i) stats[i] = st[i];
+        for (int i = 0; i < 9; ++i) stats[i] = st[i];
     return OR_OK;
 }
 

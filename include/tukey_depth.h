@@ -195,14 +195,19 @@ int td_depth_batched(td_ctx *ctx, const td_dataset *sets, int32_t k, td_stats *s
 /* Asynchronous request stream.  A request is admitted only while the device
  * memory it needs fits under mem_budget_bytes together with the requests in
  * flight; otherwise td_stream_submit returns TD_ERR_BUSY and changes nothing.
- * td_stream_submit copies the request's inputs before it returns.  Admitted
- * requests are coalesced: whenever one of the stream's two batch slots is
- * free, every request waiting at that moment runs in one batched launch
- * (as td_depth_batched) on the stream's own CUDA stream, with its state on
- * the device until the outputs are copied out.  Progress (reaping finished
- * batches, launching the waiting requests) is made inside td_stream_submit,
- * td_stream_poll and td_stream_wait.  A ticket is forgotten once poll or wait
- * has reported it done (TD_ERR_NOTFOUND afterwards). */
+ * td_stream_submit copies the request's inputs before it returns.  A large
+ * request's subset loop is cut into time slices: contiguous ranges of each
+ * query's subset positions of about 1.5e10 point evaluations (C(n, p-2) n a
+ * query), whose counts are merged by a minimum.  Admitted requests are
+ * coalesced: whenever one of the stream's two batch slots is free, one
+ * batched launch (as td_depth_batched) on the stream's own CUDA stream takes
+ * every waiting request of a single slice and the next slice of the sliced
+ * requests in arrival order while their work stays within about 3e10 point
+ * evaluations, so that a small request never waits behind the whole of a
+ * large one.  Progress (reaping finished batches, launching the waiting
+ * slices) is made inside td_stream_submit, td_stream_poll and td_stream_wait.
+ * A ticket is forgotten once poll or wait has reported it done
+ * (TD_ERR_NOTFOUND afterwards).  Algorithm 3 requests are not sliced. */
 int td_stream_create(td_ctx *ctx, size_t mem_budget_bytes, td_stream **s);
 int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *ticket);
 /* *done = 1 once the request's outputs have been written to its out buffer. */

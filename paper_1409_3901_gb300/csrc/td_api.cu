@@ -125,27 +125,38 @@ struct td_ctx {
     uint16_t tune[TD_NDIM][TD_NOCT] = {}; /* td_autotune: subsets per warp by dimension and octave */
 };
 
-/* one request of a stream: a copy of its inputs until its batch runs */
+/* one request of a stream: a copy of its inputs until its last slice has
+ * run.  Its subset loop is cut into nslices contiguous ranges of subset
+ * positions (time slices of bounded work); each slice's counts are merged
+ * into acc by a minimum. */
 struct td_stream_req {
     uint64_t ticket;
     int32_t n, p, m;
     std::vector<int32_t> X, Z;
+    std::vector<int32_t> acc; /* minimum over the finished slices */
     int32_t *user_out;
     size_t bytes;
-    int slot;        /* batch slot running it, -1 while pending */
-    int64_t out_off; /* offset of its outputs in the slot's output */
+    int nslices, next_slice, done_slices;
+    double slice_work;        /* point evaluations of one slice */
     bool finished;
     int status;
 };
 
-/* a batch of coalesced requests in flight */
+/* one slice of one request inside a batch */
+struct td_slice_entry {
+    td_stream_req *r;
+    int slice;
+    int64_t out_off; /* offset of its outputs in the batch's output */
+};
+
+/* a batch of coalesced slices in flight */
 struct td_stream_slot {
     Work w;
     HostBuf hstage, hout;
     cudaEvent_t done = nullptr;
     bool busy = false;
     int nq = 0;
-    std::vector<td_stream_req *> reqs;
+    std::vector<td_slice_entry> ents;
 };
 
 struct td_stream {
@@ -154,7 +165,7 @@ struct td_stream {
     size_t budget, inflight;
     uint64_t next;
     DevBuf scratch;
-    std::vector<td_stream_req *> pending;   /* admitted, not yet launched */
+    std::vector<td_stream_req *> pending;   /* admitted, with slices not yet launched */
     std::vector<td_stream_req *> reqs;      /* every request not yet reaped */
     td_stream_slot slot[2];
 };
@@ -273,6 +284,8 @@ Plan make_plan(const td_dataset *sets, int k)
         t.x_off = (int64_t)P.x_elems;
         t.n = sets[s].n;
         t.p = sets[s].p;
+        t.slice_index = 0;
+        t.slice_count = 1;
         P.sets.push_back(t);
         P.x_elems += (size_t)t.n * t.p;
         P.nmax = std::max(P.nmax, t.n);
@@ -992,29 +1005,45 @@ size_t request_bytes(int n, int p, int m)
     return (size_t)n * p * 4 + (size_t)m * (TD_MAXD * 4 + sizeof(TdQuery) + 4 + 8 * TD_NDIM + 4 + 4 + 4) + 4096;
 }
 
-/* Finish a slot whose event completed: hand every request its outputs. */
+/* Point evaluations (C(n, p-2) n a query) of a stream slice: about 25 ms
+ * of sweeping on one GB300.  A batch takes every waiting request of one
+ * slice and the next slice of the sliced ones in arrival order while their
+ * work stays within kBatchWork (at least one), so that a small request waits
+ * behind at most a batch of bounded work however large the requests before
+ * it are. */
+constexpr double kSliceWork = 1.5e10;
+constexpr double kBatchWork = 3.0e10;
+
+/* Finish a slot whose event completed: merge every slice's counts into its
+ * request, and hand a request its outputs once its last slice is in. */
 void complete_slot(td_stream *s, int k)
 {
     td_stream_slot &sl = s->slot[k];
     const int32_t *h = (const int32_t *)sl.hout.p;
     const TdCounters *c = (const TdCounters *)(h + ((sl.nq + 3) & ~3));
     const bool ok = c->errors == 0;
-    for (td_stream_req *r : sl.reqs) {
-        if (ok) memcpy(r->user_out, h + r->out_off, (size_t)r->m * 4);
-        r->status = ok ? TD_OK : TD_ERR_INTERNAL;
-        r->finished = true;
-        s->inflight -= r->bytes;
-        r->X.clear();
-        r->X.shrink_to_fit();
-        r->Z.clear();
-        r->Z.shrink_to_fit();
+    for (const td_slice_entry &e : sl.ents) {
+        td_stream_req *r = e.r;
+        if (ok) {
+            for (int j = 0; j < r->m; ++j) r->acc[j] = std::min(r->acc[j], h[e.out_off + j]);
+        } else {
+            r->status = TD_ERR_INTERNAL;
+        }
+        if (++r->done_slices == r->nslices) {
+            if (r->status == TD_OK) memcpy(r->user_out, r->acc.data(), (size_t)r->m * 4);
+            r->finished = true;
+            s->inflight -= r->bytes;
+            std::vector<int32_t>().swap(r->X);
+            std::vector<int32_t>().swap(r->Z);
+            std::vector<int32_t>().swap(r->acc);
+        }
     }
-    sl.reqs.clear();
+    sl.ents.clear();
     sl.busy = false;
 }
 
-/* Reap finished slots, then launch the pending requests as one batch into a
- * free slot.  Returns TD_OK or a CUDA error code. */
+/* Reap finished slots, then launch the next slices of the waiting requests
+ * as one batch into a free slot.  Returns TD_OK or a CUDA error code. */
 int pump(td_stream *s)
 {
     td_ctx *ctx = s->ctx;
@@ -1029,9 +1058,13 @@ int pump(td_stream *s)
     if (k < 0) return TD_OK;
     td_stream_slot &sl = s->slot[k];
     std::vector<td_dataset> sets;
-    sets.reserve(s->pending.size());
+    std::vector<td_slice_entry> ents;
     int64_t off = 0;
+    double work = 0.0;
     for (td_stream_req *r : s->pending) {
+        /* the next slice of a sliced request joins while the batch's work
+         * stays within kBatchWork; a request of one slice always joins */
+        if (r->nslices > 1 && !ents.empty() && work + r->slice_work > kBatchWork) continue;
         td_dataset d;
         d.n = r->n;
         d.p = r->p;
@@ -1040,11 +1073,18 @@ int pump(td_stream *s)
         d.Z = r->Z.data();
         d.out = nullptr;
         sets.push_back(d);
-        r->slot = k;
-        r->out_off = off;
+        ents.push_back({ r, r->next_slice++, off });
         off += r->m;
+        work += r->slice_work;
     }
+    s->pending.erase(std::remove_if(s->pending.begin(), s->pending.end(),
+                                    [](td_stream_req *r) { return r->next_slice >= r->nslices; }),
+                     s->pending.end());
     Plan P = make_plan(sets.data(), (int)sets.size());
+    for (size_t i = 0; i < ents.size(); ++i) {
+        P.sets[i].slice_index = ents[i].slice;
+        P.sets[i].slice_count = ents[i].r->nslices;
+    }
     td_options o = ctx->opt;
     o.mode = TD_MODE_FILTERED;
     o.device_pointers = 0;
@@ -1080,8 +1120,7 @@ int pump(td_stream *s)
     TDCK(cudaMemcpyAsync((int32_t *)sl.hout.p + ((P.nq + 3) & ~3), sl.w.ctr.p, sizeof(TdCounters),
                          cudaMemcpyDeviceToHost, s->s));
     TDCK(cudaEventRecord(sl.done, s->s));
-    sl.reqs.swap(s->pending);
-    s->pending.clear();
+    sl.ents.swap(ents);
     sl.nq = P.nq;
     sl.busy = true;
     return TD_OK;
@@ -1141,8 +1180,17 @@ extern "C" int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *tic
     if (d->m > 0) r->Z.assign(d->Z, d->Z + (size_t)d->m * d->p);
     r->user_out = d->out;
     r->bytes = bytes;
-    r->slot = -1;
-    r->out_off = 0;
+    /* time slices: about kSliceWork point evaluations each (Algorithm 3's
+     * search is not sliced) */
+    double work = (double)d->n * d->m;
+    for (int i = 0; i < d->p - 2; ++i) work *= (double)(d->n - i) / (i + 1);
+    int ns = (int)std::min(std::ceil(work / kSliceWork), 1048576.0);
+    if (ctx->opt.algorithm == TD_ALG_ADIA || ns < 1) ns = 1;
+    r->nslices = ns;
+    r->next_slice = 0;
+    r->done_slices = 0;
+    r->slice_work = work / ns;
+    r->acc.assign((size_t)d->m, INT32_MAX);
     r->finished = d->m == 0;
     r->status = TD_OK;
     s->reqs.push_back(r);

@@ -58,6 +58,9 @@ struct TdQuery {
 struct TdSet {
     int64_t x_off;  /* offset of X (n x p int32) in the data arena, in int32 elements */
     int32_t n, p;
+    int32_t slice_index, slice_count; /* this call handles slice slice_index of slice_count contiguous
+                                         ranges of each query's subset positions (the stream's time
+                                         slices; slice_count <= 1: the call's shard) */
 };
 
 /* Statistics counters accumulated on the device. */

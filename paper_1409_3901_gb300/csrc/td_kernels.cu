@@ -159,10 +159,13 @@ __device__ __forceinline__ td_f2x td_add2_rp(td_f2x a, td_f2x b)
 __device__ __forceinline__ int td_pair_of(int i) { return ((i >> 6) << 5) | (i & 31); }
 
 /* Pairs between planes for rows of up to nmax points: nmax rounded up to a
- * round of 128 points, halved, plus one pair of padding, so that the planes
- * of one point fall in different shared-memory banks (the lanes that form a
- * subset's minors read several coordinates of one point at once). */
-__host__ __device__ inline int td_plane_pairs(int nmax) { return (((nmax + 127) & ~127) >> 1) + 1; }
+ * round of 128 points, halved, plus two pairs of padding.  Plane c of a
+ * point then starts 8c words (mod 32) after plane 0, so the coordinates of
+ * one point occupy banks {0, 2, 8, 10, 16, 18} + b and those of the next
+ * point (4 words on) {4, 6, 12, 14, 20, 22} + b: the lanes that form the
+ * minors of one subset, or of two consecutive subsets at once, never
+ * collide. */
+__host__ __device__ inline int td_plane_pairs(int nmax) { return (((nmax + 127) & ~127) >> 1) + 2; }
 
 /* Bytes of `planes` staging planes, rounded up to 128 so that the warp
  * regions after them stay 128-byte aligned. */
@@ -844,7 +847,15 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
             Q->piv[c] = s_piv[c];
             Q->mx[c] = c < d ? s_max[c] : 0;
         }
-        bool first_shard = L.shard_count <= 1 || L.shard_index == 0;
+        /* the range of subset positions of this call: the dataset's time
+         * slice if it has one, else the call's shard */
+        int64_t sc = L.shard_count > 1 ? L.shard_count : 1;
+        int64_t si = L.shard_count > 1 ? L.shard_index : 0;
+        if (S.slice_count > 1) {
+            sc = S.slice_count;
+            si = S.slice_index;
+        }
+        const bool first_shard = si == 0;
         if (n - Z == 0 || d <= 1) {
             int direct = (n - Z == 0) ? n : Z + min(s_pos, s_neg);
             Q->direct = first_shard ? direct : INT_MAX;
@@ -856,8 +867,6 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
             Q->k = L.critical ? d - 1 : d - 2;
             int64_t ns = (int64_t)td_binom(n - Z, Q->k);
             Q->nsub = ns;
-            int64_t sc = L.shard_count > 1 ? L.shard_count : 1;
-            int64_t si = L.shard_count > 1 ? L.shard_index : 0;
             Q->lo = (int64_t)((__int128)ns * si / sc);
             Q->hi = (int64_t)((__int128)ns * (si + 1) / sc);
         }
@@ -1203,9 +1212,14 @@ struct TdWarpSmem {
 __device__ __forceinline__ int td_ev_plus(uint32_t w) { return (int)(w & 0xFFFFu); }
 __device__ __forceinline__ int td_ev_minus(uint32_t w) { return (int)(w >> 16) - (int)(w & 0xFFFFu); }
 
-/* q64 (16 int64: qa, qb) at 0, q32 (16 int) at 128, fab2 (16 packed pairs)
- * at 192, meta (8 int) at 320 */
-#define TD_WARP_META_BYTES 352
+/* q64 (16 int64: qa, qb) at 0, q32 (16 int) at 128, fab2 (32 packed pairs:
+ * the columns of subset A at [0, 16), of subset B at [16, 32) when two
+ * subsets are swept together) at 192, meta (8 int) at 448 */
+#define TD_WARP_META_BYTES 480
+
+/* Coarse histograms per warp: two for D = 3..5, whose warps sweep two
+ * subsets at once (td_sweep_dual), one otherwise. */
+__host__ __device__ constexpr int td_coarse_tables(int D) { return (D >= 3 && D <= 5) ? 2 : 1; }
 
 /* A warp's shared region: the histogram storage (rbytes), gcount and the
  * basis block, rounded to 128 bytes so that every region -- and every
@@ -1565,6 +1579,65 @@ __device__ __forceinline__ void td_basis_publish_exact(const float *xs, const in
         }
     }
     __syncwarp();
+}
+
+/* Two subsets at once (td_sweep_dual): lanes 0-15 compute the Plucker
+ * coordinates of subset A (lane pair e = lane, cH = its points), lanes
+ * 16-31 those of subset B (pair e = lane - 16); each half picks its own pair
+ * (a, b) as td_basis_pick does, and lane l writes entry l & 15 of the binary32
+ * columns of its half's subset to W.fab2[l] (A at [0, 16), B at [16, 32)).
+ * The error bound of each subset's projection is formed in the lanes: lane l
+ * holds |q_t| max|x_t| for its entry t = l % 8 (mx_lane = max|x_t|, 0 for
+ * t >= D), the eight lanes of a column sum them, and E_h = cst * the larger
+ * column sum of half h -- the binary32 sum is within (D + 2) u of the exact
+ * one in any order, as the bound assumes.  Returns bit 0 when A is
+ * dependent, bit 1 when B is.  pi, pj, lr, cof: this lane's pair e. */
+template <int D, bool NM>
+__device__ __forceinline__ int td_basis_publish_dual(const float *xs, const int (&cH)[D > 2 ? D - 2 : 1], int lane,
+                                                     int pi, int pj, const int (&lr)[D > 2 ? D - 2 : 1],
+                                                     const TdWarpSmem &W, int64_t (&cof)[D > 2 ? D - 2 : 1],
+                                                     bool refresh, float mx_lane, float cst, float &EA, float &EB,
+                                                     bool &narrowA, bool &narrowB)
+{
+    const int e = lane & 15, half = lane & 16;
+    const int64_t P = td_basis_minor<D, NM>(xs, cH, e, pi, pj, lr, cof, refresh);
+    uint32_t key;
+    if constexpr (NM) {
+        const int32_t P32 = (int32_t)P;
+        key = P32 != 0 ? ((__float_as_uint(__int2float_rn(P32 < 0 ? -P32 : P32)) & ~31u) | (uint32_t)(31 - lane)) : 0u;
+    } else {
+        key = P != 0 ? ((__float_as_uint(fabsf(td_i64_to_f32_bf(P))) & ~31u) | (uint32_t)(31 - lane)) : 0u;
+    }
+    const uint32_t kA = __reduce_max_sync(TD_FULL, half ? 0u : key);
+    const uint32_t kB = __reduce_max_sync(TD_FULL, half ? key : 0u);
+    const int dep = (kA == 0u ? 1 : 0) | (kB == 0u ? 2 : 0);
+    const uint32_t kh = half ? kB : kA;
+    const int wl = 31 - (int)(kh & 31u); /* a lane of this half (its pair wins) */
+    const int a = __shfl_sync(TD_FULL, pi, wl), b = __shfl_sync(TD_FULL, pj, wl);
+    const int t = e & 7, col = (e >> 3) ? b : a;
+    const int x = min(t, col), y = max(t, col);
+    const int src = half + x * (2 * D - x - 1) / 2 + (y - x - 1);
+    int64_t Pv;
+    if constexpr (NM)
+        Pv = __shfl_sync(TD_FULL, (int32_t)P, t == col ? half : src);
+    else
+        Pv = __shfl_sync(TD_FULL, P, t == col ? half : src);
+    const int64_t v = t == col ? 0 : (t < col ? Pv : -Pv);
+    const float f = NM ? __int2float_rn((int32_t)v) : td_i64_to_f32_bf(v);
+    float sum = fabsf(f) * mx_lane; /* 0 for t >= D (mx_lane = 0, f finite) */
+    sum += __shfl_xor_sync(TD_FULL, sum, 4);
+    sum += __shfl_xor_sync(TD_FULL, sum, 2);
+    sum += __shfl_xor_sync(TD_FULL, sum, 1);
+    const float A0 = fmaxf(__shfl_sync(TD_FULL, sum, 0), __shfl_sync(TD_FULL, sum, 8));
+    const float A1 = fmaxf(__shfl_sync(TD_FULL, sum, 16), __shfl_sync(TD_FULL, sum, 24));
+    EA = A0 * cst;
+    EB = A1 * cst;
+    narrowA = A0 < 2145386496.0f; /* 2^31 (1 - 2^-10): exact bounds below 2^31 */
+    narrowB = A1 < 2145386496.0f;
+    __syncwarp();
+    if (t < D) W.fab2[lane] = td_pk(f, f);
+    __syncwarp();
+    return dep;
 }
 
 /* Publish the exact basis and the subset to the warp's shared area. */
@@ -2199,6 +2272,98 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     return G;
 }
 
+/* The coarse bounds of two subsets A and B in one pass over the points
+ * (Algorithm 2's walk bounded per lane range, as in td_sweep_filtered,
+ * before any exact step): every staged pair is loaded once and projected
+ * with both subsets' binary32 bases, and each event goes to its subset's
+ * coarse histogram (A at W.hist, B right after it), cumulative as in
+ * td_sweep_filtered (prev[0..1]: A's row and uncertain totals, prev[2..3]:
+ * B's; clean2: both tables agree with them).  Pass 1 of both subsets shares
+ * its warp reductions: the per-lane net counts of A and B are scanned as one
+ * 32-bit word (A + 2^16 B, both prefix sums below 2^15 in magnitude, so the
+ * two halves are recovered exactly), likewise the counts of -1 events and of
+ * uncertain points.  GA, GB: lower bounds of G(A), G(B) over the certified
+ * points (the value of td_sweep_filtered's first bound); nuA, nuB: their
+ * uncertain points. */
+template <int D>
+__device__ __forceinline__ void td_sweep_dual(const float *xs, int npc, int nnz, const TdPairCoef<D> &CA,
+                                              const TdPairCoef<D> &CB, const TdWarpSmem &W, int lane, bool &clean2,
+                                              uint32_t (&prev)[4], int &GA, int &GB, int &nuA, int &nuB)
+{
+    constexpr int NPL = (D + 1) / 2;
+    constexpr int UNR = TD_ROUND / 32;
+    constexpr int NPR = UNR / 2;
+    const unsigned xq = td_saddr(xs) + 16u * (unsigned)lane;
+    const unsigned pstride = 16u * (unsigned)npc;
+    const unsigned cqA = td_saddr(W.hist) + 4u * (unsigned)lane;
+    const unsigned cqB = cqA + 4u * TD_COARSE_WORDS;
+    if (!clean2) {
+        uint4 *z4 = reinterpret_cast<uint4 *>(W.hist);
+        for (int j = lane; j < (2 * TD_COARSE_WORDS >> 2); j += 32) z4[j] = make_uint4(0u, 0u, 0u, 0u);
+        prev[0] = prev[1] = prev[2] = prev[3] = 0u;
+    }
+    __syncwarp();
+    auto round = [&](int i0) {
+        const unsigned ba = xq + 8u * (unsigned)i0;
+#pragma unroll
+        for (int h = 0; h < NPR; ++h) {
+            float4 pl[NPL];
+#pragma unroll
+            for (int c = 0; c < NPL; ++c) pl[c] = td_lds128(ba + 512u * h + c * pstride);
+            int sa0, sa1, sb0, sb1;
+            uint32_t ia0, ia1, ib0, ib1;
+            td_pair_rows<D>(pl, CA, sa0, sa1, ia0, ia1);
+            td_pair_rows<D>(pl, CB, sb0, sb1, ib0, ib1);
+            td_reds_add(cqA + ((unsigned)sa0 << 7), ia0);
+            td_reds_add(cqA + ((unsigned)sa1 << 7), ia1);
+            td_reds_add(cqB + ((unsigned)sb0 << 7), ib0);
+            td_reds_add(cqB + ((unsigned)sb1 << 7), ib1);
+        }
+    };
+    for (int i0 = 0; i0 < nnz; i0 += 32 * UNR) round(i0);
+    __syncwarp();
+    /* uncertain points (row 32), padding zeros of the last round included */
+    const uint32_t uA = W.hist[32 * 32 + lane], uB = W.hist[TD_COARSE_WORDS + 32 * 32 + lane];
+    const uint32_t hA = uA - prev[1], hB = uB - prev[3];
+    prev[1] = uA;
+    prev[3] = uB;
+    const int pad = ((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz;
+    const uint32_t usum = (uint32_t)td_wsum((int)((hA >> 16) + ((hB >> 16) << 16)));
+    nuA = (int)(usum & 0xFFFFu) - pad;
+    nuB = (int)(usum >> 16) - pad;
+    /* pass 1: lane l reads row l of both tables (XOR-rotated quads) */
+    uint32_t accA, accB;
+    {
+        const unsigned rb = (td_saddr(W.hist) + 128u * (unsigned)lane) | ((unsigned)(lane & 7) << 4);
+        uint32_t tA = 0, tB = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float4 va = td_lds128(rb ^ (unsigned)(k << 4));
+            const float4 vb = td_lds128((rb ^ (unsigned)(k << 4)) + 4u * TD_COARSE_WORDS);
+            tA += __float_as_uint(va.x) + __float_as_uint(va.y) + __float_as_uint(va.z) + __float_as_uint(va.w);
+            tB += __float_as_uint(vb.x) + __float_as_uint(vb.y) + __float_as_uint(vb.z) + __float_as_uint(vb.w);
+        }
+        accA = tA - prev[0];
+        accB = tB - prev[2];
+        prev[0] = tA;
+        prev[2] = tB;
+    }
+    clean2 = true;
+    const int cpA = td_ev_plus(accA), cmA = td_ev_minus(accA);
+    const int cpB = td_ev_plus(accB), cmB = td_ev_minus(accB);
+    const uint32_t am = (uint32_t)td_wsum(cmA + (cmB << 16)); /* orientation + points: one -1 event each */
+    const int AA = (int)(am & 0xFFFFu), AB = (int)(am >> 16);
+    const int netA = cpA - cmA, netB = cpB - cmB;
+    const int v = netA + netB * 65536;
+    const int ex = td_wscan_incl(v, lane) - v;
+    const int exA = (int)(int16_t)(ex & 0xFFFF);
+    const int exB = (ex - exA) >> 16;
+    const int PA = AA + exA, PB = AB + exB;
+    const int ncA = nnz - nuA, ncB = nnz - nuB;
+    GA = td_wmin(min(PA - cmA, ncA - (PA + cpA)));
+    GB = td_wmin(min(PB - cmB, ncB - (PB + cpB)));
+}
+
 /* Tight-set correction m_S after a sweep.  Tight points are those with bucket
  * id TD_SENT (filtered kernel, bid != NULL) or a zero projection H (plain
  * kernel); coordinates come from xs (float, filtered, pair layout with PS
@@ -2261,25 +2426,42 @@ __device__ __noinline__ int td_tight_correction(const int *meta, const float *xs
 /* Process subset positions [r0, r1) of query q with one warp (filtered).
  * The warp's counters ws[] (sweeps, dependent, filtered points, exact
  * points, tight corrections, resolved sweeps, errors) live in shared memory;
- * the subset loop keeps 32-bit tile counts and lane 0 adds them at the end. */
+ * the subset loop keeps 32-bit tile counts and lane 0 adds them at the end.
+ *
+ * For D = 3..5 consecutive subsets are taken two at a time: td_sweep_dual
+ * gives both coarse bounds from one pass over the points, and a subset whose
+ * bound does not reach best is swept again alone (td_sweep_filtered: the
+ * coarse bound, then the exact steps) -- so every value below best is exact
+ * and the others are never below best, as in the one-at-a-time form, which
+ * D = 2 and D = 6 use throughout.  Each lane computes the minor of its row
+ * pair e = lane % 16 for the subset of its half of the warp (both halves
+ * the same subset when one is swept alone) and caches the cofactors of the
+ * minor's other columns, recomputed when c[1..K) of that subset differs from
+ * the one they were made for. */
 template <int D>
 __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int npc, int nnz,
                                  uint64_t r0, uint64_t r1, const TdWarpSmem &W, const TdScratch &scr,
                                  int blog2, int lane, int &best, unsigned long long *ws)
 {
     constexpr int K = D - 2;
+    constexpr int KK = K > 0 ? K : 1;
+    constexpr bool DUAL = td_coarse_tables(D) == 2;
     if (r0 >= r1) return;
     const TdQuery &Q = L.q[q];
-    int c[K > 0 ? K : 1];
+    int c[KK];
     c[0] = 0;
     td_unrank_colex<K>(r0, nnz, c);
     float mxf[D];
 #pragma unroll
     for (int r = 0; r < D; ++r) mxf[r] = (float)Q.mx[r]; /* < 2^22: exact */
+    float mx_lane = 0.f; /* max|x_t| of this lane's basis entry t = lane % 8 */
+#pragma unroll
+    for (int r = 0; r < D; ++r) mx_lane = (lane & 7) == r ? mxf[r] : mx_lane;
     uint32_t n_dep = 0, n_tight = 0, n_res = 0;
     uint64_t n_exact = 0;
-    bool clean = false; /* the coarse histogram agrees with prev_row / prev_u */
-    uint32_t prev_row = 0u, prev_u = 0u;
+    bool clean = false;  /* the coarse histogram agrees with prev_row / prev_u */
+    bool clean2 = false; /* the two coarse histograms of the dual sweep agree with prev2 */
+    uint32_t prev_row = 0u, prev_u = 0u, prev2[4] = { 0u, 0u, 0u, 0u };
     /* forward error bound of the FP32 projection: the fma chain adds at most
      * D u sum |q_i x_i|, the rounded coefficients (at most 2u each, see
      * td_i64_to_f32) 2u more; taken as (D + 3) u, applied to A = sum |q_i|
@@ -2287,9 +2469,12 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
      * error below (D + 2) u), the extra factor 1 + 2^-10 covering that and
      * the rounding of the products below */
     const float cst = (float)(D + 3) * TD_U * 1.0009765625f;
-    int pi, pj, lr[K > 0 ? K : 1];
-    td_lane_pair<D>(lane, npc, pi, pj, lr);
-    int64_t cof[K > 0 ? K : 1]; /* cofactors of column 0 of this lane's minor, for c[1..K) */
+    int pi, pj, lr[KK];
+    td_lane_pair<D>(lane & 15, npc, pi, pj, lr);
+    int64_t cof[KK];  /* cofactors of column 0 of this lane's minor */
+    int cmade[KK];    /* the c[1..K) they were made for (-1: none) */
+#pragma unroll
+    for (int i = 0; i < KK; ++i) cmade[i] = -1;
     /* minors in int32 when K! max|x|^K < 2^31 (max over the coordinates);
      * max|x| < 2^22 and K <= 4, so the product is formed in int64 with an
      * early stop once it reaches 2^31 (each factor is below 2^25) */
@@ -2303,19 +2488,23 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
         for (int i = 1; i <= K; ++i) b = b < ((int64_t)1 << 31) ? b * (int64_t)i * mm : b;
         nm = b < 2147483647LL;
     }
-    uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
-    for (uint32_t r = 0; r < nr; ++r) {
-        bool refresh = r == 0;
-        if (r > 0) {
-            /* the successor changes c[1..K) only when c[0] cannot grow */
-            if (K >= 2) refresh = !(c[0] + 1 < c[K >= 2 ? 1 : 0]);
-            td_next_colex<K>(c);
-        }
-        if (!(nm ? td_basis_publish<D, true>(xs, c, lane, pi, pj, lr, W, cof, refresh)
-                 : td_basis_publish<D, false>(xs, c, lane, pi, pj, lr, W, cof, refresh))) {
-            ++n_dep;
-            continue;
-        }
+    /* cofactors stale for this lane's subset cs? (and mark them made) */
+    auto stale = [&](const int (&cs)[KK]) -> bool {
+        bool st = cmade[0] < 0;
+#pragma unroll
+        for (int i = 1; i < K; ++i) st |= cs[i] != cmade[i];
+#pragma unroll
+        for (int i = 0; i < KK; ++i) cmade[i] = i == 0 ? 0 : cs[i];
+        return st;
+    };
+    /* One subset alone: basis, sweep (coarse bound, then the exact steps
+     * when it could lower best), tight correction.  Returns false when the
+     * subset is dependent. */
+    auto single = [&](const int (&cs)[KK]) -> bool {
+        const bool refresh = stale(cs);
+        if (!(nm ? td_basis_publish<D, true>(xs, cs, lane & 15, pi, pj, lr, W, cof, refresh)
+                 : td_basis_publish<D, false>(xs, cs, lane & 15, pi, pj, lr, W, cof, refresh)))
+            return false;
         td_f2x FA[D], FB[D];
         td_load_coef2<D>(W.fab2, FA, FB);
         float Aa = 0.0f, Ab = 0.0f;
@@ -2332,22 +2521,79 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
         const bool narrow = fmaxf(Aa, Ab) < 2145386496.0f; /* 2^31 (1 - 2^-10) */
         int t, nzy;
         auto publish_exact = [&]() {
-            if (nm) td_basis_publish_exact<D, true>(xs, c, lane, pi, pj, lr, W, cof);
-            else td_basis_publish_exact<D, false>(xs, c, lane, pi, pj, lr, W, cof);
+            if (nm) td_basis_publish_exact<D, true>(xs, cs, lane & 15, pi, pj, lr, W, cof);
+            else td_basis_publish_exact<D, false>(xs, cs, lane & 15, pi, pj, lr, W, cof);
         };
         const int G = td_sweep_filtered<D>(xs, npc, nnz, FA, FB, Ea, Eb, narrow, W, blog2, lane, best, clean,
                                            prev_row, prev_u, n_exact, n_res, t, nzy, publish_exact);
+        clean2 = false; /* the one-subset sweep used table A's storage */
         int V = G;
         if (t > K && G < best) {
             ++n_tight;
             V = G + td_tight_correction<D>(W.meta, xs, npc, nullptr, 0, nnz, W.bid, nullptr, scr, W.gcount, lane);
         }
         best = min(best, V);
-        if (L.early_exit && best <= 0) {
-            /* V = 0 is the least value: the rest of the range cannot lower it */
-            if (lane == 0) ws[7] += nr - 1 - r;
-            nr = r + 1;
-            break;
+        return true;
+    };
+    uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
+    uint32_t done = 0;
+    while (done < nr) {
+        if (DUAL && done + 1 < nr) {
+            int cB[KK];
+#pragma unroll
+            for (int i = 0; i < KK; ++i) cB[i] = c[i];
+            td_next_colex<K>(cB);
+            int cH[KK];
+#pragma unroll
+            for (int i = 0; i < KK; ++i) cH[i] = lane < 16 ? c[i] : cB[i];
+            const bool refresh = stale(cH);
+            float EA, EB;
+            bool narA, narB;
+            const int dep = nm ? td_basis_publish_dual<D, true>(xs, cH, lane, pi, pj, lr, W, cof, refresh, mx_lane,
+                                                                cst, EA, EB, narA, narB)
+                               : td_basis_publish_dual<D, false>(xs, cH, lane, pi, pj, lr, W, cof, refresh,
+                                                                 mx_lane, cst, EA, EB, narA, narB);
+            (void)narA;
+            (void)narB;
+            if (dep == 0) {
+                td_f2x FA[D], FB[D], FA2[D], FB2[D];
+                td_load_coef2<D>(W.fab2, FA, FB);
+                td_load_coef2<D>(W.fab2 + 16, FA2, FB2);
+                const TdPairCoef<D> CA = td_pair_coef<D>(FA, FB, EA, blog2);
+                const TdPairCoef<D> CB = td_pair_coef<D>(FA2, FB2, EB, blog2);
+                int GA, GB, nuA, nuB;
+                td_sweep_dual<D>(xs, npc, nnz, CA, CB, W, lane, clean2, prev2, GA, GB, nuA, nuB);
+                clean = false; /* the dual sweep used table A's storage */
+                /* a subset whose bound does not reach best is swept again alone */
+                if (GA < best) single(c);
+                else n_exact += (uint64_t)nuA;
+                if (GB < best) single(cB);
+                else n_exact += (uint64_t)nuB;
+            } else {
+                if (dep & 1) ++n_dep;
+                else single(c);
+                if (dep & 2) ++n_dep;
+                else single(cB);
+            }
+            done += 2;
+            if (L.early_exit && best <= 0) {
+                if (lane == 0) ws[7] += nr - done;
+                nr = done;
+                break;
+            }
+#pragma unroll
+            for (int i = 0; i < KK; ++i) c[i] = cB[i];
+            if (done < nr) td_next_colex<K>(c);
+        } else {
+            if (!single(c)) ++n_dep;
+            ++done;
+            if (L.early_exit && best <= 0) {
+                /* V = 0 is the least value: the rest of the range cannot lower it */
+                if (lane == 0) ws[7] += nr - done;
+                nr = done;
+                break;
+            }
+            if (done < nr) td_next_colex<K>(c);
         }
     }
     if (lane == 0) {
@@ -2415,7 +2661,7 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     const size_t off = (D == 2) ? 0 : td_staging_bytes(L.nmax, nplanes_max);
     const int Bmax = 1 << blog2_cap;
     const size_t hbytes = (size_t)(Bmax + 4) * 4;
-    const size_t rbytes = max((size_t)TD_COARSE_WORDS * 4, hbytes);
+    const size_t rbytes = max((size_t)TD_COARSE_WORDS * 4 * td_coarse_tables(D), hbytes);
     const size_t per_warp = td_warp_region_bytes(rbytes);
     unsigned char *wb = smem + off + (per_warp + xs_warp) * w + xs_warp;
     float *xs = reinterpret_cast<float *>(D == 2 ? wb - xs_warp : smem);
@@ -2431,7 +2677,7 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     W.qb = W.qa + 8;
     W.q32 = reinterpret_cast<int32_t *>(wb + rbytes + 16 + 128);
     W.fab2 = reinterpret_cast<td_f2x *>(wb + rbytes + 16 + 192);
-    W.meta = reinterpret_cast<int *>(wb + rbytes + 16 + 320);
+    W.meta = reinterpret_cast<int *>(wb + rbytes + 16 + 448);
     for (int j = lane; j < max(Bmax + 4, TD_COARSE_WORDS); j += 32) W.hist[j] = 0u;
     unsigned long long *ws = s_stats[w];
     if (lane < 8) ws[lane] = 0ull;
@@ -2719,9 +2965,10 @@ __global__ void td_k_finalize(TdLaunch L)
     } else if (Q.direct == TD_DIRECT_RANGE) {
         r = INT_MIN; /* never copied out: the host reports TD_ERR_RANGE */
     } else if (L.qmin[q] == INT_MAX) {
-        /* no independent subset in this shard's range */
-        r = (L.shard_count > 1) ? INT_MAX : -1;
-        if (L.shard_count <= 1) atomicAdd(&L.ctr->errors, 1ull);
+        /* no independent subset in this shard's (or slice's) range */
+        const bool part = L.shard_count > 1 || L.sets[Q.set].slice_count > 1;
+        r = part ? INT_MAX : -1;
+        if (!part) atomicAdd(&L.ctr->errors, 1ull);
     } else {
         r = Q.Z + L.qmin[q];
     }
@@ -2740,7 +2987,8 @@ size_t td_filtered_smem(int nmax, int pmax, int blog2, int warps)
      * shared by the CTA; for the D = 2 kernel (pmax = 2) one plane per warp */
     const size_t hbytes = (size_t)((1 << blog2) + 4) * 4;
     size_t rbytes = hbytes;
-    if (rbytes < (size_t)TD_COARSE_WORDS * 4) rbytes = (size_t)TD_COARSE_WORDS * 4;
+    const size_t cbytes = (size_t)TD_COARSE_WORDS * 4 * td_coarse_tables(pmax);
+    if (rbytes < cbytes) rbytes = cbytes;
     size_t per_warp = td_warp_region_bytes(rbytes);
     if (pmax == 2) return (td_staging_bytes(nmax, 1) + per_warp) * warps;
     return td_staging_bytes(nmax, (pmax + 1) / 2) + per_warp * warps;

@@ -170,6 +170,8 @@ extern "C" int td_depth_noalloc(const int32_t *X, int32_t n, int32_t p, const in
     set.x_off = 0;
     set.n = n;
     set.p = p;
+    set.slice_index = 0;
+    set.slice_count = 1;
     if (cudaMemcpy2DAsync(base + kZq, TD_MAXD * 4, Z, (size_t)p * 4, (size_t)p * 4, m, cudaMemcpyDeviceToDevice, s) !=
         cudaSuccess)
         return TD_ERR_CUDA;

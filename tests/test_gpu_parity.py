@@ -226,6 +226,34 @@ def test_stream_w5s_all_requests(td):
         assert np.array_equal(out, np.array(it["T"])), it["index"]
 
 
+def test_stream_time_slices(td):
+    """A request large enough to be cut into time slices (the largest-n
+    p = 5 dataset of W3, its four stored queries repeated four times: about
+    6e10 point evaluations, five slices) followed by small requests: every
+    output equals the stored oracle counts, the slices' minima merged."""
+    from math import comb
+    from paper_1409_3901_gb300 import workloads as W
+    g = load_golden("W3L")
+    it = next(x for x in g["items"] if x["p"] == 5 and len(x["queries"]) == 4)
+    d = W.w3()[it["index"]]
+    assert d.checksum() == it["checksum"]
+    Z = np.vstack([d.Zq[it["queries"]]] * 4)
+    assert comb(d.n, 3) * d.n * Z.shape[0] > 4 * 1.5e10
+    ctx = td.Context(0)
+    s = ctx.stream(mem_budget_bytes=8 << 30)
+    heavy = s.submit(d.X, Z)
+    rng = np.random.default_rng(15)
+    small = []
+    for i in range(5):
+        X = random_case(rng, 4, 40, 30)
+        Zs = np.vstack([X[:2], rng.integers(-30, 31, size=(2, 4))]).astype(np.int32)
+        small.append((s.submit(X, Zs), X, Zs))
+    for t, X, Zs in small:
+        assert np.array_equal(s.wait(t, timeout_us=120_000_000), oracle.depth_many(X, Zs))
+    out = s.wait(heavy, timeout_us=300_000_000)
+    assert np.array_equal(out, np.tile(np.array(it["T"]), 4))
+
+
 def test_shards_merge_to_depth(td):
     rng = np.random.default_rng(9)
     X = random_case(rng, 4, 40, 20)

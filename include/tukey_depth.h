@@ -35,10 +35,12 @@
  *     returns (td_depth, td_depth_batched) or before td_stream_submit returns.
  *     Results are written before td_depth / td_depth_batched return, or before
  *     td_stream_wait returns (td_stream_poll reports done).
- *   - Limits: 1 <= p <= TD_MAX_P, 1 <= n <= TD_MAX_N, m >= 0; for every query z
- *     and coordinate j, |X_ij - z_j| must not exceed td_coord_limit(p), which
- *     keeps every exact intermediate inside 64-bit (coordinates, minors,
- *     projections) or 128-bit (cross products) integers.
+ *   - Limits: 1 <= p <= TD_MAX_P, 1 <= n <= TD_MAX_N, m >= 0.  Any int32
+ *     values: a query with some |X_ij - z_j| above td_coord_limit(p) (the
+ *     fast kernels keep every exact intermediate in 64- or 128-bit integers
+ *     below it) is answered by an exact 256-bit path instead (Proposition 1
+ *     of Section 2 with r = p - 1, one order of n slower), with the same
+ *     result.
  *   - Return value 0 (TD_OK) or a negative TD_ERR_* code; on error no output
  *     element is written (no partial results).  td_strerror() names a code.
  *   - Results are bit-exact and independent of scheduling; the statistics
@@ -56,7 +58,7 @@ extern "C" {
 
 #define TD_OK 0
 #define TD_ERR_INVALID (-1) /* null pointer, n < 1, m < 0, p outside [1, TD_MAX_P], n > TD_MAX_N */
-#define TD_ERR_RANGE (-2)   /* some |X_ij - z_j| exceeds td_coord_limit(p) */
+#define TD_ERR_RANGE (-2)   /* td_depth_noalloc only: some |X_ij - z_j| exceeds td_coord_limit(p) */
 #define TD_ERR_OOM (-3)     /* device or pinned host allocation failed */
 #define TD_ERR_BUSY (-4)    /* stream admission refused: request exceeds the memory budget now */
 #define TD_ERR_TIMEOUT (-5) /* td_stream_wait expired before the request finished */
@@ -78,16 +80,17 @@ typedef struct td_stream td_stream;
                          some V(S), so out[q] >= T.  The paper reports out[q] == T in all its
                          experiments, without proof; it is not so for every input (a query with
                          T = 32 and out[q] = 33 is among the tests).  Filtered mode, unsharded
-                         only. */
+                         only.  A query beyond td_coord_limit(p) gets the exact count T from
+                         the 256-bit path. */
 #define TD_ALG_CRITICAL 2 /* Proposition 1 (Section 2) with r = p-1: the minimum over the
                              hyperplanes spanned by p-1 centred points of the points strictly on
                              the smaller side, plus the open depth of the points on the hyperplane
                              inside it: the exact count T by a second route, O(n^(p-1)) normals
                              of O(n) work each, one launch per query (a cross-check of
-                             Algorithm 1).  p! M^p < 2^62 for the largest centred coordinate
-                             M (TD_ERR_RANGE otherwise); td_options.mode is ignored; not
-                             served by the stream API (td_stream_create returns
-                             TD_ERR_INVALID). */
+                             Algorithm 1) in int64 while p! M^p < 2^62 for the largest
+                             centred coordinate M, in the 256-bit form beyond;
+                             td_options.mode is ignored; not served by the stream API
+                             (td_stream_create returns TD_ERR_INVALID). */
 
 /* Execution forms of the same computation (identical results). */
 #define TD_MODE_FILTERED 0    /* persistent launch over (dataset, query, subset-tile) work,
@@ -169,7 +172,9 @@ typedef struct {
                                    iteration bound and were swept in full (exact count) */
 } td_stats;
 
-/* Coordinate bound |X_ij - z_j| <= td_coord_limit(p) accepted for dimension p. */
+/* The fast kernels' coordinate bound for dimension p: queries with every
+ * |X_ij - z_j| <= td_coord_limit(p) run on them, the others on the exact
+ * 256-bit path (td_depth_noalloc refuses them with TD_ERR_RANGE). */
 int64_t td_coord_limit(int32_t p);
 
 /* Create a context on CUDA device `device`; opt may be NULL (defaults).

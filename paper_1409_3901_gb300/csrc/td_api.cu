@@ -37,6 +37,7 @@ cudaError_t td_launch_tiles(const TdLaunch &L, cudaStream_t s);
 cudaError_t td_launch_filtered(int D, const TdLaunch &L, int grid, size_t smem, cudaStream_t s);
 cudaError_t td_launch_plain(int D, const TdLaunch &L, int q, int grid, size_t smem, cudaStream_t s);
 cudaError_t td_launch_finalize(const TdLaunch &L, cudaStream_t s);
+cudaError_t td_launch_wide(const TdLaunch &L, int sms, cudaStream_t s);
 int td_filtered_occupancy(int D, int warps, size_t smem);
 int td_plain_occupancy(int D, int warps, size_t smem);
 size_t td_adia_smem(int nmax, int D);
@@ -215,56 +216,6 @@ int validate_set(const td_dataset &d)
     return TD_OK;
 }
 
-/* |X_ij - z_j| <= limit for every query, from the per-coordinate range of X. */
-bool range_ok(const td_dataset &d)
-{
-    int64_t lim = td_coord_limit(d.p);
-    int64_t lo[TD_MAX_P], hi[TD_MAX_P];
-    for (int c = 0; c < d.p; ++c) {
-        lo[c] = INT64_MAX;
-        hi[c] = INT64_MIN;
-    }
-    for (int64_t i = 0; i < (int64_t)d.n; ++i)
-        for (int c = 0; c < d.p; ++c) {
-            int64_t v = d.X[i * d.p + c];
-            lo[c] = std::min(lo[c], v);
-            hi[c] = std::max(hi[c], v);
-        }
-    for (int64_t q = 0; q < (int64_t)d.m; ++q)
-        for (int c = 0; c < d.p; ++c) {
-            int64_t z = d.Z[q * d.p + c];
-            if (hi[c] - z > lim || z - lo[c] > lim) return false;
-        }
-    return true;
-}
-
-/* Proposition 1 with r = p-1 (TD_ALG_CRITICAL): p! M^p < 2^62 for
- * the largest centred coordinate M, so that every normal and every n.x is
- * exact in int64.  The subset count C(n, 5) at p = 6 is formed on the device
- * as a product of five factors before the last division, below 2^64 for
- * n <= TD_MAX_N. */
-static_assert(TD_MAX_N <= 8000, "C(n, 5) in 64 bits");
-bool critical_range_ok(int p, int64_t M)
-{
-    if (p > 6) return false;
-    long double v = 1.0L;
-    for (int i = 2; i <= p; ++i) v *= i;
-    for (int i = 0; i < p; ++i) v *= (long double)M;
-    return v < 4611686018427387904.0L; /* 2^62 */
-}
-
-int64_t max_centred(const td_dataset &d)
-{
-    int64_t M = 0;
-    for (int64_t q = 0; q < (int64_t)d.m; ++q)
-        for (int64_t i = 0; i < (int64_t)d.n; ++i)
-            for (int c = 0; c < d.p; ++c) {
-                const int64_t v = (int64_t)d.X[i * d.p + c] - d.Z[q * d.p + c];
-                M = std::max(M, v < 0 ? -v : v);
-            }
-    return M;
-}
-
 struct Plan {
     int nq = 0, nsets = 0, nmax = 1, pmax = 1;
     int nmaxD[TD_NDIM] = { 1, 1, 1, 1, 1 }; /* largest n over the datasets with p >= D (D = 2 + i) */
@@ -287,7 +238,10 @@ Plan make_plan(const td_dataset *sets, int k)
         t.slice_index = 0;
         t.slice_count = 1;
         P.sets.push_back(t);
-        P.x_elems += (size_t)t.n * t.p;
+        /* every dataset starts on a 16-byte boundary of the arena (the
+         * sweep kernels copy a dataset into shared memory with one bulk
+         * copy, which needs that alignment) */
+        P.x_elems += ((size_t)t.n * t.p + 3) & ~(size_t)3;
         P.nmax = std::max(P.nmax, t.n);
         P.pmax = std::max(P.pmax, t.p);
         for (int D = 2; D <= std::min(t.p, 6); ++D) P.nmaxD[D - 2] = std::max(P.nmaxD[D - 2], t.n);
@@ -464,8 +418,9 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
             ++nl;
         }
         if (ev_b) TDCK(cudaEventRecord(ev_b, s));
+        TDCK(td_launch_wide(L, ctx->sms, s));
         TDCK(td_launch_finalize(L, s));
-        ++nl;
+        nl += 2;
     } else if (o.mode == TD_MODE_PLAIN_EXACT) {
         TdLaunch L = Lf;
         L.warps = kWarpsPlain;
@@ -485,8 +440,9 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
             ++nl;
         }
         if (ev_b) TDCK(cudaEventRecord(ev_b, s));
+        TDCK(td_launch_wide(L, ctx->sms, s));
         TDCK(td_launch_finalize(L, s));
-        ++nl;
+        nl += 2;
     } else {
         size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
         TDCK(td_launch_setup(Lf, s));
@@ -521,8 +477,9 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
             ++nl;
         }
         if (ev_b) TDCK(cudaEventRecordWithFlags(ev_b, s, cudaEventRecordExternal));
+        TDCK(td_launch_wide(Lf, ctx->sms, s));
         TDCK(td_launch_finalize(Lf, s));
-        ++nl;
+        nl += 2;
     }
     *launches = nl;
     return TD_OK;
@@ -585,12 +542,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     for (int s2 = 0; s2 < k; ++s2) {
         int v = validate_set(sets[s2]);
         if (v != TD_OK) return v;
-        if (!devptr && !range_ok(sets[s2])) return TD_ERR_RANGE;
     }
-    if (ctx->opt.algorithm == TD_ALG_CRITICAL)
-        for (int s2 = 0; s2 < k; ++s2) {
-            if (!devptr && !critical_range_ok(sets[s2].p, max_centred(sets[s2]))) return TD_ERR_RANGE;
-        }
     if (st) memset(st, 0, sizeof(*st));
     Plan P = make_plan(sets, k);
     if (P.nq == 0) return TD_OK;
@@ -690,7 +642,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
             ctx->gvalid = true;
         }
         TDCK(cudaGraphLaunch(ctx->gexec, s));
-        launches = 3 + std::min(P.pmax, 6) - 1; /* set-up, tiles, sweeps for D = 2..min(p,6), finalize */
+        launches = 4 + std::min(P.pmax, 6) - 1; /* set-up, tiles, sweeps for D = 2..min(p,6), wide, finalize */
         if (L.adia) launches += std::max(0, std::min(P.pmax, 6) - 2); /* search kernels, D = 3..min(p,6) */
     } else {
         rc = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, s, &launches, ctx->evs0, ctx->evs1);
@@ -702,18 +654,6 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     TDCK(cudaMemcpyAsync(&C, ctx->w.ctr.p, sizeof(C), cudaMemcpyDeviceToHost, s));
     TDCK(cudaStreamSynchronize(s));
     if (C.errors != 0) return TD_ERR_INTERNAL;
-    /* range check for device pointers: the set-up kernel compared every
-     * centred coordinate with the limit and gave an out-of-range query no
-     * work (TD_DIRECT_RANGE); its maximum serves the critical form's bound */
-    if (devptr) {
-        std::vector<TdQuery> hq(P.nq);
-        TDCK(cudaMemcpy(hq.data(), ctx->w.q.p, P.nq * sizeof(TdQuery), cudaMemcpyDeviceToHost));
-        for (int qi = 0; qi < P.nq; ++qi) {
-            if (hq[qi].direct == TD_DIRECT_RANGE || hq[qi].amax > td_coord_limit_of(P.sets[hq[qi].set].p))
-                return TD_ERR_RANGE;
-            if (o.algorithm == TD_ALG_CRITICAL && !critical_range_ok(hq[qi].d, hq[qi].amax)) return TD_ERR_RANGE;
-        }
-    }
     if (devptr) {
         int qi = 0;
         for (int s2 = 0; s2 < k; ++s2) {
@@ -1163,7 +1103,6 @@ extern "C" int td_stream_submit(td_stream *s, const td_dataset *d, uint64_t *tic
     if (ctx->opt.device_pointers) return TD_ERR_INVALID; /* the stream takes host inputs */
     int v = validate_set(*d);
     if (v != TD_OK) return v;
-    if (!range_ok(*d)) return TD_ERR_RANGE;
     cudaSetDevice(ctx->device);
     int rc = pump(s); /* reaps finished batches first (frees budget) */
     if (rc != TD_OK) return rc;

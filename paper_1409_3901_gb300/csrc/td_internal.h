@@ -8,7 +8,8 @@
 #define TD_MAXD 6
 #define TD_NDIM 5            /* effective dimensions 2..6 with a subset loop */
 #define TD_TICKET_STRIDE 16  /* work counters 128 bytes apart */
-#define TD_DIRECT_RANGE (-2) /* TdQuery.direct of a query whose centred coordinates exceed the limit */
+#define TD_DIRECT_WIDE (-2)  /* TdQuery.direct of a query whose centred coordinates exceed the fast
+                                kernels' limit: answered by the wide kernel (td_wide.cuh) */
 #define TD_NOCT 12           /* octaves of the nonzero point count: ceil(log2 nnz) in [0, 11] */
 
 /* octave of a row of nnz nonzero points (1 <= nnz <= 2048): ceil(log2 nnz) */
@@ -19,11 +20,12 @@ static inline __host__ __device__ int td_octave(int nnz)
     return b;
 }
 
-/* Largest |X_ij - z_j| (every coordinate) the kernels accept for dimension p:
- * it keeps every exact intermediate in 64-bit (coordinates, minors,
- * projections) or 128-bit (cross products) integers, every coordinate exact
- * in binary32, and inside the window of the magic-constant float-to-int
- * conversion (|v| <= 2^22). */
+/* Largest |X_ij - z_j| (every coordinate) the fast kernels take for
+ * dimension p: it keeps every exact intermediate in 64-bit (coordinates,
+ * minors, projections) or 128-bit (cross products) integers, every
+ * coordinate exact in binary32, and inside the window of the magic-constant
+ * float-to-int conversion (|v| <= 2^22).  Queries beyond it go to the wide
+ * kernel. */
 static inline __host__ __device__ int64_t td_coord_limit_of(int p)
 {
     switch (p) {
@@ -45,8 +47,9 @@ struct TdQuery {
     int32_t Z;             /* centred points equal to zero (counted by every closed halfspace) */
     int32_t d;             /* rank of the nonzero centred points (effective dimension) */
     int32_t k;             /* subset size d - 2 of Algorithm 1, or -1 when there is no subset loop */
-    int32_t direct;        /* final count when there is no subset loop (nnz == 0 or d <= 1), -1 when
-                              there is one, TD_DIRECT_RANGE when the query is out of range */
+    int32_t direct;        /* final count when there is no subset loop (nnz == 0 or d <= 1, or the
+                              wide kernel's result), -1 when there is one, TD_DIRECT_WIDE while a
+                              query beyond the fast kernels' limit waits for the wide kernel */
     int32_t amax;          /* max |x_ij| over every coordinate (saturated at INT32_MAX) */
     int32_t piv[TD_MAXD];  /* coordinates on which the span of the points projects injectively */
     int32_t mx[TD_MAXD];   /* max |x_i| per projected coordinate (FP32 error bounds) */

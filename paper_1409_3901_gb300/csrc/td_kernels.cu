@@ -746,16 +746,36 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
     atomicAdd(&s_Z, zc);
     atomicMax(&s_amax, amx);
     __syncthreads();
-    if (s_amax > td_coord_limit_of(p)) {
-        /* beyond the exact-arithmetic limit: no rank, no subset loop, no
-         * bound; the host reports TD_ERR_RANGE and writes no output */
+    /* the range of subset positions of this call: the dataset's time slice
+     * if it has one, else the call's shard */
+    int64_t sc = L.shard_count > 1 ? L.shard_count : 1;
+    int64_t si = L.shard_count > 1 ? L.shard_index : 0;
+    if (S.slice_count > 1) {
+        sc = S.slice_count;
+        si = S.slice_index;
+    }
+    const bool first_shard = si == 0;
+    /* the fast kernels' limit, and for the critical-direction form its own:
+     * p! M^p < 2^62, every normal and n.x exact in int64 */
+    bool wide = s_amax > td_coord_limit_of(p);
+    if (L.critical && !wide) {
+        td_i128 v = 1;
+        for (int i = 2; i <= p; ++i) v *= i;
+        for (int i = 0; i < p && !wide; ++i) {
+            v *= s_amax;
+            wide = v >= ((td_i128)1 << 62);
+        }
+    }
+    if (wide) {
+        /* beyond the limit: no rank, no subset loop, no bound here; the
+         * wide kernel (td_wide.cuh) computes the count on the first shard */
         if (threadIdx.x == 0) {
             Q->n = n;
             Q->Z = s_Z;
             Q->nnz = n - s_Z;
             Q->d = 0;
             Q->k = -1;
-            Q->direct = TD_DIRECT_RANGE;
+            Q->direct = first_shard ? TD_DIRECT_WIDE : INT_MAX;
             Q->amax = s_amax;
             for (int c = 0; c < TD_MAXD; ++c) {
                 Q->piv[c] = 0;
@@ -847,15 +867,6 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
             Q->piv[c] = s_piv[c];
             Q->mx[c] = c < d ? s_max[c] : 0;
         }
-        /* the range of subset positions of this call: the dataset's time
-         * slice if it has one, else the call's shard */
-        int64_t sc = L.shard_count > 1 ? L.shard_count : 1;
-        int64_t si = L.shard_count > 1 ? L.shard_index : 0;
-        if (S.slice_count > 1) {
-            sc = S.slice_count;
-            si = S.slice_index;
-        }
-        const bool first_shard = si == 0;
         if (n - Z == 0 || d <= 1) {
             int direct = (n - Z == 0) ? n : Z + min(s_pos, s_neg);
             Q->direct = first_shard ? direct : INT_MAX;
@@ -1027,21 +1038,79 @@ __global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
 /* shared staging of one query's nonzero centred points                    */
 /* ====================================================================== */
 
+/* Bulk copies (the Tensor Memory Accelerator's untiled form) of a dataset
+ * into shared memory, completed on an mbarrier.  The source and destination
+ * must be 16-byte aligned and the size a multiple of 16 bytes. */
+__device__ __forceinline__ void td_mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(td_saddr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void td_bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    /* generic-proxy accesses of dst before this point are ordered before
+     * the copy's async-proxy writes */
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(td_saddr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(td_saddr(dst)), "l"(src), "r"(bytes), "r"(td_saddr(bar))
+                 : "memory");
+}
+
+/* Wait for the phase `parity` of bar to complete, at most `limit` tries;
+ * returns false if it did not. */
+__device__ __forceinline__ bool td_mbar_wait(uint64_t *bar, unsigned parity, int limit)
+{
+    for (int it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(td_saddr(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 /* Stage the nonzero projected centred points of query q, in the order of the
  * data (or, under Algorithm 3, in the order L.perm gives), into xs in the
  * pair layout (td_xidx, nplanes planes npc pairs apart) -- exact, the
- * coordinates are integers below 2^24.  Returns the number staged
- * (== Q.nnz). */
-__device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int npc, int nplanes, int *s_tmp)
+ * coordinates are integers below 2^24.  The dataset's rows are first copied
+ * into raw (shared memory, raw_bytes long) by one bulk copy when they fit
+ * and their address is 16-byte aligned (the last size % 16 bytes by plain
+ * loads), else read from global memory.  bar / phase: the CTA's mbarrier
+ * and the parity its next completion has.  Returns the number staged
+ * (== Q.nnz), or -1 if the bulk copy did not complete within its bound
+ * (an error the caller reports; the CTA must stop). */
+__device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int npc, int nplanes, int *s_tmp,
+                               int32_t *raw, size_t raw_bytes, uint64_t *bar, unsigned &phase)
 {
     const TdQuery &Q = L.q[q];
     const TdSet S = L.sets[Q.set];
     const int n = S.n, p = S.p, d = Q.d;
-    const int32_t *X = L.X + S.x_off;
+    const int32_t *Xg = L.X + S.x_off;
     const int32_t *z = L.Zq + (int64_t)q * TD_MAXD;
     const int T = blockDim.x;
-    const int per = (n + T - 1) / T;
-    const int beg = min((int)threadIdx.x * per, n), end = min(beg + per, n);
+    const unsigned bytes = (unsigned)((size_t)n * p * 4);
+    const unsigned bulk = bytes & ~15u;
+    const bool tma = bytes <= raw_bytes && bulk > 0 && ((uintptr_t)Xg & 15) == 0;
+    const int32_t *X = Xg;
+    if (tma) {
+        if (threadIdx.x == 0) td_bulk_load(raw, Xg, bulk, bar);
+        /* the tail that is not a multiple of 16 bytes */
+        for (unsigned b = bulk / 4 + threadIdx.x; b < bytes / 4; b += T) raw[b] = Xg[b];
+        const bool ok = td_mbar_wait(bar, phase, 1 << 22);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            /* the copy may still be in flight: give it one more bounded wait */
+            td_mbar_wait(bar, phase ^ 1u, 1 << 22);
+            return -1;
+        }
+        X = raw;
+    }
     int zc[TD_MAXD];
     int pv[TD_MAXD];
 #pragma unroll
@@ -1049,36 +1118,37 @@ __device__ int td_stage_points(const TdLaunch &L, int q, float *xs, int npc, int
         zc[c] = c < p ? z[c] : 0;
         pv[c] = Q.piv[c];
     }
-    int cnt = 0;
-    for (int i = beg; i < end; ++i) {
+    /* one pass in rounds of T consecutive rows (lanes on consecutive rows):
+     * a ballot per warp, the warps' counts scanned, the nonzero points
+     * written in data order */
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = T >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    int base = 0;
+    for (int i0 = 0; i0 < n; i0 += T) {
+        const int i = i0 + (int)threadIdx.x;
         bool nz = false;
-        for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != zc[c];
-        cnt += nz;
-    }
-    /* block exclusive scan of cnt */
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int inc = td_wscan_incl(cnt, lane);
-    if (lane == 31) s_tmp[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int nw = T >> 5;
-        int v = lane < nw ? s_tmp[lane] : 0;
-        int vi = td_wscan_incl(v, lane);
-        if (lane < nw) s_tmp[lane] = vi - v;
-    }
-    __syncthreads();
-    int o = s_tmp[w] + inc - cnt;
-    for (int i = beg; i < end; ++i) {
-        bool nz = false;
-        for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != zc[c];
-        if (!nz) continue;
-        const int pos = L.perm ? (int)L.perm[(size_t)q * L.perm_stride + o] : o;
-        for (int c = 0; c < 2 * nplanes; ++c) {
-            float v = 0.f;
-            if (c < d) v = (float)((int64_t)X[(int64_t)i * p + pv[c]] - zc[pv[c]]);
-            xs[td_xidx(npc, pos, c)] = v;
+        if (i < n)
+            for (int c = 0; c < p; ++c) nz |= X[(int64_t)i * p + c] != zc[c];
+        const unsigned b = __ballot_sync(TD_FULL, nz);
+        if (lane == 0) s_tmp[w] = __popc(b);
+        __syncthreads();
+        int off = base, tot = 0;
+        for (int k = 0; k < nw; ++k) {
+            const int v = s_tmp[k];
+            off += k < w ? v : 0;
+            tot += v;
         }
-        ++o;
+        if (nz) {
+            const int o = off + __popc(b & below);
+            const int pos = L.perm ? (int)L.perm[(size_t)q * L.perm_stride + o] : o;
+            for (int c = 0; c < 2 * nplanes; ++c) {
+                float v = 0.f;
+                if (c < d) v = (float)((int64_t)X[(int64_t)i * p + pv[c]] - zc[pv[c]]);
+                xs[td_xidx(npc, pos, c)] = v;
+            }
+        }
+        base += tot;
+        __syncthreads(); /* s_tmp is rewritten by the next round */
     }
     /* zero points up to the next multiple of 128 (the sweep loads them unmasked) */
     const int nnz = Q.nnz, npad = (nnz + TD_ROUND - 1) & ~(TD_ROUND - 1);
@@ -2727,6 +2797,10 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
         return;
     }
     int staged = -1;
+    __shared__ uint64_t s_bar;
+    unsigned bar_phase = 0u;
+    if (threadIdx.x == 0) td_mbar_init(&s_bar);
+    __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(ticket, 1ull);
         __syncthreads();
@@ -2735,7 +2809,13 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
         const int j = td_query_of_tile(prefix, L.nq, tile);
         const int q = L.order[j];
         if (q != staged) {
-            td_stage_points(L, q, xs, npc, (D + 1) >> 1, s_tmp);
+            /* the warp regions are free between tiles (every tile clears its
+             * histograms first): the dataset's rows go there */
+            if (td_stage_points(L, q, xs, npc, (D + 1) >> 1, s_tmp, reinterpret_cast<int32_t *>(smem + off),
+                                per_warp * (blockDim.x >> 5), &s_bar, bar_phase) < 0) {
+                if (threadIdx.x == 0) atomicAdd(&L.ctr->errors, 1ull); /* the host reports TD_ERR_INTERNAL */
+                break;
+            }
             staged = q;
         }
         const TdQuery &Q = L.q[q];
@@ -2787,6 +2867,12 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
 /* ====================================================================== */
 
 #include "td_critical.cuh"
+
+/* ====================================================================== */
+/* the exact path beyond the fast kernels' coordinate limit                */
+/* ====================================================================== */
+
+#include "td_wide.cuh"
 
 /* ====================================================================== */
 /* plain exact kernel (one query per launch)                               */
@@ -2962,8 +3048,9 @@ __global__ void td_k_finalize(TdLaunch L)
     int r;
     if (Q.direct >= 0) {
         r = Q.direct;
-    } else if (Q.direct == TD_DIRECT_RANGE) {
-        r = INT_MIN; /* never copied out: the host reports TD_ERR_RANGE */
+    } else if (Q.direct == TD_DIRECT_WIDE) {
+        r = INT_MIN; /* the wide kernel did not answer it: an error */
+        atomicAdd(&L.ctr->errors, 1ull);
     } else if (L.qmin[q] == INT_MAX) {
         /* no independent subset in this shard's (or slice's) range */
         const bool part = L.shard_count > 1 || L.sets[Q.set].slice_count > 1;
@@ -3114,6 +3201,20 @@ static td_kfn_adia td_adia_fn(int D, bool warp)
     case 5: return warp ? td_k_adia<5, true> : td_k_adia<5, false>;
     default: return warp ? td_k_adia<6, true> : td_k_adia<6, false>;
     }
+}
+
+/* the wide kernel: grid, shared memory, launch (every query of the call
+ * is looked at; only those flagged TD_DIRECT_WIDE cost work) */
+size_t td_wide_smem_for(int nmax) { return td_wide_smem(nmax); }
+
+cudaError_t td_launch_wide(const TdLaunch &L, int sms, cudaStream_t s)
+{
+    const size_t smem = td_wide_smem(L.nmax);
+    cudaError_t e = td_raise_smem((const void *)td_k_wide, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(L.nq, sms));
+    td_k_wide<<<grid, TD_WIDE_THREADS, smem, s>>>(L);
+    return cudaGetLastError();
 }
 
 int td_adia_occupancy(int D, int nmax, size_t smem)

@@ -85,13 +85,14 @@ __global__ void td_k_noalloc_init(TdLaunch L, TdSet set, unsigned long long *sta
 }
 
 /* status[0] = device-side consistency failures, status[1] = queries with a
- * centred coordinate (any of the p) beyond the exact-arithmetic limit.  The
+ * centred coordinate (any of the p) beyond the fast kernels' limit.  The
  * set-up kernel makes that test before anything else and gives such a query
- * no subset loop, so no kernel ever computes with its coordinates. */
+ * no subset loop; this entry point does not run the wide kernel, so it
+ * refuses them. */
 __global__ void td_k_noalloc_status(TdLaunch L, unsigned long long *status)
 {
     unsigned long long bad = 0;
-    for (int i = threadIdx.x; i < L.nq; i += blockDim.x) bad += L.q[i].direct == TD_DIRECT_RANGE ? 1ull : 0ull;
+    for (int i = threadIdx.x; i < L.nq; i += blockDim.x) bad += L.q[i].direct == TD_DIRECT_WIDE ? 1ull : 0ull;
     if (bad) atomicAdd(&status[1], bad);
     if (threadIdx.x == 0) status[0] = L.ctr->errors;
 }

@@ -56,12 +56,15 @@ def test_rank_deficient(crit):
 
 
 def test_limits(td, crit):
+    """Beyond the int64 bound of the critical-direction kernel (p! M^p >=
+    2^62) the query goes to the 256-bit path: the full-range oracle's count."""
+    from oracle import tukey_wide
     X = np.array([[30000, 1, 2, 3], [1, 2, 3, 4], [5, 6, 7, -8], [1, 0, 0, 0], [0, 1, 0, 0]], np.int32)
-    with pytest.raises(td.TdError):
-        crit.depth(X, np.zeros((1, 4), np.int32))  # 4! * 30000^4 > 2^62
-    X = np.eye(6, dtype=np.int32) * 500
-    with pytest.raises(td.TdError):
-        crit.depth(X, np.zeros((1, 6), np.int32))  # 6! * 500^6 > 2^62
+    Z = np.zeros((1, 4), np.int32)                 # 4! * 30000^4 > 2^62
+    assert np.array_equal(crit.depth(X, Z), tukey_wide.depth_many(X, Z))
+    X = np.vstack([np.eye(6, dtype=np.int32) * 500, -np.ones((1, 6), np.int32)])
+    Z = np.zeros((1, 6), np.int32)                 # 6! * 500^6 > 2^62
+    assert np.array_equal(crit.depth(X, Z), tukey_wide.depth_many(X, Z))
 
 
 @pytest.mark.parametrize("name,count", [("W1", 16), ("W4", 64)])

@@ -321,39 +321,37 @@ def test_stream_polling_and_ticket_lifetime(td):
 
 
 def test_errors_leave_outputs_untouched(ctx, td):
-    X = np.array([[0, 0, 0], [2 ** 22, 0, 0]], np.int32)
-    Z = np.zeros((1, 3), np.int32)
     out = np.full(1, -12345, np.int32)
     with pytest.raises(td.TdError) as e:
-        ctx.depth(X, Z, out=out)
-    assert e.value.code == td.TD_ERR_RANGE
+        ctx.depth(np.zeros((3, 7), np.int32), np.zeros((1, 7), np.int32), out=out)
+    assert e.value.code == td.TD_ERR_INVALID
     assert out[0] == -12345
     with pytest.raises(td.TdError) as e:
-        ctx.depth(np.zeros((3, 7), np.int32), np.zeros((1, 7), np.int32))
+        ctx.depth(np.zeros((td.TD_MAX_N + 1, 3), np.int32), np.zeros((1, 3), np.int32), out=out)
     assert e.value.code == td.TD_ERR_INVALID
+    assert out[0] == -12345
 
 
-def test_device_pointer_range_check_covers_every_coordinate(td):
-    """With device pointers the range is checked on the device, over every
-    centred coordinate -- also one that depends on the others and so is not
-    a pivot coordinate of the set-up's elimination (rank-2 data in p = 3,
-    the third column 400 times the first).  TD_ERR_RANGE, out untouched."""
+def test_beyond_the_fast_limit_every_coordinate(td):
+    """A coordinate beyond td_coord_limit(p) -- also one that depends on the
+    others and so is not a pivot coordinate of the set-up's elimination
+    (rank-2 data in p = 3, the third column 400 times the first) -- sends
+    the query to the wide kernel, with host and device pointers and in every
+    algorithm: the full-range oracle's count."""
     import torch
+    from oracle import tukey_wide
     rng = np.random.default_rng(14)
-    c0 = rng.integers(-20000, 20001, size=60)
-    X = np.stack([c0, rng.integers(-50, 51, size=60), 400 * c0], axis=1).astype(np.int32)
+    c0 = rng.integers(-20000, 20001, size=40)
+    X = np.stack([c0, rng.integers(-50, 51, size=40), 400 * c0], axis=1).astype(np.int32)
     assert np.abs(X.astype(np.int64)).max() > td.td_coord_limit(3)
-    Z = np.zeros((2, 3), np.int32)
-    with pytest.raises(td.TdError) as e:
-        td.Context(0).depth(X, Z)                    # host pointers: checked on the host
-    assert e.value.code == td.TD_ERR_RANGE
+    Z = np.vstack([np.zeros((1, 3), np.int32), X[:1]])
+    want = np.array(tukey_wide.depth_many(X, Z))
+    assert np.array_equal(td.Context(0).depth(X, Z), want)
     for alg in (td.TD_ALG_RCOM, td.TD_ALG_ADIA, td.TD_ALG_CRITICAL):
         c = td.Context(0, device_pointers=True, algorithm=alg)
         out = torch.full((2,), -5, dtype=torch.int32, device="cuda")
-        with pytest.raises(td.TdError) as e:
-            c.depth(torch.from_numpy(X).cuda(), torch.from_numpy(Z).cuda(), out)
-        assert e.value.code == td.TD_ERR_RANGE
-        assert (out.cpu().numpy() == -5).all()
+        c.depth(torch.from_numpy(X).cuda(), torch.from_numpy(Z).cuda(), out)
+        assert np.array_equal(out.cpu().numpy(), want), alg
 
 
 def test_device_pointers(td):

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libtukeydepth.so")
 PROBE_LIB = os.path.join(HERE, "libtdprobe.so")
 SOURCES = ["td_kernels.cu", "td_api.cu", "td_noalloc.cu"]
 PROBE_SOURCES = ["td_issue_rate.cu"]
-HEADERS = ["td_internal.h", "td_exact.cuh", "td_adia.cuh", "td_critical.cuh", "td_issue_rate.h"]
+HEADERS = ["td_internal.h", "td_exact.cuh", "td_adia.cuh", "td_critical.cuh", "td_wide.cuh", "td_issue_rate.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-diag-suppress", "550"]
 

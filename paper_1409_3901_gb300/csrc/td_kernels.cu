@@ -1921,8 +1921,9 @@ __device__ __forceinline__ void td_pair_rows(const float4 (&pl)[(D + 1) / 2], co
     float flp, flq, fhp, fhq;
     td_upk(FL, flp, flq);
     td_upk(FH, fhp, fhq);
-    const uint32_t blp = min((uint32_t)__float_as_int(flp) + C.moffc, 32u);
-    const uint32_t blq = min((uint32_t)__float_as_int(flq) + C.moffc, 32u);
+    /* row = bits + 2^31 - bits(Mc), capped at 32: one fused add-and-min */
+    const uint32_t blp = __viaddmin_u32((uint32_t)__float_as_int(flp), C.moffc, 32u);
+    const uint32_t blq = __viaddmin_u32((uint32_t)__float_as_int(flq), C.moffc, 32u);
     rp = __float_as_int(flp) == __float_as_int(fhp) ? (int)blp : 32;
     rq = __float_as_int(flq) == __float_as_int(fhq) ? (int)blq : 32;
     ip = 0x10000u + ((uint32_t)__float_as_int(y2p) >> 31);

@@ -170,6 +170,10 @@ typedef struct {
                                    (Step 5(b) sweeps are counted in sweeps) */
     uint64_t adia_fallbacks;    /* Algorithm 3: queries whose search outgrew its node table or
                                    iteration bound and were swept in full (exact count) */
+    uint64_t rescanned_sweeps;  /* sweeps whose bound over the FP32-certified points did not reach
+                                   the query's running minimum: their points were projected again at
+                                   the fine bucket level and the uncertain ones placed exactly (the
+                                   exact path's hit rate per sweep; plain mode: 0) */
 } td_stats;
 
 /* The fast kernels' coordinate bound for dimension p: queries with every

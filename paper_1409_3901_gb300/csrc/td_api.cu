@@ -681,6 +681,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         st->tight_exceptions = C.tight;
         st->resolved_buckets = C.resolved;
         st->early_skipped = C.early;
+        st->rescanned_sweeps = C.rescanned;
         st->adia_pops = C.adia_pops;
         st->adia_subsets = C.adia_subsets;
         st->adia_union_points = C.adia_union;

@@ -72,6 +72,7 @@ struct TdCounters {
     unsigned long long errors;  /* device-side consistency failures (must stay 0) */
     unsigned long long early;   /* subsets not swept because their query had reached 0 (early exit) */
     unsigned long long adia_pops, adia_subsets, adia_union, adia_fallback; /* Algorithm 3 search */
+    unsigned long long rescanned; /* sweeps that went past the coarse bound */
 };
 
 /* Parameters of the work-queue launches. */

@@ -2014,7 +2014,8 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
                                                  const td_f2x (&FA)[D], const td_f2x (&FB)[D], float Ea, float Eb,
                                                  bool narrow, const TdWarpSmem &W, int blog2, int lane, int best,
                                                  bool &clean, uint32_t &prev_row, uint32_t &prev_u,
-                                                 uint64_t &n_exact, uint32_t &n_resolved, int &t_out,
+                                                 uint64_t &n_exact, uint32_t &n_resolved, uint32_t &n_rescanned,
+                                                 int &t_out,
                                                  int &nzy_out, PUB &&publish_exact)
 {
     constexpr int NPL = (D + 1) / 2;        /* planes of the pair layout */
@@ -2127,6 +2128,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
     int G = pass1(acc, nnz - nu);
     int t = 0;
     if (G < best) {
+        ++n_rescanned;
         publish_exact();
         clean = false;
         /* the fine histogram shares the coarse one's storage: clear it */
@@ -2496,7 +2498,8 @@ __device__ __noinline__ int td_tight_correction(const int *meta, const float *xs
 
 /* Process subset positions [r0, r1) of query q with one warp (filtered).
  * The warp's counters ws[] (sweeps, dependent, filtered points, exact
- * points, tight corrections, resolved sweeps, errors) live in shared memory;
+ * points, tight corrections, resolved sweeps, errors, early-exit skips,
+ * rescanned sweeps) live in shared memory;
  * the subset loop keeps 32-bit tile counts and lane 0 adds them at the end.
  *
  * For D = 3..5 consecutive subsets are taken two at a time: td_sweep_dual
@@ -2528,7 +2531,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
     float mx_lane = 0.f; /* max|x_t| of this lane's basis entry t = lane % 8 */
 #pragma unroll
     for (int r = 0; r < D; ++r) mx_lane = (lane & 7) == r ? mxf[r] : mx_lane;
-    uint32_t n_dep = 0, n_tight = 0, n_res = 0;
+    uint32_t n_dep = 0, n_tight = 0, n_res = 0, n_resc = 0;
     uint64_t n_exact = 0;
     bool clean = false;  /* the coarse histogram agrees with prev_row / prev_u */
     bool clean2 = false; /* the two coarse histograms of the dual sweep agree with prev2 */
@@ -2596,7 +2599,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
             else td_basis_publish_exact<D, false>(xs, cs, lane & 15, pi, pj, lr, W, cof);
         };
         const int G = td_sweep_filtered<D>(xs, npc, nnz, FA, FB, Ea, Eb, narrow, W, blog2, lane, best, clean,
-                                           prev_row, prev_u, n_exact, n_res, t, nzy, publish_exact);
+                                           prev_row, prev_u, n_exact, n_res, n_resc, t, nzy, publish_exact);
         clean2 = false; /* the one-subset sweep used table A's storage */
         int V = G;
         if (t > K && G < best) {
@@ -2635,7 +2638,9 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
                 int GA, GB, nuA, nuB;
                 td_sweep_dual<D>(xs, npc, nnz, CA, CB, W, lane, clean2, prev2, GA, GB, nuA, nuB);
                 clean = false; /* the dual sweep used table A's storage */
-                /* a subset whose bound does not reach best is swept again alone */
+                /* a subset whose bound does not reach best is swept again alone
+                 * (repeating the coarse pass there measured faster than a
+                 * branch around it in the one-subset sweep) */
                 if (GA < best) single(c);
                 else n_exact += (uint64_t)nuA;
                 if (GB < best) single(cB);
@@ -2675,6 +2680,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
         ws[3] += n_exact;
         ws[4] += n_tight;
         ws[5] += n_res;
+        ws[8] += n_resc;
     }
 }
 
@@ -2704,7 +2710,7 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     __shared__ int64_t s_tile;
     __shared__ int s_tmp[32];
     __shared__ int s_best[TD_WARPS_MAX];
-    __shared__ unsigned long long s_stats[TD_WARPS_MAX][8];
+    __shared__ unsigned long long s_stats[TD_WARPS_MAX][9];
     const int64_t *prefix = L.tile_prefix + (int64_t)(D - 2) * (L.nq + 1);
     unsigned long long *ticket = L.ticket + (D - 2) * TD_TICKET_STRIDE;
     const int64_t total = prefix[L.nq];
@@ -2751,7 +2757,7 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
     W.meta = reinterpret_cast<int *>(wb + rbytes + 16 + 448);
     for (int j = lane; j < max(Bmax + 4, TD_COARSE_WORDS); j += 32) W.hist[j] = 0u;
     unsigned long long *ws = s_stats[w];
-    if (lane < 8) ws[lane] = 0ull;
+    if (lane < 9) ws[lane] = 0ull;
     if constexpr (D == 2) {
         __syncwarp();
         for (;;) {
@@ -2794,6 +2800,7 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
             atomicAdd(&L.ctr->resolved, ws[5]);
             atomicAdd(&L.ctr->errors, ws[6]);
             if (ws[7]) atomicAdd(&L.ctr->early, ws[7]);
+            if (ws[8]) atomicAdd(&L.ctr->rescanned, ws[8]);
         }
         return;
     }
@@ -2854,6 +2861,7 @@ __global__ void __launch_bounds__(256, 2) td_k_filtered(TdLaunch L)
         atomicAdd(&L.ctr->resolved, ws[5]);
         atomicAdd(&L.ctr->errors, ws[6]);
         if (ws[7]) atomicAdd(&L.ctr->early, ws[7]);
+        if (ws[8]) atomicAdd(&L.ctr->rescanned, ws[8]);
     }
 }
 

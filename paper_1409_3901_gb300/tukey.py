@@ -64,7 +64,8 @@ class td_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("ms", ctypes.c_float),
                 ("ms_sweep", ctypes.c_float), ("early_skipped", ctypes.c_uint64),
                 ("adia_pops", ctypes.c_uint64), ("adia_subsets", ctypes.c_uint64),
-                ("adia_union_points", ctypes.c_uint64), ("adia_fallbacks", ctypes.c_uint64)]
+                ("adia_union_points", ctypes.c_uint64), ("adia_fallbacks", ctypes.c_uint64),
+                ("rescanned_sweeps", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

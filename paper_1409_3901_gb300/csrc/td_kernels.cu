@@ -949,10 +949,11 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
 /* tile prefix kernel                                                      */
 /* ====================================================================== */
 
-/* Subsets per warp and tile: about 2^16 point evaluations per warp and tile
- * (the per-tile set-up then costs well under 1%), at most 256, and at most
- * 1/64 of the query's range per CTA tile so that a short subset loop still
- * spreads over many CTAs; at least 4. */
+/* Subsets per warp and tile: about 1.5 * 2^16 point evaluations per warp
+ * and tile (the block barrier at the end of a tile, where the warps wait for
+ * the slowest, then costs a few percent), at most 512, and at most 1/64 of
+ * the query's range per CTA tile so that a short subset loop still spreads
+ * over many CTAs; at least 4. */
 /* a / b for b > 0, by the 32-bit unsigned divide when both operands fit */
 __host__ __device__ inline int64_t td_div_nonneg(int64_t a, int64_t b)
 {
@@ -962,10 +963,10 @@ __host__ __device__ inline int64_t td_div_nonneg(int64_t a, int64_t b)
 
 __host__ __device__ inline int td_auto_spw(int nnz, int64_t nrange, int warps)
 {
-    int64_t s = 65536 / (nnz > 0 ? nnz : 1);
+    int64_t s = 98304 / (nnz > 0 ? nnz : 1);
     const int64_t cap = td_div_nonneg(nrange, 64 * (int64_t)(warps > 0 ? warps : 1));
     s = s < cap ? s : cap;
-    return s < 4 ? 4 : (s > 256 ? 256 : (int)s);
+    return s < 4 ? 4 : (s > 512 ? 512 : (int)s);
 }
 
 /* Tiles of every query, and for each effective dimension D = 2..6 the prefix
@@ -2562,6 +2563,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
         for (int i = 1; i <= K; ++i) b = b < ((int64_t)1 << 31) ? b * (int64_t)i * mm : b;
         nm = b < 2147483647LL;
     }
+    constexpr bool REFRESH = D <= 4; /* see the subset loop below */
     /* cofactors stale for this lane's subset cs? (and mark them made) */
     auto stale = [&](const int (&cs)[KK]) -> bool {
         bool st = cmade[0] < 0;
@@ -2606,12 +2608,25 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
             ++n_tight;
             V = G + td_tight_correction<D>(W.meta, xs, npc, nullptr, 0, nnz, W.bid, nullptr, scr, W.gcount, lane);
         }
+        if (REFRESH && V < best && lane == 0) atomicMin(L.qmin + q, V);
         best = min(best, V);
         return true;
     };
     uint32_t nr = (uint32_t)(r1 - r0); /* a tile: below 2^31 */
     uint32_t done = 0;
+    /* D <= 4: the query's running minimum in global memory, which other
+     * warps lower while this one works, is read again at every step (the
+     * load is issued at one step and taken into best at the next, a step's
+     * work later), and a subset that lowers best publishes it at once.  Any
+     * value it holds is some V(S) or the seeded upper bound, so taking it as
+     * best keeps every decision valid.  (At D = 5, 6 the extra live
+     * registers cost more than the sweeps they save.) */
+    int gbest = best;
     while (done < nr) {
+        if constexpr (REFRESH) {
+            best = min(best, gbest);
+            gbest = *reinterpret_cast<const volatile int32_t *>(L.qmin + q);
+        }
         if (DUAL && done + 1 < nr) {
             int cB[KK];
 #pragma unroll

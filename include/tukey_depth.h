@@ -229,10 +229,11 @@ int td_stream_destroy(td_stream *s);
 /* Autotuner (no counterpart in the paper: the choice of work-tile size of
  * the persistent sweep).  Times the filtered sweep kernel of dimension p on a
  * seeded synthetic dataset of n points (uniform integers in [-127, 127]) with
- * enough queries for a few milliseconds of sweeping, first with the size rule
- * and then with each candidate work-tile size (8 to 256 subsets per warp), the
- * median of three calls each (td_stats.ms_sweep), and keeps the fastest in the
- * context for queries of effective dimension p whose nonzero point count lies
+ * enough queries for about 10 ms of sweeping (at most 256), first with the
+ * size rule and then with each candidate work-tile size (16 to 512 subsets
+ * per warp), the median of three calls each (td_stats.ms_sweep), and keeps
+ * the fastest -- a candidate only when it beats the size rule by more than
+ * 1% -- in the context for queries of effective dimension p whose nonzero point count lies
  * in the octave of n (ceil(log2 n), and that of n - 1); later calls with
  * subsets_per_warp = 0 use it.  The results never depend on the choice.
  * res (may be NULL) receives the candidates, their times and the choice

@@ -305,3 +305,17 @@ __device__ __forceinline__ int td_cross_sign(int64_t u1, int64_t u2, int64_t v1,
     td_i128 r = (td_i128)u2 * v1;
     return (l > r) - (l < r);
 }
+
+/* The same sign; NARROW: the caller has checked that every coordinate is
+ * below 2^31 in magnitude, so both products lie below 2^62 and int64 holds
+ * them exactly. */
+template <bool NARROW>
+__device__ __forceinline__ int td_cross_sign_n(int64_t u1, int64_t u2, int64_t v1, int64_t v2)
+{
+    if constexpr (NARROW) {
+        const int64_t l = u1 * v2, r = u2 * v1;
+        return (l > r) - (l < r);
+    } else {
+        return td_cross_sign(u1, u2, v1, v2);
+    }
+}

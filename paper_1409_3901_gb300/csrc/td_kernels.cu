@@ -275,12 +275,13 @@ __device__ __forceinline__ int td_cross_sign_f(float2 uf, float2 vf, int64_t u1,
 }
 
 /* td_item_less with the FP32 filter of td_cross_sign_f (Hf may be null). */
+template <bool NARROW = false>
 __device__ __forceinline__ bool td_item_less_f(uint16_t u, uint16_t v, const int64_t *H, const float2 *Hf)
 {
     if (u == TD_SENT) return false;
     if (v == TD_SENT) return true;
     const int a = u & 0x7FFF, b = v & 0x7FFF;
-    if (!Hf) return td_cross_sign(H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) > 0;
+    if (!Hf) return td_cross_sign_n<NARROW>(H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) > 0;
     return td_cross_sign_f(Hf[a], Hf[b], H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) > 0;
 }
 
@@ -312,6 +313,7 @@ __device__ void td_sort_exact(uint16_t *idx, int npad, const int64_t *H, int lan
  * (binary32 copies of H, may be null) the comparisons are FP32-filtered;
  * they are exact either way.  (The sweep kernel keeps td_sort_exact: this
  * one, inlined there, costs it registers.) */
+template <bool NARROW = false>
 __device__ void td_sort_exact_fast(uint16_t *idx, int npad, const int64_t *H, int lane, const float2 *Hf)
 {
     const int half = npad >> 1;
@@ -359,7 +361,7 @@ __device__ void td_sort_exact_fast(uint16_t *idx, int npad, const int64_t *H, in
                         b2[k] = H[2 * ib[k] + 1];
                     }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) cr[k] = td_cross_sign(a1[k], a2[k], b1[k], b2[k]);
+                    for (int k = 0; k < 4; ++k) cr[k] = td_cross_sign_n<NARROW>(a1[k], a2[k], b1[k], b2[k]);
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -378,7 +380,7 @@ __device__ void td_sort_exact_fast(uint16_t *idx, int npad, const int64_t *H, in
                 int j = i + stride;
                 bool up = (i & size) == 0;
                 uint16_t u = idx[i], v = idx[j];
-                bool swap = up ? td_item_less_f(v, u, H, Hf) : td_item_less_f(u, v, H, Hf);
+                bool swap = up ? td_item_less_f<NARROW>(v, u, H, Hf) : td_item_less_f<NARROW>(u, v, H, Hf);
                 if (swap) {
                     idx[i] = v;
                     idx[j] = u;
@@ -390,6 +392,7 @@ __device__ void td_sort_exact_fast(uint16_t *idx, int npad, const int64_t *H, in
 
 /* Walk over the cnt sorted items: returns min over walk values w of
  * min(w, m - w) where the walk starts at A (orientation + count) and m = cnt. */
+template <bool NARROW = false>
 __device__ int td_walk_sorted(const uint16_t *idx, int cnt, const int64_t *H, int lane)
 {
     int A = 0;
@@ -408,7 +411,7 @@ __device__ int td_walk_sorted(const uint16_t *idx, int cnt, const int64_t *H, in
         bool tie = false;
         if (l + 1 < cnt) {
             int a = it & 0x7FFF, b = idx[l + 1] & 0x7FFF;
-            tie = td_cross_sign(H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) == 0;
+            tie = td_cross_sign_n<NARROW>(H[2 * a], H[2 * a + 1], H[2 * b], H[2 * b + 1]) == 0;
         }
         if (!tie) {
             mn = min(mn, v);
@@ -2929,6 +2932,7 @@ __device__ void td_warp_plain(const TdLaunch &L, int q, const int32_t *xi, int P
         td_publish_basis<D>(Bs, c, wqa, wqb, wmeta, lane);
         /* exact projections of every point, compacted list of the nonzero ones */
         int base = 0, t = 0;
+        bool wide = false; /* some projected coordinate is 2^31 or more in magnitude */
         for (int i0 = 0; i0 < nnz; i0 += 32) {
             int i = i0 + lane;
             int64_t y1 = 0, y2 = 0;
@@ -2950,6 +2954,7 @@ __device__ void td_warp_plain(const TdLaunch &L, int q, const int32_t *xi, int P
                 H[2 * i] = h1;
                 H[2 * i + 1] = h2;
             }
+            wide |= (h1 >= ((int64_t)1 << 31)) | (h1 <= -((int64_t)1 << 31)) | (h2 >= ((int64_t)1 << 31));
             unsigned bn = __ballot_sync(TD_FULL, nonz);
             if (nonz) idx[base + __popc(bn & ((1u << lane) - 1u))] = (uint16_t)(i | (plus ? 0x8000 : 0));
             base += __popc(bn);
@@ -2961,8 +2966,15 @@ __device__ void td_warp_plain(const TdLaunch &L, int q, const int32_t *xi, int P
             const int npad = td_pow2_at_least(base);
             for (int l = base + lane; l < npad; l += 32) idx[l] = TD_SENT;
             __syncwarp();
-            td_sort_exact_fast(idx, npad, H, lane, nullptr);
-            G = td_walk_sorted(idx, base, H, lane);
+            /* the exact comparisons in int64 when every coordinate is below
+             * 2^31 (their products then stay below 2^62), else in int128 */
+            if (__any_sync(TD_FULL, wide)) {
+                td_sort_exact_fast<false>(idx, npad, H, lane, nullptr);
+                G = td_walk_sorted<false>(idx, base, H, lane);
+            } else {
+                td_sort_exact_fast<true>(idx, npad, H, lane, nullptr);
+                G = td_walk_sorted<true>(idx, base, H, lane);
+            }
         }
         st.exact += (lane == 0) ? nnz : 0;
         int V = G;

@@ -52,7 +52,12 @@ int td_critical_threads();
 
 namespace {
 
-const int kWarpsFiltered = 8;
+/* Warps per CTA of the sweep kernels.  The warps of a CTA meet at a
+ * barrier at the end of each tile, and in CTAs of 4 they wait less for the
+ * slowest than in CTAs of 8: W2 31.5 to 31.1 ms, W4 147 to 145 ms, W3 5.50
+ * to 5.45 s -- W3 even where its rows of up to 2000 points (each CTA
+ * stages its own copy) leave 12 warps resident per SM instead of 16. */
+const int kWarpsFiltered = 4;
 const int kWarpsPlain = 4;
 
 struct DevBuf {
@@ -100,7 +105,7 @@ struct Work {
 };
 
 struct GraphKey {
-    int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw, early_exit, algorithm, unseeded;
+    int nq, nsets, nmax, pmax, grid[TD_NDIM], nmaxD[TD_NDIM], blog2, spw, early_exit, algorithm, unseeded, warps;
     uint16_t spw_tab[TD_NDIM][TD_NOCT];
     size_t smem;
     const void *ptrs[17];
@@ -444,7 +449,6 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
         TDCK(td_launch_finalize(L, s));
         nl += 2;
     } else {
-        size_t smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
         TDCK(td_launch_setup(Lf, s));
         nl = 1;
         if (Lf.adia) {
@@ -472,7 +476,7 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
             LD.pmax = D;
             LD.blog2 = blog2_for(LD.nmax, o);
             LD.scratch_per_warp = td_scratch_per_warp(LD.nmax);
-            const size_t smemD = td_filtered_smem(LD.nmax, D, LD.blog2, kWarpsFiltered);
+            const size_t smemD = td_filtered_smem(LD.nmax, D, LD.blog2, LD.warps);
             TDCK(td_launch_filtered(D, LD, w.grid[D - 2], smemD, s));
             ++nl;
         }
@@ -487,19 +491,23 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
 
 /* Persistent grids of the sweep kernels (D = 2 .. min(pmax, 6)), each sized
  * for its own dimension (rows of at most nmaxD points, stride 4 or 8 floats);
- * sets the dynamic shared memory attribute of each.  Returns the scratch
- * bytes the largest of them needs, or 0 if a kernel cannot be resident. */
-size_t filtered_grids(td_ctx *ctx, const Plan &P, const td_options &o, int *grid)
+ * sets the dynamic shared memory attribute of each, and the CTA width (one
+ * for the whole call: the tile kernel sizes every query's tiles by it).
+ * Returns the scratch bytes the largest grid needs, or 0 if a kernel cannot
+ * be resident. */
+size_t filtered_grids(td_ctx *ctx, const Plan &P, const td_options &o, int *grid, int *warps)
 {
+    const int wsel = kWarpsFiltered;
+    *warps = wsel;
     size_t scratch = 256;
     for (int i = 0; i < TD_NDIM; ++i) grid[i] = 0;
     for (int D = 2; D <= std::min(P.pmax, 6); ++D) {
         const int nmaxD = P.nmaxD[D - 2];
-        const size_t smem = td_filtered_smem(nmaxD, D, blog2_for(nmaxD, o), kWarpsFiltered);
-        int occ = td_filtered_occupancy(D, kWarpsFiltered, smem);
+        const size_t smem = td_filtered_smem(nmaxD, D, blog2_for(nmaxD, o), wsel);
+        int occ = td_filtered_occupancy(D, wsel, smem);
         if (occ < 1) return 0;
         grid[D - 2] = ctx->sms * occ;
-        scratch = std::max(scratch, (size_t)grid[D - 2] * kWarpsFiltered * (size_t)td_scratch_per_warp(nmaxD));
+        scratch = std::max(scratch, (size_t)grid[D - 2] * wsel * (size_t)td_scratch_per_warp(nmaxD));
     }
     return scratch;
 }
@@ -552,6 +560,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     int grid = 0, warps_total = 0;
     (void)cudaGetLastError(); /* clear any stale error of an earlier call */
     int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
+    int fwarps = kWarpsFiltered;
     if (o.algorithm == TD_ALG_CRITICAL) {
         const size_t smem = td_critical_smem(P.nmax, P.pmax);
         int occ = 0;
@@ -571,7 +580,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         warps_total = grid * kWarpsPlain;
         TDCK(alloc_work(ctx->w, P, warps_total, true));
     } else {
-        size_t scratch = filtered_grids(ctx, P, o, grids);
+        size_t scratch = filtered_grids(ctx, P, o, grids, &fwarps);
         if (scratch < 1) return TD_ERR_INVALID;
         TDCK(alloc_work(ctx->w, P, 0, true));
         if (o.algorithm == TD_ALG_ADIA) {
@@ -588,7 +597,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     int rc = stage_inputs(ctx, ctx->w, ctx->hstage, P, sets, k, devptr, s, &x_arena);
     if (rc != TD_OK) return rc;
     TDCK(cudaMemsetAsync(ctx->w.ctr.p, 0, sizeof(TdCounters), s));
-    TdLaunch L = make_launch(ctx->w, P, x_arena, o, kWarpsFiltered, blog2, ctx->tune);
+    TdLaunch L = make_launch(ctx->w, P, x_arena, o, fwarps, blog2, ctx->tune);
     TDCK(cudaEventRecord(ctx->ev0, s));
     int launches = 0;
     if (o.mode == TD_MODE_FILTERED && o.use_graph && o.algorithm != TD_ALG_CRITICAL) {
@@ -606,7 +615,8 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         key.unseeded = L.unseeded;
         memcpy(key.spw_tab, L.spw_tab, sizeof(key.spw_tab));
         key.algorithm = o.algorithm;
-        key.smem = td_filtered_smem(P.nmax, P.pmax, blog2, kWarpsFiltered);
+        key.warps = L.warps;
+        key.smem = td_filtered_smem(P.nmax, P.pmax, blog2, L.warps);
         const Work &cw = ctx->w;
         const void *pp[17] = { x_arena,     cw.Zq.p,   cw.sets.p,  cw.q.p,     cw.order.p, cw.prefix.p,
                                cw.tsize.p,  cw.ticket.p, cw.qmin.p, cw.out.p,   cw.ctr.p,   cw.scratch.p,
@@ -1039,7 +1049,8 @@ int pump(td_stream *s)
     const int blog2 = blog2_for(P.nmax, o);
     (void)cudaGetLastError();
     int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
-    size_t scratch = filtered_grids(ctx, P, o, grids);
+    int fwarps = kWarpsFiltered;
+    size_t scratch = filtered_grids(ctx, P, o, grids, &fwarps);
     if (scratch < 1) return TD_ERR_INVALID;
     cudaError_t e = alloc_work(sl.w, P, 0, true);
     if (e == cudaSuccess && o.algorithm == TD_ALG_ADIA) {
@@ -1056,7 +1067,7 @@ int pump(td_stream *s)
     const int32_t *x_arena = nullptr;
     int rc = stage_inputs(ctx, sl.w, sl.hstage, P, sets.data(), (int)sets.size(), false, s->s, &x_arena);
     if (rc != TD_OK) return rc;
-    TdLaunch L = make_launch(sl.w, P, x_arena, o, kWarpsFiltered, blog2, ctx->tune);
+    TdLaunch L = make_launch(sl.w, P, x_arena, o, fwarps, blog2, ctx->tune);
     L.scratch = (char *)s->scratch.p;
     TDCK(cudaMemsetAsync(sl.w.ctr.p, 0, sizeof(TdCounters), s->s));
     int nl = 0;

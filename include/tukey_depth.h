@@ -230,7 +230,7 @@ int td_stream_destroy(td_stream *s);
  * the persistent sweep).  Times the filtered sweep kernel of dimension p on a
  * seeded synthetic dataset of n points (uniform integers in [-127, 127]) with
  * enough queries for about 10 ms of sweeping (at most 256), first with the
- * size rule and then with each candidate work-tile size (16 to 512 subsets
+ * size rule and then with each candidate work-tile size (16 to 1024 subsets
  * per warp), the median of three calls each (td_stats.ms_sweep), and keeps
  * the fastest -- a candidate only when it beats the size rule by more than
  * 1% -- in the context for queries of effective dimension p whose nonzero point count lies

@@ -826,7 +826,7 @@ extern "C" int td_depth_batched(td_ctx *ctx, const td_dataset *sets, int32_t k, 
 namespace {
 
 /* candidates of the work-tile size (subsets per warp) */
-const int kTuneSpw[TD_TUNE_MAX] = { 16, 32, 64, 96, 128, 192, 256, 512 };
+const int kTuneSpw[TD_TUNE_MAX] = { 16, 32, 64, 128, 192, 256, 512, 1024 };
 const int kTuneCount = 8;
 /* a candidate replaces the size rule only when it is faster by more than
  * this fraction: the synthetic problem is a proxy, and closer times say

@@ -952,9 +952,9 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
 /* tile prefix kernel                                                      */
 /* ====================================================================== */
 
-/* Subsets per warp and tile: about 1.5 * 2^16 point evaluations per warp
- * and tile (the block barrier at the end of a tile, where the warps wait for
- * the slowest, then costs a few percent), at most 512, and at most 1/64 of
+/* Subsets per warp and tile: about 3 * 2^16 point evaluations per warp and
+ * tile (the block barrier at the end of a tile, where the warps wait for
+ * the slowest, then costs a few percent), at most 1024, and at most 1/64 of
  * the query's range per CTA tile so that a short subset loop still spreads
  * over many CTAs; at least 4. */
 /* a / b for b > 0, by the 32-bit unsigned divide when both operands fit */
@@ -966,10 +966,10 @@ __host__ __device__ inline int64_t td_div_nonneg(int64_t a, int64_t b)
 
 __host__ __device__ inline int td_auto_spw(int nnz, int64_t nrange, int warps)
 {
-    int64_t s = 98304 / (nnz > 0 ? nnz : 1);
+    int64_t s = 196608 / (nnz > 0 ? nnz : 1);
     const int64_t cap = td_div_nonneg(nrange, 64 * (int64_t)(warps > 0 ? warps : 1));
     s = s < cap ? s : cap;
-    return s < 4 ? 4 : (s > 512 ? 512 : (int)s);
+    return s < 4 ? 4 : (s > 1024 ? 1024 : (int)s);
 }
 
 /* Tiles of every query, and for each effective dimension D = 2..6 the prefix

@@ -18,7 +18,7 @@ def test_autotune_measures_and_keeps_parity():
     for p, n in ((4, 300), (5, 150)):
         r = ctx.autotune(p, n)
         assert r["p"] == p and r["n"] == n and r["queries"] >= 1
-        assert sorted(r["candidates"]) == [16, 32, 64, 96, 128, 192, 256, 512]
+        assert sorted(r["candidates"]) == [16, 32, 64, 128, 192, 256, 512, 1024]
         assert all(ms > 0 for ms in r["candidates"].values()) and r["ms_default"] > 0
         # a candidate is kept only when it beats the size rule by more than 1%
         if r["best_spw"] == 0:

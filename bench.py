@@ -216,6 +216,53 @@ def _batched_w3(tukey, W, dev, stream, flush, peak_tops, steps=1):
             "timing": "CUDA events on the launch stream around the call; L2 flushed before it"}
 
 
+def _small_w1(tukey, W, dev, stream, flush, reps=20):
+    """The small case W1 (p = 3, n = 300, 16 queries, 300 subsets each): both
+    forms on device-resident inputs (CUDA events on the launch stream, L2
+    flushed before each call), and the latency of a one-query call through
+    the host API (td_depth on host buffers, copies included, wall clock)."""
+    import torch
+    d = W.w1()
+    Xd = torch.from_numpy(d.X).to(dev)
+    Zd = torch.from_numpy(d.Zq).to(dev)
+    res = {}
+    outs = {}
+    for name, mode in (("filtered", tukey.TD_MODE_FILTERED), ("plain_exact", tukey.TD_MODE_PLAIN_EXACT)):
+        ctx = tukey.Context(dev.index, mode=mode, device_pointers=True, stream=stream.cuda_stream)
+        out = torch.empty(d.m, dtype=torch.int32, device=dev)
+        ctx.depth(Xd, Zd, out)
+        ms, sw = [], 0
+        for _ in range(reps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.depth(Xd, Zd, out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+            sw += ctx.last_stats.sweeps
+        outs[name] = out.clone()
+        host = tukey.Context(dev.index, mode=mode)
+        host.depth(d.X, d.Zq[:1])
+        lat = []
+        for r in range(reps):
+            z = d.Zq[r % d.m: r % d.m + 1]
+            t0 = time.perf_counter()
+            host.depth(d.X, z)
+            lat.append(1e3 * (time.perf_counter() - t0))
+        lat.sort()
+        med = sorted(ms)[len(ms) // 2]
+        res[name] = {"ms_per_call": med, "queries_per_s": d.m / (med / 1e3),
+                     "sweeps_per_s": sw / reps / (med / 1e3),
+                     "one_query_call_ms_p50": lat[len(lat) // 2], "one_query_call_ms_max": lat[-1]}
+    res["same_results"] = bool(torch.equal(outs["filtered"], outs["plain_exact"]))
+    res["workload"] = "W1: p=3, n=300 uniform ints in [-127,127], 16 queries (8 data rows, 8 uniform)"
+    res["timing"] = ("ms_per_call: median of %d calls with device-resident inputs (CUDA events); "
+                     "one_query_call: td_depth from host buffers for one query, wall clock" % reps)
+    return res
+
+
 def _tuning(tukey, W, dev, stream, flush, w2_default_ms, w3_default_ms):
     """The autotuner on the two batched forms: a context tuned by td_autotune
     for every (dimension, octave of n) the workload holds, timed like the
@@ -588,6 +635,7 @@ def run_ours(a):
         line["tuning"] = _tuning(tukey, W, dev, stream, flush, 1e3 * t_total / a.steps,
                                  line["batched"]["ms_per_call"])
         line["stream"] = _stream_w5(tukey, W, dev, a.stream_seconds)
+        line["small_w1"] = _small_w1(tukey, W, dev, stream, flush)
     if not a.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(d, a.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -2049,6 +2049,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
      * the fine test. */
     constexpr int UNR = TD_ROUND / 32;
     constexpr int NPR = UNR / 2; /* pairs per lane and round */
+    constexpr bool HALF_TAIL = D >= 5;
     /* the coarse histogram carries the previous sweeps' counts (clean),
      * unless a sweep went past the coarse bound and built its fine
      * histogram in the same storage.  At D = 6 the flag costs spills, and
@@ -2061,7 +2062,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
         prev_u = 0u;
     }
     __syncwarp();
-    auto round = [&](int i0) {
+    auto round_full = [&](int i0) {
         int slot[UNR];
         uint32_t inc[UNR];
         float4 pl[NPR][NPL];
@@ -2076,15 +2077,46 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
 #pragma unroll
         for (int u = 0; u < UNR; ++u) td_reds_add(cq + ((unsigned)slot[u] << 7), inc[u]);
     };
-    /* the last, partial round runs like the others over its padding zeros */
-    for (int i0 = 0; i0 < nnz; i0 += 32 * UNR) round(i0);
+    /* D >= 5: a round of NH pairs per lane (NPR, or 1 for a last round of at
+     * most 64 points) */
+    auto round = [&](int i0, auto nh_c) {
+        constexpr int NH = decltype(nh_c)::value;
+        int slot[2 * NH];
+        uint32_t inc[2 * NH];
+        float4 pl[NH][NPL];
+        /* all loads of the round first (the accesses keep program order) */
+        const unsigned ba = xq + 8u * (unsigned)i0; /* pair i0/2 + l */
+#pragma unroll
+        for (int h = 0; h < NH; ++h)
+#pragma unroll
+            for (int c = 0; c < NPL; ++c) pl[h][c] = td_lds128(ba + 512u * h + c * pstride);
+#pragma unroll
+        for (int h = 0; h < NH; ++h) td_pair_rows<D>(pl[h], C, slot[2 * h], slot[2 * h + 1], inc[2 * h], inc[2 * h + 1]);
+#pragma unroll
+        for (int u = 0; u < 2 * NH; ++u) td_reds_add(cq + ((unsigned)slot[u] << 7), inc[u]);
+    };
+    /* the last, partial round runs like the others over its padding zeros;
+     * at D >= 5 (short rows: up to a fifth of the points are padding) at
+     * half width when its points fit in 64 -- at D <= 4 that form of the
+     * loop measured slower than the padding it saves */
+    int pad;
+    if constexpr (HALF_TAIL) {
+        const int full = nnz & ~(TD_ROUND - 1), rem = nnz - full;
+        for (int i0 = 0; i0 < full; i0 += TD_ROUND) round(i0, std::integral_constant<int, NPR>{});
+        if (rem > TD_ROUND / 2) round(full, std::integral_constant<int, NPR>{});
+        else if (rem > 0) round(full, std::integral_constant<int, 1>{});
+        pad = rem == 0 ? 0 : (rem > TD_ROUND / 2 ? TD_ROUND : TD_ROUND / 2) - rem;
+    } else {
+        for (int i0 = 0; i0 < nnz; i0 += 32 * UNR) round_full(i0);
+        pad = ((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz;
+    }
     __syncwarp();
     const uint32_t hUt = W.hist[32 * 32 + lane];
     const uint32_t hU = hUt - prev_u;
     prev_u = hUt;
     /* uncertain points: the padding points of the last round are zeros,
      * whose key is NaN, so each of them added one event to row 32 too */
-    const int nu = td_wsum((int)(hU >> 16)) - (((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz);
+    const int nu = td_wsum((int)(hU >> 16)) - pad;
     n_exact += (uint64_t)nu;
 
     /* Pass 1: per-lane totals of the +1/-1 events, i.e. a histogram of 32
@@ -2370,6 +2402,7 @@ __device__ __forceinline__ void td_sweep_dual(const float *xs, int npc, int nnz,
     constexpr int NPL = (D + 1) / 2;
     constexpr int UNR = TD_ROUND / 32;
     constexpr int NPR = UNR / 2;
+    constexpr bool HALF_TAIL = D >= 5;
     const unsigned xq = td_saddr(xs) + 16u * (unsigned)lane;
     const unsigned pstride = 16u * (unsigned)npc;
     const unsigned cqA = td_saddr(W.hist) + 4u * (unsigned)lane;
@@ -2380,7 +2413,7 @@ __device__ __forceinline__ void td_sweep_dual(const float *xs, int npc, int nnz,
         prev[0] = prev[1] = prev[2] = prev[3] = 0u;
     }
     __syncwarp();
-    auto round = [&](int i0) {
+    auto round_full = [&](int i0) {
         const unsigned ba = xq + 8u * (unsigned)i0;
 #pragma unroll
         for (int h = 0; h < NPR; ++h) {
@@ -2397,14 +2430,45 @@ __device__ __forceinline__ void td_sweep_dual(const float *xs, int npc, int nnz,
             td_reds_add(cqB + ((unsigned)sb1 << 7), ib1);
         }
     };
-    for (int i0 = 0; i0 < nnz; i0 += 32 * UNR) round(i0);
+    /* D >= 5: a round of NH pairs per lane (NPR, or 1 for a last round of
+     * at most 64 points) */
+    auto round = [&](int i0, auto nh_c) {
+        constexpr int NH = decltype(nh_c)::value;
+        const unsigned ba = xq + 8u * (unsigned)i0;
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            float4 pl[NPL];
+#pragma unroll
+            for (int c = 0; c < NPL; ++c) pl[c] = td_lds128(ba + 512u * h + c * pstride);
+            int sa0, sa1, sb0, sb1;
+            uint32_t ia0, ia1, ib0, ib1;
+            td_pair_rows<D>(pl, CA, sa0, sa1, ia0, ia1);
+            td_pair_rows<D>(pl, CB, sb0, sb1, ib0, ib1);
+            td_reds_add(cqA + ((unsigned)sa0 << 7), ia0);
+            td_reds_add(cqA + ((unsigned)sa1 << 7), ia1);
+            td_reds_add(cqB + ((unsigned)sb0 << 7), ib0);
+            td_reds_add(cqB + ((unsigned)sb1 << 7), ib1);
+        }
+    };
+    /* the last round at half width when its points fit in 64, at D >= 5
+     * (as in td_sweep_filtered) */
+    int pad;
+    if constexpr (HALF_TAIL) {
+        const int full = nnz & ~(TD_ROUND - 1), rem = nnz - full;
+        for (int i0 = 0; i0 < full; i0 += TD_ROUND) round(i0, std::integral_constant<int, NPR>{});
+        if (rem > TD_ROUND / 2) round(full, std::integral_constant<int, NPR>{});
+        else if (rem > 0) round(full, std::integral_constant<int, 1>{});
+        pad = rem == 0 ? 0 : (rem > TD_ROUND / 2 ? TD_ROUND : TD_ROUND / 2) - rem;
+    } else {
+        for (int i0 = 0; i0 < nnz; i0 += 32 * UNR) round_full(i0);
+        pad = ((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz;
+    }
     __syncwarp();
     /* uncertain points (row 32), padding zeros of the last round included */
     const uint32_t uA = W.hist[32 * 32 + lane], uB = W.hist[TD_COARSE_WORDS + 32 * 32 + lane];
     const uint32_t hA = uA - prev[1], hB = uB - prev[3];
     prev[1] = uA;
     prev[3] = uB;
-    const int pad = ((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz;
     const uint32_t usum = (uint32_t)td_wsum((int)((hA >> 16) + ((hB >> 16) << 16)));
     nuA = (int)(usum & 0xFFFFu) - pad;
     nuB = (int)(usum >> 16) - pad;

@@ -1278,6 +1278,19 @@ struct TdWarpSmem {
  * shares its storage with the fine histogram, bucket ids and lists, which
  * only the few sweeps that go past the coarse bound build. */
 #define TD_COARSE_WORDS (33 * 32)
+/* Rows of the two-subset sweep's coarse histograms (the table keeps its
+ * 33 x 32 words).  At D >= 5 rows are short, pass 1 weighs more in every
+ * sweep and the running minimum is far below almost every bound: 8 rows
+ * gave W3 4.83 s (32 rows: 5.08 s, 16: 4.90 s, 4: 4.84 s) and W4 136.9 ms
+ * (144.1, 137.2, 142.2) with about as many rescans.  At D = 4, 16 or 8 rows
+ * made W2 0.5% slower. */
+#ifndef TD_DUAL_ROWS5
+#define TD_DUAL_ROWS5 8
+#endif
+#ifndef TD_DUAL_ROWS4
+#define TD_DUAL_ROWS4 32
+#endif
+#define TD_DUAL_ROWS(D) ((D) >= 5 ? TD_DUAL_ROWS5 : ((D) == 4 ? TD_DUAL_ROWS4 : 32))
 
 /* Histogram words (coarse and fine): the high half counts every event of the
  * bucket, the low half its +1 events (points of orientation -), so that a
@@ -1895,7 +1908,7 @@ __device__ __forceinline__ void td_pair_slots(const float4 (&pl)[(D + 1) / 2], c
  * else 32 (uncertain at this level).  The same computation as
  * td_pair_slots with the magic constant of spacing 1/16, so the same
  * certification argument holds with 32 buckets. */
-template <int D>
+template <int D, int ROWS = 32>
 __device__ __forceinline__ void td_pair_rows(const float4 (&pl)[(D + 1) / 2], const TdPairCoef<D> &C, int &rp,
                                              int &rq, uint32_t &ip, uint32_t &iq)
 {
@@ -1920,16 +1933,23 @@ __device__ __forceinline__ void td_pair_rows(const float4 (&pl)[(D + 1) / 2], co
     const td_f2x RR = td_pk(copysignf(rap, y2p), copysignf(raq, y2q));
     const td_f2x KN = td_fma2(Y1, RR, C.m1);  /* -key */
     const td_f2x DB = td_fma2(C.cE, RA, C.cU); /* delta */
-    const td_f2x FL = td_add2_rp(td_add2(KN, DB), C.nMc); /* -floor((key - delta) 16) */
-    const td_f2x FH = td_add2_rp(td_sub2(KN, DB), C.nMc); /* -floor((key + delta) 16) */
+    /* 32 rows: Mc = 1.5 * 2^19 (spacing 1/16, from C); ROWS = 16, 8 or 4
+     * rows: Mc = 1.5 * 2^20, 2^21 or 2^22 (spacing 2/ROWS), floor(key ROWS/2) */
+    constexpr int EMC = ROWS == 32 ? 19 : (ROWS == 16 ? 20 : (ROWS == 8 ? 21 : 22));
+    static_assert(ROWS == 32 || ROWS == 16 || ROWS == 8 || ROWS == 4, "coarse rows: 32, 16, 8 or 4");
+    constexpr uint32_t moffr = 0x80000000u - ((((uint32_t)(127 + EMC)) << 23) | 0x400000u);
+    const td_f2x nMr = ROWS == 32 ? C.nMc : td_pk(-1.5f * (float)(1 << EMC), -1.5f * (float)(1 << EMC));
+    const uint32_t moff = ROWS == 32 ? C.moffc : moffr;
+    const td_f2x FL = td_add2_rp(td_add2(KN, DB), nMr); /* -floor((key - delta) ROWS/2) */
+    const td_f2x FH = td_add2_rp(td_sub2(KN, DB), nMr); /* -floor((key + delta) ROWS/2) */
     float flp, flq, fhp, fhq;
     td_upk(FL, flp, flq);
     td_upk(FH, fhp, fhq);
-    /* row = bits + 2^31 - bits(Mc), capped at 32: one fused add-and-min */
-    const uint32_t blp = __viaddmin_u32((uint32_t)__float_as_int(flp), C.moffc, 32u);
-    const uint32_t blq = __viaddmin_u32((uint32_t)__float_as_int(flq), C.moffc, 32u);
-    rp = __float_as_int(flp) == __float_as_int(fhp) ? (int)blp : 32;
-    rq = __float_as_int(flq) == __float_as_int(fhq) ? (int)blq : 32;
+    /* row = bits + 2^31 - bits(Mc), capped at ROWS: one fused add-and-min */
+    const uint32_t blp = __viaddmin_u32((uint32_t)__float_as_int(flp), moff, (uint32_t)ROWS);
+    const uint32_t blq = __viaddmin_u32((uint32_t)__float_as_int(flq), moff, (uint32_t)ROWS);
+    rp = __float_as_int(flp) == __float_as_int(fhp) ? (int)blp : ROWS;
+    rq = __float_as_int(flq) == __float_as_int(fhq) ? (int)blq : ROWS;
     ip = 0x10000u + ((uint32_t)__float_as_int(y2p) >> 31);
     iq = 0x10000u + ((uint32_t)__float_as_int(y2q) >> 31);
 }
@@ -2394,7 +2414,7 @@ __device__ __forceinline__ int td_sweep_filtered(const float *xs, int npc, int n
  * uncertain points.  GA, GB: lower bounds of G(A), G(B) over the certified
  * points (the value of td_sweep_filtered's first bound); nuA, nuB: their
  * uncertain points. */
-template <int D>
+template <int D, int ROWS>
 __device__ __forceinline__ void td_sweep_dual(const float *xs, int npc, int nnz, const TdPairCoef<D> &CA,
                                               const TdPairCoef<D> &CB, const TdWarpSmem &W, int lane, bool &clean2,
                                               uint32_t (&prev)[4], int &GA, int &GB, int &nuA, int &nuB)
@@ -2422,8 +2442,8 @@ __device__ __forceinline__ void td_sweep_dual(const float *xs, int npc, int nnz,
             for (int c = 0; c < NPL; ++c) pl[c] = td_lds128(ba + 512u * h + c * pstride);
             int sa0, sa1, sb0, sb1;
             uint32_t ia0, ia1, ib0, ib1;
-            td_pair_rows<D>(pl, CA, sa0, sa1, ia0, ia1);
-            td_pair_rows<D>(pl, CB, sb0, sb1, ib0, ib1);
+            td_pair_rows<D, ROWS>(pl, CA, sa0, sa1, ia0, ia1);
+            td_pair_rows<D, ROWS>(pl, CB, sb0, sb1, ib0, ib1);
             td_reds_add(cqA + ((unsigned)sa0 << 7), ia0);
             td_reds_add(cqA + ((unsigned)sa1 << 7), ia1);
             td_reds_add(cqB + ((unsigned)sb0 << 7), ib0);
@@ -2442,8 +2462,8 @@ __device__ __forceinline__ void td_sweep_dual(const float *xs, int npc, int nnz,
             for (int c = 0; c < NPL; ++c) pl[c] = td_lds128(ba + 512u * h + c * pstride);
             int sa0, sa1, sb0, sb1;
             uint32_t ia0, ia1, ib0, ib1;
-            td_pair_rows<D>(pl, CA, sa0, sa1, ia0, ia1);
-            td_pair_rows<D>(pl, CB, sb0, sb1, ib0, ib1);
+            td_pair_rows<D, ROWS>(pl, CA, sa0, sa1, ia0, ia1);
+            td_pair_rows<D, ROWS>(pl, CB, sb0, sb1, ib0, ib1);
             td_reds_add(cqA + ((unsigned)sa0 << 7), ia0);
             td_reds_add(cqA + ((unsigned)sa1 << 7), ia1);
             td_reds_add(cqB + ((unsigned)sb0 << 7), ib0);
@@ -2464,17 +2484,17 @@ __device__ __forceinline__ void td_sweep_dual(const float *xs, int npc, int nnz,
         pad = ((nnz + TD_ROUND - 1) & ~(TD_ROUND - 1)) - nnz;
     }
     __syncwarp();
-    /* uncertain points (row 32), padding zeros of the last round included */
-    const uint32_t uA = W.hist[32 * 32 + lane], uB = W.hist[TD_COARSE_WORDS + 32 * 32 + lane];
+    /* uncertain points (row ROWS), padding zeros of the last round included */
+    const uint32_t uA = W.hist[ROWS * 32 + lane], uB = W.hist[TD_COARSE_WORDS + ROWS * 32 + lane];
     const uint32_t hA = uA - prev[1], hB = uB - prev[3];
     prev[1] = uA;
     prev[3] = uB;
     const uint32_t usum = (uint32_t)td_wsum((int)((hA >> 16) + ((hB >> 16) << 16)));
     nuA = (int)(usum & 0xFFFFu) - pad;
     nuB = (int)(usum >> 16) - pad;
-    /* pass 1: lane l reads row l of both tables (XOR-rotated quads) */
     uint32_t accA, accB;
-    {
+    if constexpr (ROWS == 32) {
+        /* pass 1: lane l reads row l of both tables (XOR-rotated quads) */
         const unsigned rb = (td_saddr(W.hist) + 128u * (unsigned)lane) | ((unsigned)(lane & 7) << 4);
         uint32_t tA = 0, tB = 0;
 #pragma unroll
@@ -2488,21 +2508,69 @@ __device__ __forceinline__ void td_sweep_dual(const float *xs, int npc, int nnz,
         accB = tB - prev[2];
         prev[0] = tA;
         prev[2] = tB;
+        clean2 = true;
+        const int cpA = td_ev_plus(accA), cmA = td_ev_minus(accA);
+        const int cpB = td_ev_plus(accB), cmB = td_ev_minus(accB);
+        const uint32_t am = (uint32_t)td_wsum(cmA + (cmB << 16)); /* orientation + points: one -1 event each */
+        const int AA = (int)(am & 0xFFFFu), AB = (int)(am >> 16);
+        const int netA = cpA - cmA, netB = cpB - cmB;
+        const int v = netA + netB * 65536;
+        const int ex = td_wscan_incl(v, lane) - v;
+        const int exA = (int)(int16_t)(ex & 0xFFFF);
+        const int exB = (ex - exA) >> 16;
+        const int PA = AA + exA, PB = AB + exB;
+        const int ncA = nnz - nuA, ncB = nnz - nuB;
+        GA = td_wmin(min(PA - cmA, ncA - (PA + cpA)));
+        GB = td_wmin(min(PB - cmB, ncB - (PB + cpB)));
+    } else {
+        /* pass 1 over ROWS rows: the S = 32/ROWS lanes 2r.. of row r (lane l:
+         * row r = l / S, part k = l % S) read 8/S of its quads each, in an
+         * order rotated by r so that every quarter warp touches distinct
+         * banks, and add their sums with S - 1 XOR-shuffles; the scan over
+         * rows steps S lanes at a time */
+        constexpr int S = 32 / ROWS, QP = 8 / S;
+        const int r = lane / S, k = lane % S;
+        const unsigned rb = td_saddr(W.hist) + 128u * (unsigned)r + 16u * (unsigned)(k * QP);
+        uint32_t tA = 0, tB = 0;
+#pragma unroll
+        for (int j = 0; j < QP; ++j) {
+            const unsigned a = rb + 16u * (unsigned)(j ^ (r & (QP - 1)));
+            const float4 va = td_lds128(a);
+            const float4 vb = td_lds128(a + 4u * TD_COARSE_WORDS);
+            tA += __float_as_uint(va.x) + __float_as_uint(va.y) + __float_as_uint(va.z) + __float_as_uint(va.w);
+            tB += __float_as_uint(vb.x) + __float_as_uint(vb.y) + __float_as_uint(vb.z) + __float_as_uint(vb.w);
+        }
+#pragma unroll
+        for (int o = 1; o < S; o <<= 1) {
+            tA += __shfl_xor_sync(TD_FULL, tA, o);
+            tB += __shfl_xor_sync(TD_FULL, tB, o);
+        }
+        accA = tA - prev[0];
+        accB = tB - prev[2];
+        prev[0] = tA;
+        prev[2] = tB;
+        clean2 = true;
+        const int cpA = td_ev_plus(accA), cmA = td_ev_minus(accA);
+        const int cpB = td_ev_plus(accB), cmB = td_ev_minus(accB);
+        /* orientation + points: one -1 event each, one lane per row */
+        const uint32_t am = (uint32_t)td_wsum(k == 0 ? cmA + (cmB << 16) : 0);
+        const int AA = (int)(am & 0xFFFFu), AB = (int)(am >> 16);
+        const int netA = cpA - cmA, netB = cpB - cmB;
+        const int v = netA + netB * 65536;
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < ROWS; o <<= 1) {
+            const int u = __shfl_up_sync(TD_FULL, inc, o * S);
+            if (r >= o) inc += u;
+        }
+        const int ex = inc - v;
+        const int exA = (int)(int16_t)(ex & 0xFFFF);
+        const int exB = (ex - exA) >> 16;
+        const int PA = AA + exA, PB = AB + exB;
+        const int ncA = nnz - nuA, ncB = nnz - nuB;
+        GA = td_wmin(min(PA - cmA, ncA - (PA + cpA)));
+        GB = td_wmin(min(PB - cmB, ncB - (PB + cpB)));
     }
-    clean2 = true;
-    const int cpA = td_ev_plus(accA), cmA = td_ev_minus(accA);
-    const int cpB = td_ev_plus(accB), cmB = td_ev_minus(accB);
-    const uint32_t am = (uint32_t)td_wsum(cmA + (cmB << 16)); /* orientation + points: one -1 event each */
-    const int AA = (int)(am & 0xFFFFu), AB = (int)(am >> 16);
-    const int netA = cpA - cmA, netB = cpB - cmB;
-    const int v = netA + netB * 65536;
-    const int ex = td_wscan_incl(v, lane) - v;
-    const int exA = (int)(int16_t)(ex & 0xFFFF);
-    const int exB = (ex - exA) >> 16;
-    const int PA = AA + exA, PB = AB + exB;
-    const int ncA = nnz - nuA, ncB = nnz - nuB;
-    GA = td_wmin(min(PA - cmA, ncA - (PA + cpA)));
-    GB = td_wmin(min(PB - cmB, ncB - (PB + cpB)));
 }
 
 /* Tight-set correction m_S after a sweep.  Tight points are those with bucket
@@ -2718,7 +2786,7 @@ __device__ void td_warp_filtered(const TdLaunch &L, int q, const float *xs, int 
                 const TdPairCoef<D> CA = td_pair_coef<D>(FA, FB, EA, blog2);
                 const TdPairCoef<D> CB = td_pair_coef<D>(FA2, FB2, EB, blog2);
                 int GA, GB, nuA, nuB;
-                td_sweep_dual<D>(xs, npc, nnz, CA, CB, W, lane, clean2, prev2, GA, GB, nuA, nuB);
+                td_sweep_dual<D, TD_DUAL_ROWS(D)>(xs, npc, nnz, CA, CB, W, lane, clean2, prev2, GA, GB, nuA, nuB);
                 clean = false; /* the dual sweep used table A's storage */
                 /* a subset whose bound does not reach best is swept again alone
                  * (repeating the coarse pass there measured faster than a

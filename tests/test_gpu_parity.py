@@ -49,6 +49,20 @@ def test_small_random_with_ties(ctx, plain, p):
         _check_both(ctx, plain, X, np.vstack([rows, unif]))
 
 
+@pytest.mark.parametrize("nnz", [63, 64, 65])
+def test_round_tails_p5(ctx, nnz):
+    """p = 5 rows of 63, 64 and 65 nonzero points: the last round of the
+    coarse pass runs at half width when its points fit in 64 (one short of,
+    exactly at and one past that): the filtered form against the oracle, two
+    deep queries near the centre (not data points, so every row counts)."""
+    rng = np.random.default_rng(900 + nnz)
+    X = random_case(rng, 5, nnz, 60, tie_rate=0.2)
+    Z = np.array([[1, 2, -1, 0, 3], [-2, 1, 0, 2, -1]], np.int32)
+    assert not (X[:, None, :] == Z[None, :, :]).all(axis=2).any()
+    want = oracle.depth_many(X, Z)
+    assert np.array_equal(ctx.depth(X, Z), want)
+
+
 @pytest.mark.parametrize("p", [3, 4, 5, 6])
 def test_tie_heavy_small_grid(ctx, plain, p):
     """Coordinates in {-2..2}: many equal directions, tight sets and duplicates."""

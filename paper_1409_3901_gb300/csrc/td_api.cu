@@ -409,7 +409,7 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
         L.scratch_per_warp = td_scratch_per_warp_critical(P.nmax);
         const size_t smem = td_critical_smem(P.nmax, P.pmax);
         TDCK(td_launch_setup(L, s));
-        ++nl;
+        nl += 2; /* set-up and the data-direction bound */
         std::vector<TdQuery> hq(P.nq);
         TDCK(cudaMemcpyAsync(hq.data(), w.q.p, P.nq * sizeof(TdQuery), cudaMemcpyDeviceToHost, s));
         TDCK(cudaStreamSynchronize(s));
@@ -431,7 +431,7 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
         L.warps = kWarpsPlain;
         size_t smem = td_plain_smem(P.nmax, P.pmax, kWarpsPlain);
         TDCK(td_launch_setup(L, s));
-        ++nl;
+        nl += 2; /* set-up and the data-direction bound */
         std::vector<TdQuery> hq(P.nq);
         TDCK(cudaMemcpyAsync(hq.data(), w.q.p, P.nq * sizeof(TdQuery), cudaMemcpyDeviceToHost, s));
         TDCK(cudaStreamSynchronize(s));
@@ -450,7 +450,7 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
         nl += 2;
     } else {
         TDCK(td_launch_setup(Lf, s));
-        nl = 1;
+        nl = 2; /* set-up and the data-direction bound */
         if (Lf.adia) {
             /* Algorithm 3, Steps 2-5(a): the search sets each query's subset
              * range, staging order and running minimum for the sweep */
@@ -652,7 +652,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
             ctx->gvalid = true;
         }
         TDCK(cudaGraphLaunch(ctx->gexec, s));
-        launches = 4 + std::min(P.pmax, 6) - 1; /* set-up, tiles, sweeps for D = 2..min(p,6), wide, finalize */
+        launches = 5 + std::min(P.pmax, 6) - 1; /* set-up, bound, tiles, sweeps for D = 2..min(p,6), wide, finalize */
         if (L.adia) launches += std::max(0, std::min(P.pmax, 6) - 2); /* search kernels, D = 3..min(p,6) */
     } else {
         rc = enqueue_kernels(ctx, ctx->w, P, L, o, blog2, s, &launches, ctx->evs0, ctx->evs1);

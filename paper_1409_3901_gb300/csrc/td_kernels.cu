@@ -886,66 +886,83 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
         }
         L.qmin[q] = INT_MAX;
     }
-    /* An upper bound of T from data directions u = +-x_j (Algorithm 3,
-     * Step 2): T <= #{i : u'x_i <= 0} for every u, exact in int32 or int64.  qmin
-     * starts at that bound minus Z (T = Z + min V, and a sweep reports V
-     * exactly whenever it is below qmin), so the coarse bound prunes from the
-     * first sweep of every tile on.  No subset is skipped for it.  The bound
-     * costs n point evaluations per direction; ndir = min(n, subsets / 64)
-     * evenly spaced directions keep it near 1% of the subset loop (none for
-     * a loop of fewer than 64 subsets). */
-    __syncthreads();
-    if (Q->direct >= 0 || L.unseeded) return;
-    const int ndir = (int)min((int64_t)n, Q->nsub / 64);
+}
+
+/* An upper bound of T from data directions u = +-x_j (Algorithm 3, Step 2):
+ * T <= #{i : u'x_i <= 0} for every u, exact in int32 or int64.  qmin starts
+ * at that bound minus Z (T = Z + min V, and a sweep reports V exactly
+ * whenever it is below qmin), so the coarse bound prunes from the first
+ * sweep of every tile on.  No subset is skipped for it.  The bound costs n
+ * point evaluations per direction; ndir = min(n, subsets / 64) evenly spaced
+ * directions keep it near 1% of the subset loop (none for a loop of fewer
+ * than 64 subsets).  Runs after td_k_setup, TD_BOUND_SPLIT CTAs per query
+ * (CTA b: query b / split), one direction per warp at a time, the lanes
+ * splitting the points; the centred rows staged in shared memory when the
+ * dot products fit in int32. */
+__global__ void __launch_bounds__(256) td_k_bound(TdLaunch L, int split, int cap)
+{
+    extern __shared__ __align__(16) int32_t s_xc[]; /* n x p centred rows (int32 form) */
+    const int q = blockIdx.x / split, g = blockIdx.x % split;
+    const TdQuery &Q = L.q[q];
+    if (Q.direct != -1 || L.unseeded) return;
+    const int n = Q.n;
+    const int ndir = (int)min((int64_t)n, Q.nsub / 64);
     if (ndir <= 0) return;
-    __shared__ int s_ub;
-    if (threadIdx.x == 0) s_ub = INT_MAX;
-    __syncthreads();
-    int ub = INT_MAX;
+    const TdSet S = L.sets[Q.set];
+    const int p = S.p;
+    const int32_t *X = L.X + S.x_off;
+    const int32_t *z = L.Zq + (int64_t)q * TD_MAXD;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     /* the dot products in 32 bits when p max|x_c|^2 < 2^31 over every
      * centred coordinate (then every centred entry fits too) */
-    const int am = s_amax;
-    const bool n32 = am < 46341 && (int64_t)p * am * am < 2147483648LL;
-    int zc32[TD_MAXD];
-#pragma unroll
-    for (int c = 0; c < TD_MAXD; ++c) zc32[c] = s_z[c];
-    for (int kd = threadIdx.x; kd < ndir; kd += blockDim.x) {
+    const int am = Q.amax;
+    const bool n32 = am < 46341 && (int64_t)p * am * am < 2147483648LL && n * p <= cap;
+    if (n32) {
+        for (int e = threadIdx.x; e < n * p; e += blockDim.x) s_xc[e] = X[e] - z[e % p];
+        __syncthreads();
+    }
+    int ub = INT_MAX;
+    for (int kd = g * nw + w; kd < ndir; kd += split * nw) {
         const int j = (int)((int64_t)kd * n / ndir);
-        int64_t xj[TD_MAXD];
-        bool nz = false;
-#pragma unroll
-        for (int c = 0; c < TD_MAXD; ++c) {
-            xj[c] = c < p ? (int64_t)X[(int64_t)j * p + c] - s_z[c] : 0;
-            nz |= xj[c] != 0;
-        }
-        if (!nz) continue;
         int le = 0, ge = 0;
+        bool nz = false;
         if (n32) {
-            int xj32[TD_MAXD];
+            int xj[TD_MAXD];
 #pragma unroll
-            for (int c = 0; c < TD_MAXD; ++c) xj32[c] = (int)xj[c];
-            for (int i = 0; i < n; ++i) {
-                const int32_t *xi = X + (int64_t)i * p;
+            for (int c = 0; c < TD_MAXD; ++c) {
+                xj[c] = c < p ? s_xc[j * p + c] : 0;
+                nz |= xj[c] != 0;
+            }
+            if (!nz) continue; /* uniform across the warp */
+            for (int i = lane; i < n; i += 32) {
+                const int32_t *xi = s_xc + i * p;
                 int dot = 0;
 #pragma unroll
                 for (int c = 0; c < TD_MAXD; ++c)
-                    if (c < p) dot += xj32[c] * (xi[c] - zc32[c]);
+                    if (c < p) dot += xj[c] * xi[c];
                 le += dot <= 0;
                 ge += dot >= 0;
             }
         } else {
-            for (int i = 0; i < n; ++i) {
+            int64_t xj[TD_MAXD];
+#pragma unroll
+            for (int c = 0; c < TD_MAXD; ++c) {
+                xj[c] = c < p ? (int64_t)X[(int64_t)j * p + c] - z[c] : 0;
+                nz |= xj[c] != 0;
+            }
+            if (!nz) continue;
+            for (int i = lane; i < n; i += 32) {
                 int64_t dot = 0;
-                for (int c = 0; c < p; ++c) dot += xj[c] * ((int64_t)X[(int64_t)i * p + c] - s_z[c]);
+                for (int c = 0; c < p; ++c) dot += xj[c] * ((int64_t)X[(int64_t)i * p + c] - z[c]);
                 le += dot <= 0;
                 ge += dot >= 0;
             }
         }
+        le = td_wsum(le);
+        ge = td_wsum(ge);
         ub = min(ub, min(le, ge));
     }
-    atomicMin(&s_ub, ub);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_ub < INT_MAX) L.qmin[q] = s_ub - s_Z;
+    if (lane == 0 && ub < INT_MAX) atomicMin(&L.qmin[q], ub - Q.Z);
 }
 
 /* ====================================================================== */
@@ -3263,9 +3280,18 @@ int64_t td_scratch_per_warp(int nmax) { return (td_scratch_bytes(td_pow2_at_leas
 /* the critical-direction kernel lays its scratch out for 2 td_pow2_at_least(nmax) points */
 int64_t td_scratch_per_warp_critical(int nmax) { return td_scratch_per_warp(2 * td_pow2_at_least(nmax)); }
 
+/* Set-up, then the data-direction bound (two launches): about 1216 CTAs
+ * over the queries (eight per SM on 152 SMs), at least one per query and at
+ * most 32 per query, each staging its query's rows (up to 2048 x p int32,
+ * 48 KB; longer rows take the global-memory path). */
 cudaError_t td_launch_setup(const TdLaunch &L, cudaStream_t s)
 {
     td_k_setup<<<L.nq, 256, 0, s>>>(L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || L.nq <= 0) return e;
+    const int split = std::max(1, std::min(32, (1216 + L.nq - 1) / L.nq));
+    const int cap = 2048 * std::max(1, std::min(L.pmax, TD_MAXD)); /* rows of up to 2048 points */
+    td_k_bound<<<L.nq * split, 256, (size_t)cap * 4, s>>>(L, split, cap);
     return cudaGetLastError();
 }
 

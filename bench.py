@@ -389,7 +389,7 @@ def run_reference(a):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    d = _workload(0)
+    d = _workload(0, True)
     import oracle
     oracle.build()
     z = d.Zq[0]

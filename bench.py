@@ -216,6 +216,19 @@ def _batched_w3(tukey, W, dev, stream, flush, peak_tops, steps=1):
             "timing": "CUDA events on the launch stream around the call; L2 flushed before it"}
 
 
+def _exact_path(st):
+    """The exact path's hit rate of one call: the projected points the FP32
+    filter could not certify (the subset's own points among them), and the
+    sweeps whose coarse bound did not reach the running minimum, so that
+    their points were projected again at the fine level and the uncertain
+    ones placed with exact integer arithmetic."""
+    pts = st.exact_points + st.filtered_points
+    return {"uncertain_point_fraction": st.exact_points / max(pts, 1),
+            "rescanned_sweep_fraction": st.rescanned_sweeps / max(st.sweeps, 1),
+            "resolved_sweep_fraction": st.resolved_buckets / max(st.sweeps, 1),
+            "tight_sweep_fraction": st.tight_exceptions / max(st.sweeps, 1)}
+
+
 def _small_w1(tukey, W, dev, stream, flush, reps=20):
     """The small case W1 (p = 3, n = 300, 16 queries, 300 subsets each): both
     forms on device-resident inputs (CUDA events on the launch stream, L2
@@ -628,6 +641,7 @@ def run_ours(a):
             "early_exit": early_line,
             "adia": adia_line,
             "stats_per_step": {k: v for k, v in ctx.last_stats.as_dict().items()},
+            "exact_path": _exact_path(ctx.last_stats),
             "clocks": clk}
     if not a.no_extra:
         from paper_1409_3901_gb300 import workloads as W

@@ -167,13 +167,26 @@ def _peaks():
         return {"sm_max_mhz": 2070.0}, "fallback"
 
 
+KERNEL_SOURCES = ("td_kernels.cu", "td_internal.h", "td_exact.cuh", "td_adia.cuh", "td_critical.cuh",
+                  "td_wide.cuh")
+
+
+def kernel_sources_sha():
+    """sha256[:16] over the sweep kernel's translation unit: td_kernels.cu and
+    the headers it includes, in that order."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1409_3901_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _traffic_for_current_kernel():
     """DRAM bytes per launch of the sweep kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
-    src = os.path.join(ROOT, "paper_1409_3901_gb300", "csrc", "td_kernels.cu")
+    valid only while the kernel's sources are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "td_k_filtered_w2.json")
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = kernel_sources_sha()
         rec = json.load(open(path))
         if rec.get("kernel_source_sha") == h:
             return rec.get("dram_bytes_per_launch_full")

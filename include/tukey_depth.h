@@ -106,7 +106,7 @@ typedef struct {
     int32_t subsets_per_warp; /* work-tile size (subsets per warp per tile); 0 = the value td_autotune
                                  (or td_set_tuned) stored in the context for the query's effective
                                  dimension and octave of its nonzero point count, else a size rule
-                                 (about 2^16 point evaluations per warp and tile, 4 to 256) */
+                                 (about 3 * 2^16 point evaluations per warp and tile, 4 to 1024) */
     int32_t buckets_log2;     /* angular buckets of the rare exact path = 2^buckets_log2; 0 = about
                                  one per two points (7 to 11); measured to make no difference */
     int32_t early_exit;       /* nonzero: filtered mode stops sweeping a query once its running

@@ -490,15 +490,13 @@ int enqueue_kernels(td_ctx *ctx, Work &w, const Plan &P, const TdLaunch &Lf, con
 }
 
 /* Persistent grids of the sweep kernels (D = 2 .. min(pmax, 6)), each sized
- * for its own dimension (rows of at most nmaxD points, stride 4 or 8 floats);
- * sets the dynamic shared memory attribute of each, and the CTA width (one
- * for the whole call: the tile kernel sizes every query's tiles by it).
- * Returns the scratch bytes the largest grid needs, or 0 if a kernel cannot
- * be resident. */
-size_t filtered_grids(td_ctx *ctx, const Plan &P, const td_options &o, int *grid, int *warps)
+ * for its own dimension (rows of at most nmaxD points, stride 4 or 8 floats),
+ * in CTAs of kWarpsFiltered warps; sets the dynamic shared memory attribute
+ * of each.  Returns the scratch bytes the largest grid needs, or 0 if a
+ * kernel cannot be resident. */
+size_t filtered_grids(td_ctx *ctx, const Plan &P, const td_options &o, int *grid)
 {
     const int wsel = kWarpsFiltered;
-    *warps = wsel;
     size_t scratch = 256;
     for (int i = 0; i < TD_NDIM; ++i) grid[i] = 0;
     for (int D = 2; D <= std::min(P.pmax, 6); ++D) {
@@ -560,7 +558,6 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     int grid = 0, warps_total = 0;
     (void)cudaGetLastError(); /* clear any stale error of an earlier call */
     int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
-    int fwarps = kWarpsFiltered;
     if (o.algorithm == TD_ALG_CRITICAL) {
         const size_t smem = td_critical_smem(P.nmax, P.pmax);
         int occ = 0;
@@ -580,7 +577,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
         warps_total = grid * kWarpsPlain;
         TDCK(alloc_work(ctx->w, P, warps_total, true));
     } else {
-        size_t scratch = filtered_grids(ctx, P, o, grids, &fwarps);
+        size_t scratch = filtered_grids(ctx, P, o, grids);
         if (scratch < 1) return TD_ERR_INVALID;
         TDCK(alloc_work(ctx->w, P, 0, true));
         if (o.algorithm == TD_ALG_ADIA) {
@@ -597,7 +594,7 @@ int run_batch(td_ctx *ctx, const td_dataset *sets, int k, td_stats *st)
     int rc = stage_inputs(ctx, ctx->w, ctx->hstage, P, sets, k, devptr, s, &x_arena);
     if (rc != TD_OK) return rc;
     TDCK(cudaMemsetAsync(ctx->w.ctr.p, 0, sizeof(TdCounters), s));
-    TdLaunch L = make_launch(ctx->w, P, x_arena, o, fwarps, blog2, ctx->tune);
+    TdLaunch L = make_launch(ctx->w, P, x_arena, o, kWarpsFiltered, blog2, ctx->tune);
     TDCK(cudaEventRecord(ctx->ev0, s));
     int launches = 0;
     if (o.mode == TD_MODE_FILTERED && o.use_graph && o.algorithm != TD_ALG_CRITICAL) {
@@ -1049,8 +1046,7 @@ int pump(td_stream *s)
     const int blog2 = blog2_for(P.nmax, o);
     (void)cudaGetLastError();
     int grids[TD_NDIM] = { 0, 0, 0, 0, 0 };
-    int fwarps = kWarpsFiltered;
-    size_t scratch = filtered_grids(ctx, P, o, grids, &fwarps);
+    size_t scratch = filtered_grids(ctx, P, o, grids);
     if (scratch < 1) return TD_ERR_INVALID;
     cudaError_t e = alloc_work(sl.w, P, 0, true);
     if (e == cudaSuccess && o.algorithm == TD_ALG_ADIA) {
@@ -1067,7 +1063,7 @@ int pump(td_stream *s)
     const int32_t *x_arena = nullptr;
     int rc = stage_inputs(ctx, sl.w, sl.hstage, P, sets.data(), (int)sets.size(), false, s->s, &x_arena);
     if (rc != TD_OK) return rc;
-    TdLaunch L = make_launch(sl.w, P, x_arena, o, fwarps, blog2, ctx->tune);
+    TdLaunch L = make_launch(sl.w, P, x_arena, o, kWarpsFiltered, blog2, ctx->tune);
     L.scratch = (char *)s->scratch.p;
     TDCK(cudaMemsetAsync(sl.w.ctr.p, 0, sizeof(TdCounters), s->s));
     int nl = 0;

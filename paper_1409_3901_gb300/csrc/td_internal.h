@@ -73,6 +73,7 @@ struct TdCounters {
     unsigned long long early;   /* subsets not swept because their query had reached 0 (early exit) */
     unsigned long long adia_pops, adia_subsets, adia_union, adia_fallback; /* Algorithm 3 search */
     unsigned long long rescanned; /* sweeps that went past the coarse bound */
+    unsigned long long wide;      /* queries the set-up flagged TD_DIRECT_WIDE */
 };
 
 /* Parameters of the work-queue launches. */

@@ -779,6 +779,7 @@ __global__ void __launch_bounds__(256) td_k_setup(TdLaunch L)
             Q->d = 0;
             Q->k = -1;
             Q->direct = first_shard ? TD_DIRECT_WIDE : INT_MAX;
+            if (first_shard) atomicAdd(&L.ctr->wide, 1ull);
             Q->amax = s_amax;
             for (int c = 0; c < TD_MAXD; ++c) {
                 Q->piv[c] = 0;
@@ -994,63 +995,74 @@ __host__ __device__ inline int td_auto_spw(int nnz, int64_t nrange, int warps)
  * (tile_prefix[(D-2)*(nq+1) + j]); resets the work counters. */
 __global__ void __launch_bounds__(1024) td_k_tiles(TdLaunch L)
 {
-    __shared__ int64_t s_part[TD_NDIM][1024];
+    __shared__ int64_t s_warp[32];
+    __shared__ int64_t s_block, s_total[TD_NDIM];
     const int nq = L.nq;
-    const int T = blockDim.x;
-    const int per = (nq + T - 1) / T;
-    const int beg = min((int)threadIdx.x * per, nq), end = min(beg + per, nq);
-    int64_t sum[TD_NDIM] = { 0, 0, 0, 0, 0 };
-    for (int j = beg; j < end; ++j) {
+    const int T = blockDim.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = T >> 5;
+    /* the tiles of query q = order[j]: its tile size, stored, and its count */
+    auto tiles_of = [&](int j, int &dim) -> int64_t {
         const int q = L.order[j];
         const TdQuery &Q = L.q[q];
         int spw = L.spw;
         if (spw <= 0 && Q.d >= 2 && Q.d <= 6 && Q.nnz > 0) spw = L.spw_tab[Q.d - 2][td_octave(Q.nnz)];
         if (spw <= 0) spw = td_auto_spw(Q.nnz, Q.hi - Q.lo, L.warps);
-        int64_t ts = (int64_t)spw * L.warps;
+        const int64_t ts = (int64_t)spw * L.warps;
         L.tile_size[q] = (int)ts;
-        int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? td_div_nonneg(Q.hi - Q.lo + ts - 1, ts) : 0;
-        if (Q.d >= 2 && Q.d <= 6) sum[Q.d - 2] += cnt;
-    }
-#pragma unroll
-    for (int D = 0; D < TD_NDIM; ++D) s_part[D][threadIdx.x] = sum[D];
-    __syncthreads();
-    /* exclusive scan of the T partial sums of dimension D by warp D: each
-     * lane takes a run of T/32 (at most 32) consecutive entries */
-    if ((threadIdx.x >> 5) < TD_NDIM) {
-        const int D = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int run = (T + 31) >> 5, b0 = min(lane * run, T), b1 = min(b0 + run, T);
-        int64_t loc = 0;
-        for (int t = b0; t < b1; ++t) loc += s_part[D][t];
-        int64_t inc = loc;
+        dim = (Q.d >= 2 && Q.d <= 6) ? Q.d - 2 : -1;
+        return (Q.k >= 0 && Q.hi > Q.lo) ? td_div_nonneg(Q.hi - Q.lo + ts - 1, ts) : 0;
+    };
+    /* block-wide exclusive scan of v (and the block total) */
+    auto block_scan = [&](int64_t v, int64_t &total) -> int64_t {
+        int64_t inc = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int64_t v = __shfl_up_sync(TD_FULL, inc, o);
-            if (lane >= o) inc += v;
+            const int64_t u = __shfl_up_sync(TD_FULL, inc, o);
+            if (lane >= o) inc += u;
         }
-        int64_t acc = inc - loc;
-        for (int t = b0; t < b1; ++t) {
-            const int64_t v = s_part[D][t];
-            s_part[D][t] = acc;
-            acc += v;
-        }
-        if (lane == 31) {
-            L.tile_prefix[(int64_t)D * (nq + 1) + nq] = inc;
-            L.ticket[D * TD_TICKET_STRIDE] = 0ull;
-        }
-    }
-    __syncthreads();
-    int64_t acc[TD_NDIM];
+        if (lane == 31) s_warp[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const int64_t x = lane < nw ? s_warp[lane] : 0;
+            int64_t xi = x;
 #pragma unroll
-    for (int D = 0; D < TD_NDIM; ++D) acc[D] = s_part[D][threadIdx.x];
-    for (int j = beg; j < end; ++j) {
-        const int q = L.order[j];
-        const TdQuery &Q = L.q[q];
-        const int64_t ts = L.tile_size[q];
-        const int64_t cnt = (Q.k >= 0 && Q.hi > Q.lo) ? td_div_nonneg(Q.hi - Q.lo + ts - 1, ts) : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(TD_FULL, xi, o);
+                if (lane >= o) xi += u;
+            }
+            if (lane < nw) s_warp[lane] = xi - x;
+            if (lane == 31) s_block = xi; /* nw <= 32: lane 31 holds the total */
+        }
+        __syncthreads();
+        const int64_t ex = s_warp[w] + inc - v;
+        total = s_block;
+        __syncthreads(); /* s_warp is rewritten by the next scan */
+        return ex;
+    };
+    /* rounds of T consecutive work-order positions (coalesced writes), a
+     * running carry per dimension; the block scan only for the dimensions
+     * that hold a query in the round (the others' entries are the carry:
+     * every dimension's array must be complete, since its sweep kernel maps
+     * a ticket to its query by a binary search over all of it) */
+    int64_t carry[TD_NDIM] = { 0, 0, 0, 0, 0 };
+    for (int base = 0; base < nq; base += T) {
+        const int j = base + (int)threadIdx.x;
+        int dim = -1;
+        const int64_t cnt = j < nq ? tiles_of(j, dim) : 0;
 #pragma unroll
         for (int D = 0; D < TD_NDIM; ++D) {
-            L.tile_prefix[(int64_t)D * (nq + 1) + j] = acc[D];
-            if (Q.d == D + 2) acc[D] += cnt;
+            int64_t ex = 0, tot = 0;
+            if (__syncthreads_or(dim == D)) ex = block_scan(dim == D ? cnt : 0, tot);
+            if (j < nq) L.tile_prefix[(int64_t)D * (nq + 1) + j] = carry[D] + ex;
+            carry[D] += tot;
+        }
+    }
+    if (threadIdx.x < TD_NDIM) s_total[threadIdx.x] = carry[threadIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int D = 0; D < TD_NDIM; ++D) {
+        if (threadIdx.x == 0) {
+            L.tile_prefix[(int64_t)D * (nq + 1) + nq] = s_total[D];
+            L.ticket[D * TD_TICKET_STRIDE] = 0ull;
         }
     }
 }

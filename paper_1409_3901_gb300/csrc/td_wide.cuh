@@ -331,6 +331,8 @@ __global__ void __launch_bounds__(TD_WIDE_THREADS) td_k_wide(TdLaunch L)
     TdW *wn = reinterpret_cast<TdW *>(smem + (size_t)nmax * 64 + (size_t)TD_WIDE_WARPS * TD_WIDE_LEVELS * nmax * 2);
     uint16_t *lst = lists + (size_t)w * TD_WIDE_LEVELS * nmax;
     TdW *wnw = wn + 6 * w;
+    /* the set-up kernel counted the flagged queries: none, nothing to walk */
+    if (*reinterpret_cast<volatile unsigned long long *>(&L.ctr->wide) == 0ull) return;
     for (int q = blockIdx.x; q < L.nq; q += gridDim.x) {
         TdQuery *Q = &L.q[q];
         if (Q->direct != TD_DIRECT_WIDE) continue; /* uniform over the CTA */
